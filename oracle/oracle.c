@@ -1,0 +1,666 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle of the SMC-MPC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline of the
+ * benchmark).  It shares no code with the CUDA path.  Loops are written in
+ * the order of the paper's definitions, with no blocking or fusion; OpenMP
+ * over independent particles is the only parallelism (timing only).
+ *
+ * Readings of the paper (Eele & Maciejowski, TR.693, 2015) used here:
+ *  R1  Controls are (turn rate w, climb rate hdot, speed change a), piecewise
+ *      constant over S equal segments, segment s = floor(k*S/H).  They map to
+ *      the paper's (gamma, phi, T) of Sec. 3.3 by sin(gamma) = hdot/v,
+ *      tan(phi) = w v / (g cos(gamma)) (coordinated turn) and
+ *      T = m (a + g sin(gamma)) + D.
+ *  R2  "Standard aerodynamic relations" (Sec. 3.3): lift from the coordinated
+ *      turn, L = m g cos(gamma)/cos(phi) = C_L q S; drag polar
+ *      D = q S (CD0 + CD2 C_L^2); ISA troposphere density
+ *      rho = 1.225 (1 - 2.2558e-5 z)^4.2559; fuel flow eta = Cf1 (1 + v/Cf2)
+ *      (Sec. 6.2, Eq. (blah)).
+ *  R3  Control constraints (gamma, phi, T of Sec. 3.4) are checked on the
+ *      step-k values, unary state constraints (z, v, m) on the step-(k+1)
+ *      state.  A violating aircraft gets weight 0 (cost +inf) and is frozen
+ *      from that step on: it takes no part in later separation checks.
+ *  R4  Landing (Eq. (TO_init)) is tested on the step-(k+1) state of arrivals;
+ *      the bearing cone uses atan2(y, x) with x > 0, the heading test
+ *      |wrap(chi - pi)| <= P_chi.  A landed aircraft is frozen, leaves the
+ *      separation checks and scores the best per-step value for the remaining
+ *      steps (Sec. 3.9).
+ *  R5  Separation (Eq. (avoidance)) is violated when d_h^2 < sep_h^2 and
+ *      |dz| < sep_v, checked at steps 1..H between flying aircraft.  Soft form:
+ *      mu * sum_k sum_j softplus_beta(min(1 - d_h/sep_h, 1 - |dz|/sep_v)).
+ *  R6  Deviation sums run over steps 1..H and are divided by H (the paper's
+ *      sum from k to k+H has H+1 terms).  The extra 1/H in J_T is dropped so
+ *      that 0 <= J_T <= 1 as the paper states.  The fuel term is
+ *      1 - F/(H dt Tmax eta(vmax)) (the printed form grows with fuel burned).
+ *  R7  Departure: A = bearing error |wrap(atan2(y,x) - theta_F)| (sup pi,
+ *      inf 0); B = |Z - z| with sup/inf the per-step means of
+ *      d0 +/- k dt vmax sin(gamma_max) (inf clipped at 0); C = |v - v_D| with
+ *      sup max(vmax - v_D, v_D - vmin).
+ *  R8  Arrival flow field (Eq. (flow)) restated in the mathematical heading
+ *      convention: the arc through the aircraft tangent to the runway at the
+ *      origin has central angle 2*theta_p (theta_p = atan2(y,x)), heading
+ *      chi_hat = pi + 2*theta_p, remaining arc length
+ *      s = r*theta_p/sin(theta_p) capped at 4r (continuous cap), glide angle
+ *      beta = atan2(z, s).  D = |wrap(chi - chi_hat)| (sup pi),
+ *      E = |beta - beta_f| (sup pi/2).
+ *  R9  Weights of Table coeff attach to the named terms: departure
+ *      (bearing, fuel, altitude, speed), arrival (flow heading, glide path,
+ *      fuel).  J_T = (1 - w_n) sum alpha J + w_n J_noise (Sec. 7.1).
+ *  R10 Per-sample cost c = -ln J_T; the product of Sec. 3.6 over M samples
+ *      becomes the mean cost, and the annealed log-weight is
+ *      l = -kappa_J * mean_m c with kappa_J = floor(3 + 5 exp(0.05 J))
+ *      (SampleSchedule of Sec. 5.1), J = 0..J_max-1.
+ *  R11 Wind (Sec. 3.9.1): grid nodes inclusive over the box; covariance
+ *      sigma^2 exp(-beta |dxy|) exp(-gamma |dz|) (sigma constant); time
+ *      factor a = exp(-dt*lam_t), lam_t read in 1/s.  The field is shared by
+ *      all particles of a solve (common random numbers); white turbulence is
+ *      drawn per particle, sample, aircraft and step.  Positions are clamped
+ *      into the box before trilinear interpolation.
+ *  R12 Resampling (Sec. 3.7) is systematic on a fixed-point CDF:
+ *      q_j = floor(w_j 2^40), S = inclusive prefix sum, Q = S_{L-1},
+ *      t_l = floor((l 2^32 + r) Q / (L 2^32)), a_l = min{j : S_j > t_l}.
+ *  R13 Perturbation (Algorithm 1): Gaussian random walk, clipped to the
+ *      control box.  Final selection (Sec. 3.8): the particle with the fewest
+ *      infeasible aircraft, then the smallest sum of mean costs (= the largest
+ *      product of weights), ties to the lowest index.
+ *  R14 Random numbers: Philox4x32-10, key = seed + scenario_id*0x9E3779B97F4A7C15,
+ *      counter (c0, c1, q | stream<<24, J | mpc_step<<16); uniforms use the
+ *      top 23 bits, ((x>>9)+0.5)/2^23 (an odd multiple of 2^-24, exact in FP32
+ *      and FP64); normals by Box-Muller.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+static const double G0 = 9.80665;
+
+/* ------------------------------------------------------------------ */
+/* random numbers                                                       */
+/* ------------------------------------------------------------------ */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {              /* Weyl key schedule */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double orc_uniform23(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) / 8388608.0;
+}
+
+void orc_box_muller(uint32_t xa, uint32_t xb, double *z0, double *z1)
+{
+    double ua = orc_uniform23(xa), ub = orc_uniform23(xb);
+    double r = sqrt(-2.0 * log(ua));
+    *z0 = r * cos(2.0 * M_PI * ub);
+    *z1 = r * sin(2.0 * M_PI * ub);
+}
+
+void orc_draw(const orc_problem *P, uint32_t c0, uint32_t c1, uint32_t q, uint32_t stream,
+              uint32_t J, uint32_t out[4])
+{
+    uint64_t s = P->seed + (uint64_t)P->scenario_id * 0x9E3779B97F4A7C15ull;
+    uint32_t key[2] = {(uint32_t)s, (uint32_t)(s >> 32)};
+    uint32_t ctr[4] = {c0, c1, (q & 0xFFFFFFu) | (stream << 24),
+                       (J & 0xFFFFu) | (P->mpc_step << 16)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* wind model, Sec. 3.9.1: the standard normals v_X(k), v_Y(k)           */
+/* ------------------------------------------------------------------ */
+
+void orc_wind_normals(const orc_problem *P, int m0, int mc, double *out)
+{
+    const int64_t Pn = (int64_t)P->grid[0] * P->grid[1] * P->grid[2];
+    for (int mm = 0; mm < mc; mm++) {
+        int m = m0 + mm;
+        for (int k = 0; k < P->H; k++) {
+            for (int64_t p = 0; p < Pn; p++) {
+                uint32_t w[4];
+                orc_draw(P, (uint32_t)p, (uint32_t)m << 8, (uint32_t)k, 3u, 0u, w);
+                double z0, z1;
+                orc_box_muller(w[0], w[1], &z0, &z1);
+                double *o = out + (((int64_t)mm * P->H + k) * Pn + p) * 2;
+                o[0] = z0;
+                o[1] = z1;
+            }
+        }
+    }
+}
+
+/* trilinear interpolation of one wind field W_k[p][2] */
+static void trilinear(const orc_problem *P, const double *Wk, double x, double y, double z,
+                      double *wx, double *wy)
+{
+    double pos[3] = {x, y, z};
+    int idx[3];
+    double t[3];
+    for (int d = 0; d < 3; d++) {
+        double lo = P->box_lo[d], hi = P->box_hi[d];
+        int n = P->grid[d];
+        double h = (hi - lo) / (n - 1);
+        double c = pos[d] < lo ? lo : (pos[d] > hi ? hi : pos[d]);
+        double f = (c - lo) / h;
+        int i = (int)floor(f);
+        if (i > n - 2) i = n - 2;
+        if (i < 0) i = 0;
+        idx[d] = i;
+        t[d] = f - i;
+    }
+    const int ny = P->grid[1], nz = P->grid[2];
+    double ax = 0.0, ay = 0.0;
+    for (int dx = 0; dx < 2; dx++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dz = 0; dz < 2; dz++) {
+                double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) *
+                           (dz ? t[2] : 1.0 - t[2]);
+                int64_t p = ((int64_t)(idx[0] + dx) * ny + (idx[1] + dy)) * nz + (idx[2] + dz);
+                ax += w * Wk[2 * p];
+                ay += w * Wk[2 * p + 1];
+            }
+    *wx = ax;
+    *wy = ay;
+}
+
+/* population density of Sec. 7.1, bilinear between grid nodes, 0 outside */
+static double popdense_at(const orc_problem *P, double x, double y)
+{
+    if (!P->popdense || P->pop_n[0] < 2 || P->pop_n[1] < 2) return 0.0;
+    if (x < P->pop_lo[0] || x > P->pop_hi[0] || y < P->pop_lo[1] || y > P->pop_hi[1]) return 0.0;
+    const int n0 = P->pop_n[0], n1 = P->pop_n[1];
+    double f0 = (x - P->pop_lo[0]) / ((P->pop_hi[0] - P->pop_lo[0]) / (n0 - 1));
+    double f1 = (y - P->pop_lo[1]) / ((P->pop_hi[1] - P->pop_lo[1]) / (n1 - 1));
+    int i0 = (int)floor(f0), i1 = (int)floor(f1);
+    if (i0 > n0 - 2) i0 = n0 - 2;
+    if (i1 > n1 - 2) i1 = n1 - 2;
+    if (i0 < 0) i0 = 0;
+    if (i1 < 0) i1 = 0;
+    double t0 = f0 - i0, t1 = f1 - i1;
+    const double *g = P->popdense;
+    return (1 - t0) * (1 - t1) * g[(int64_t)i0 * n1 + i1] + (1 - t0) * t1 * g[(int64_t)i0 * n1 + i1 + 1] +
+           t0 * (1 - t1) * g[(int64_t)(i0 + 1) * n1 + i1] + t0 * t1 * g[(int64_t)(i0 + 1) * n1 + i1 + 1];
+}
+
+/* absolute angular distance of an angle difference, in [0, pi] */
+static double angdist(double a)
+{
+    double r = fmod(fabs(a), 2.0 * M_PI);
+    return r > M_PI ? 2.0 * M_PI - r : r;
+}
+
+/* ------------------------------------------------------------------ */
+/* decision margins (used by the tests to set aside near-threshold      */
+/* cases, where FP32 and FP64 may legitimately decide differently)      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n_false;
+    double min_true, max_false;
+} conj_t;
+
+static void conj_init(conj_t *c) { c->n_false = 0; c->min_true = INFINITY; c->max_false = 0.0; }
+static void conj_add(conj_t *c, int ok, double margin)
+{
+    if (ok) {
+        if (margin < c->min_true) c->min_true = margin;
+    } else {
+        c->n_false++;
+        if (margin > c->max_false) c->max_false = margin;
+    }
+}
+static int conj_ok(const conj_t *c) { return c->n_false == 0; }
+/* a true conjunction flips when any member flips; a false one only when every false member does */
+static double conj_margin(const conj_t *c) { return c->n_false == 0 ? c->min_true : c->max_false; }
+static double rel(double a, double b, double scale) { return fabs(a - b) / fabs(scale); }
+
+/* ------------------------------------------------------------------ */
+/* rollout of one (particle, wind sample): Algorithm 1, inner loop body */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double x, y, z, v, chi, m, F;
+    int dead, landed, sepv;
+    double sA, sB, sC, sN, soft;
+    double margin, smargin;
+} acst;
+
+static double softplus(double g, double beta)
+{
+    double bg = beta * g;
+    return bg > 0 ? (bg + log1p(exp(-bg))) / beta : log1p(exp(bg)) / beta;
+}
+
+static void record(const acst *st, int N, double *traj)
+{
+    for (int i = 0; i < N; i++) {
+        double *o = traj + (int64_t)i * 8;
+        o[0] = st[i].x; o[1] = st[i].y; o[2] = st[i].z; o[3] = st[i].v;
+        o[4] = st[i].chi; o[5] = st[i].m; o[6] = st[i].F;
+        o[7] = st[i].dead + 2 * st[i].landed + 4 * st[i].sepv;
+    }
+}
+
+static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const double *Wm, int m,
+                           const double *ul, int64_t l, int J, acst *st, double *ch, double *cs,
+                           double *mg, double *smg, int64_t *live, double *traj)
+{
+    const int N = P->N, H = P->H, S = P->S;
+    const int64_t Pn = (int64_t)P->grid[0] * P->grid[1] * P->grid[2];
+    const double dt = P->dt;
+    const double sgmax = sin(P->gamma_max), tpmax = tan(P->phi_max);
+    const double Sh2 = P->sep_h * P->sep_h, Sv = P->sep_v;
+    int64_t nlive = 0;
+
+    for (int i = 0; i < N; i++) {
+        acst *s = &st[i];
+        memset(s, 0, sizeof(*s));
+        s->x = A[i].x; s->y = A[i].y; s->z = A[i].z;
+        s->v = A[i].v; s->chi = A[i].chi; s->m = A[i].m;
+        s->margin = INFINITY;
+        s->smargin = INFINITY;
+    }
+    if (traj) record(st, N, traj);
+
+    for (int k = 0; k < H; k++) {
+        const double *Wk = Wm + (int64_t)k * Pn * 2;
+        for (int i = 0; i < N; i++) {
+            acst *s = &st[i];
+            const orc_aircraft *a = &A[i];
+            if (s->dead || s->landed) continue;
+            nlive++;
+            const int seg = (int)(((int64_t)k * S) / H);
+            const double *uu = ul + ((int64_t)i * S + seg) * 3;
+            const double w = uu[0], hd = uu[1], acc = uu[2];
+
+            /* control constraints on the step-k values (Sec. 3.4) */
+            double sg = hd / s->v;
+            conj_t cc;
+            conj_init(&cc);
+            conj_add(&cc, fabs(sg) <= sgmax, rel(fabs(sg), sgmax, sgmax));
+            if (!(fabs(sg) < 1.0)) {
+                double cm = conj_margin(&cc);
+                if (cm < s->margin) s->margin = cm;
+                if (cm < s->smargin) s->smargin = cm;
+                s->dead = 1;
+                continue;
+            }
+            double cg = sqrt(1.0 - sg * sg);
+            double tp = w * s->v / (G0 * cg);
+            conj_add(&cc, fabs(tp) < tpmax, rel(fabs(tp), tpmax, tpmax));
+            double cphi = 1.0 / sqrt(1.0 + tp * tp);
+            double sphi = tp * cphi;
+            double base = 1.0 - 2.2558e-5 * s->z;
+            double rho = 1.225 * pow(base > 0.0 ? base : 0.0, 4.2559);
+            double qS = 0.5 * rho * s->v * s->v * a->S;
+            double CL = s->m * G0 * cg / (qS * cphi);
+            double D = qS * (a->CD0 + a->CD2 * CL * CL);
+            double T = s->m * (acc + G0 * sg) + D;
+            conj_add(&cc, T >= a->Tmin, rel(T, a->Tmin, a->Tmax));
+            conj_add(&cc, T <= a->Tmax, rel(T, a->Tmax, a->Tmax));
+            {
+                double cm = conj_margin(&cc);
+                if (cm < s->margin) s->margin = cm;
+                if (cm < s->smargin) s->smargin = cm;
+            }
+            if (!conj_ok(&cc)) { s->dead = 1; continue; }
+            double Lift = CL * qS;
+            double eta = a->Cf1 * (1.0 + s->v / a->Cf2);
+
+            /* disturbance: wind field plus white turbulence */
+            double wx, wy;
+            trilinear(P, Wk, s->x, s->y, s->z, &wx, &wy);
+            uint32_t tb[4];
+            orc_draw(P, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8), (uint32_t)(k >> 1), 0u,
+                     (uint32_t)J, tb);
+            double n0, n1;
+            if ((k & 1) == 0) orc_box_muller(tb[0], tb[1], &n0, &n1);
+            else              orc_box_muller(tb[2], tb[3], &n0, &n1);
+            wx += P->turb_sigma * n0;
+            wy += P->turb_sigma * n1;
+
+            /* explicit Euler step, Eq. (hor) */
+            double x1 = s->x + dt * (s->v * cos(s->chi) * cg) + wx * dt;
+            double y1 = s->y + dt * (s->v * sin(s->chi) * cg) + wy * dt;
+            double z1 = s->z + dt * (s->v * sg);
+            double v1 = s->v + dt * ((T - D) / s->m - G0 * sg);
+            double chi1 = s->chi + dt * (Lift * sphi / (s->m * s->v));
+            double burn = dt * (eta * T);
+            double m1 = s->m - burn;
+            s->F += burn;
+            s->x = x1; s->y = y1; s->z = z1; s->v = v1; s->chi = chi1; s->m = m1;
+
+            /* unary state constraints on the step-(k+1) state (Sec. 3.4) */
+            conj_t cu;
+            conj_init(&cu);
+            conj_add(&cu, z1 >= P->z_min, rel(z1, P->z_min, P->z_min));
+            conj_add(&cu, z1 <= P->z_max, rel(z1, P->z_max, P->z_max));
+            conj_add(&cu, v1 >= P->v_min, rel(v1, P->v_min, P->v_min));
+            conj_add(&cu, v1 <= P->v_max, rel(v1, P->v_max, P->v_max));
+            conj_add(&cu, m1 >= a->m_empty, rel(m1, a->m_empty, a->m_empty));
+            {
+                double cm = conj_margin(&cu);
+                if (cm < s->margin) s->margin = cm;
+                if (cm < s->smargin) s->smargin = cm;
+            }
+            if (!conj_ok(&cu)) { s->dead = 1; continue; }
+
+            double th = atan2(y1, x1);
+            if (a->type == 0) {
+                /* arrival: flow-field geometry and landing sector */
+                double r = sqrt(x1 * x1 + y1 * y1);
+                double ath = fabs(th);
+                double ratio = ath < 1e-3 ? 1.0 + th * th / 6.0 : ath / fmax(sin(ath), 0.25 * ath);
+                double sarc = r * ratio;
+                double beta = atan2(z1, sarc);
+                double chihat = M_PI + 2.0 * th;
+                double hdg = angdist(chi1 - M_PI);
+                conj_t cl;
+                conj_init(&cl);
+                conj_add(&cl, r <= P->P_runway, rel(r, P->P_runway, P->P_runway));
+                conj_add(&cl, beta <= P->P_beta, rel(beta, P->P_beta, P->P_beta));
+                conj_add(&cl, x1 > 0.0, fabs(x1) / P->P_runway);
+                conj_add(&cl, ath <= P->P_chi, rel(ath, P->P_chi, P->P_chi));
+                conj_add(&cl, hdg <= P->P_chi, rel(hdg, P->P_chi, P->P_chi));
+                conj_add(&cl, v1 <= P->P_vs, rel(v1, P->P_vs, P->P_vs));
+                {
+                    double cm = conj_margin(&cl);
+                    if (cm < s->margin) s->margin = cm;
+                    if (cm < s->smargin) s->smargin = cm;
+                }
+                if (conj_ok(&cl)) { s->landed = 1; continue; }
+                s->sA += angdist(chi1 - chihat);
+                s->sB += fabs(beta - P->beta_f);
+            } else {
+                s->sA += angdist(th - a->theta_F);
+                s->sB += fabs(a->Z - z1);
+                s->sC += fabs(v1 - a->v_D);
+            }
+            if (P->w_noise != 0.0) {
+                double za = z1 / P->A_c;
+                double h = 1.0 - za * za;
+                if (h < 0.0) h = 0.0;
+                s->sN += h * popdense_at(P, x1, y1);
+            }
+        }
+
+        /* binary separation constraints at step k+1, Eq. (avoidance) */
+        for (int i = 0; i < N; i++) {
+            if (st[i].dead || st[i].landed) continue;
+            for (int j = i + 1; j < N; j++) {
+                if (st[j].dead || st[j].landed) continue;
+                double dx = st[i].x - st[j].x, dy = st[i].y - st[j].y, dz = st[i].z - st[j].z;
+                double dh2 = dx * dx + dy * dy, adz = fabs(dz);
+                conj_t cp;
+                conj_init(&cp);
+                conj_add(&cp, dh2 < Sh2, rel(dh2, Sh2, Sh2));
+                conj_add(&cp, adz < Sv, rel(adz, Sv, Sv));
+                double cm = conj_margin(&cp);
+                if (cm < st[i].margin) st[i].margin = cm;
+                if (cm < st[j].margin) st[j].margin = cm;
+                if (conj_ok(&cp)) { st[i].sepv = 1; st[j].sepv = 1; }
+                if (cs) {
+                    double g = fmin(1.0 - sqrt(dh2) / P->sep_h, 1.0 - adz / Sv);
+                    double pen = softplus(g, P->sp_beta);
+                    st[i].soft += pen;
+                    st[j].soft += pen;
+                }
+            }
+        }
+        if (traj) record(st, N, traj + (int64_t)(k + 1) * N * 8);
+    }
+
+    /* objectives (Sec. 3.5, Sec. 7.1) and per-sample cost (Sec. 3.6) */
+    double smin = INFINITY;
+    for (int i = 0; i < N; i++) {
+        const acst *s = &st[i];
+        const orc_aircraft *a = &A[i];
+        const double eta_max = a->Cf1 * (1.0 + P->v_max / a->Cf2);
+        const double Fmax = H * dt * a->Tmax * eta_max;
+        const double Jf = 1.0 - s->F / Fmax;
+        double Jsum;
+        if (a->type == 1) {
+            double d0 = fabs(a->Z - a->z), c = P->v_max * sgmax * dt;
+            double supB = 0.0, infB = 0.0;
+            for (int k = 1; k <= H; k++) {
+                supB += d0 + k * c;
+                infB += (d0 - k * c) > 0.0 ? d0 - k * c : 0.0;
+            }
+            supB /= H;
+            infB /= H;
+            double J1 = 1.0 - (s->sA / H) / M_PI;
+            double J3 = (supB - s->sB / H) / (supB - infB);
+            double Cmax = fmax(P->v_max - a->v_D, a->v_D - P->v_min);
+            double J4 = 1.0 - (s->sC / H) / Cmax;
+            Jsum = P->alpha_dep[0] * J1 + P->alpha_dep[1] * Jf + P->alpha_dep[2] * J3 +
+                   P->alpha_dep[3] * J4;
+        } else {
+            double J1 = 1.0 - (s->sA / H) / M_PI;
+            double J3 = 1.0 - (s->sB / H) / (0.5 * M_PI);
+            Jsum = P->alpha_arr[0] * J1 + P->alpha_arr[1] * J3 + P->alpha_arr[2] * Jf;
+        }
+        double JT = (1.0 - P->w_noise) * Jsum + P->w_noise * (1.0 - s->sN / H);
+        double base = -log(JT > 1e-30 ? JT : 1e-30);
+        if (ch) ch[i] = (s->dead || s->sepv) ? INFINITY : base;
+        if (cs) cs[i] = s->dead ? INFINITY : base + P->mu_sep * s->soft;
+        if (mg) mg[i] = s->margin;
+        if (s->smargin < smin) smin = s->smargin;
+    }
+    if (smg) *smg = smin;
+    if (live) *live += nlive;
+}
+
+void orc_rollout(const orc_problem *P, const orc_aircraft *A, const double *W, int m0, int mc,
+                 const double *u, const int64_t *pidx, int Lsub, int J, int nthreads,
+                 double *cost_hard, double *cost_soft, double *margin, double *smargin,
+                 int64_t *live)
+{
+    const int N = P->N;
+    const int64_t Pn = (int64_t)P->grid[0] * P->grid[1] * P->grid[2];
+    const int64_t wstride = (int64_t)P->H * Pn * 2;
+    const int64_t ustride = (int64_t)N * P->S * 3;
+    int64_t total_live = 0;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads) reduction(+ : total_live)
+    for (int ll = 0; ll < Lsub; ll++) {
+        acst st[256];
+        int64_t nl = 0;
+        for (int mm = 0; mm < mc; mm++) {
+            int64_t o = ((int64_t)ll * mc + mm) * N;
+            rollout_sample(P, A, W + (int64_t)mm * wstride, m0 + mm, u + (int64_t)ll * ustride,
+                           pidx[ll], J, st, cost_hard ? cost_hard + o : NULL,
+                           cost_soft ? cost_soft + o : NULL, margin ? margin + o : NULL,
+                           smargin ? smargin + (int64_t)ll * mc + mm : NULL, &nl, NULL);
+        }
+        total_live += nl;
+    }
+    if (live) *live = total_live;
+}
+
+void orc_trajectory(const orc_problem *P, const orc_aircraft *A, const double *Wm, int m,
+                    const double *ul, int64_t l, int J, double *traj, double *cost_hard,
+                    double *cost_soft)
+{
+    acst st[256];
+    int64_t nl = 0;
+    rollout_sample(P, A, Wm, m, ul, l, J, st, cost_hard, cost_soft, NULL, NULL, &nl, traj);
+}
+
+/* ------------------------------------------------------------------ */
+/* weights (Sec. 3.6 with the schedule of Sec. 5.1)                      */
+/* ------------------------------------------------------------------ */
+
+int orc_kappa(int J)
+{
+    return (int)floor(3.0 + 5.0 * exp(0.05 * J));
+}
+
+void orc_lse(const double *cbar, int nseg, int L, double kappa, double *wtilde, double *lmax,
+             double *wsum)
+{
+    for (int s = 0; s < nseg; s++) {
+        const double *c = cbar + (int64_t)s * L;
+        double mx = -INFINITY;
+        for (int j = 0; j < L; j++) {
+            if (isfinite(c[j])) {
+                double l = -kappa * c[j];
+                if (l > mx) mx = l;
+            }
+        }
+        double sum = 0.0;
+        for (int j = 0; j < L; j++) {
+            double w = 0.0;
+            if (isfinite(c[j]) && mx > -INFINITY) w = exp(-kappa * c[j] - mx);
+            wtilde[(int64_t)s * L + j] = w;
+            sum += w;
+        }
+        if (lmax) lmax[s] = mx;
+        if (wsum) wsum[s] = sum;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* systematic resampling on a fixed-point CDF (Sec. 3.7)                  */
+/* ------------------------------------------------------------------ */
+
+uint32_t orc_resample_uniform(const orc_problem *P, int seg, int J)
+{
+    uint32_t w[4];
+    orc_draw(P, 0u, (uint32_t)seg, 0u, 2u, (uint32_t)J, w);
+    return w[0];
+}
+
+int orc_resample(const double *wtilde, int nseg, int L, const uint32_t *r, int32_t *anc)
+{
+    int ndeg = 0;
+    uint64_t *S = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(L > 0 ? L : 1));
+    for (int s = 0; s < nseg; s++) {
+        const double *w = wtilde + (int64_t)s * L;
+        uint64_t acc = 0;
+        for (int j = 0; j < L; j++) {
+            uint64_t q = 0;
+            if (w[j] >= 1.0) q = 1ull << 40;
+            else if (w[j] > 0.0) q = (uint64_t)(w[j] * 1099511627776.0);
+            acc += q;
+            S[j] = acc;
+        }
+        int32_t *a = anc + (int64_t)s * L;
+        if (acc == 0) {
+            for (int l = 0; l < L; l++) a[l] = l;
+            ndeg++;
+            continue;
+        }
+        const unsigned __int128 den = (unsigned __int128)(uint64_t)L << 32;
+        int j = 0;
+        for (int l = 0; l < L; l++) {
+            unsigned __int128 num = (unsigned __int128)((((uint64_t)l) << 32) + r[s]) * acc;
+            uint64_t t = (uint64_t)(num / den);
+            while (S[j] <= t) j++;
+            a[l] = j;
+        }
+    }
+    free(S);
+    return ndeg;
+}
+
+/* ------------------------------------------------------------------ */
+/* perturbation (Algorithm 1) and initialisation (Sec. 3.2)              */
+/* ------------------------------------------------------------------ */
+
+void orc_move(const orc_problem *P, const double *u, const int32_t *anc, int L, int J,
+              double *u_out)
+{
+    const int N = P->N, nc = 3 * P->S, nq = (nc + 3) / 4;
+    for (int l = 0; l < L; l++) {
+        for (int i = 0; i < N; i++) {
+            const int32_t a = anc[(int64_t)i * L + l];
+            const double *src = u + ((int64_t)a * N + i) * nc;
+            double *dst = u_out + ((int64_t)l * N + i) * nc;
+            for (int q = 0; q < nq; q++) {
+                uint32_t w[4];
+                orc_draw(P, (uint32_t)l, (uint32_t)i, (uint32_t)q, 1u, (uint32_t)J, w);
+                double z[4];
+                orc_box_muller(w[0], w[1], &z[0], &z[1]);
+                orc_box_muller(w[2], w[3], &z[2], &z[3]);
+                for (int t = 0; t < 4; t++) {
+                    int n = 4 * q + t;
+                    if (n >= nc) break;
+                    int c = n % 3;
+                    double v = src[n] + P->move_sigma[c] * z[t];
+                    if (v < P->ctrl_lo[c]) v = P->ctrl_lo[c];
+                    if (v > P->ctrl_hi[c]) v = P->ctrl_hi[c];
+                    dst[n] = v;
+                }
+            }
+        }
+    }
+}
+
+void orc_init_controls(const orc_problem *P, int L, double *u)
+{
+    const int N = P->N, nc = 3 * P->S, nq = (nc + 3) / 4;
+    for (int l = 0; l < L; l++)
+        for (int i = 0; i < N; i++) {
+            double *dst = u + ((int64_t)l * N + i) * nc;
+            for (int q = 0; q < nq; q++) {
+                uint32_t w[4];
+                orc_draw(P, (uint32_t)l, (uint32_t)i, (uint32_t)q, 4u, 0u, w);
+                for (int t = 0; t < 4; t++) {
+                    int n = 4 * q + t;
+                    if (n >= nc) break;
+                    int c = n % 3;
+                    dst[n] = P->ctrl_lo[c] + (P->ctrl_hi[c] - P->ctrl_lo[c]) * orc_uniform23(w[t]);
+                }
+            }
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* final selection (Sec. 3.8)                                            */
+/* ------------------------------------------------------------------ */
+
+int64_t orc_select(const double *cbar, int N, int L, double *best_sum, int *n_inf)
+{
+    int64_t best = -1;
+    int bn = N + 1;
+    double bs = INFINITY;
+    for (int l = 0; l < L; l++) {
+        int ni = 0;
+        double sum = 0.0;
+        for (int i = 0; i < N; i++) {
+            double c = cbar[(int64_t)i * L + l];
+            if (!isfinite(c)) ni++;
+            else sum += c;
+        }
+        if (ni < bn || (ni == bn && sum < bs)) {
+            best = l;
+            bn = ni;
+            bs = sum;
+        }
+    }
+    if (best_sum) *best_sum = (bn == 0) ? bs : INFINITY;
+    if (n_inf) *n_inf = bn;
+    return best;
+}
