@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the SMC-MPC hot path on GB300.
+
+One step = one SMC solve (Algorithm 1) of the 8-aircraft TMA workload
+(L = 65536 particles, M = 32 wind samples, H = 60 steps, 64x64x8 wind grid,
+30 annealing iterations): wind-field generation, 30 rollouts with costs,
+29 x (FP64 LSE, systematic resampling, move), final selection.
+Metric: aircraft-step-samples per second = L*M*N*H*J_max per solve / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves an independent replica (its own
+seed): scaling is weak, no collective touches the data path; the time is the
+maximum over ranks.  `--impl reference` times the FP64 CPU oracle on the host
+cores (rank 0 only) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "aircraft-step-samples/sec"
+UNIT = "aircraft-step-samples/s"
+WORKLOAD = "tma-8ac-L65536-M32-H60-grid64x64x8-J30"
+
+# Peaks: measured copy bandwidth from MEASURED_PEAKS.json when present; the FP32
+# CUDA-core peak is derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock.
+SMS, FP32_LANES = 152, 128
+
+
+def fp32_peak_tflops(sm_mhz):
+    return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+def flops_per_unit(p):
+    """Algorithmic FP32 operations of one aircraft-step-sample (one aircraft
+    advanced one step under one wind sample in one particle), counted from the
+    per-step formulas: +, -, *, /, sqrt, min/max/compare and each elementary
+    function count 1, an FMA 2.  Pairwise separation is counted once per
+    unordered pair ((N-1)/2 pairs per unit)."""
+    import numpy as np
+    base = 31 + 1        # control-derived quantities, limits, mass
+    wind = 21 + 28       # cell search in 3 axes, 7 lerps x 2 components
+    turb = 8 + 4         # Box-Muller per 2 normals (2 per step), 2 fma
+    euler = 24           # sincos, position/altitude/speed/heading, fuel (Kahan), unary checks
+    arr = 38             # bearing, arc, glide angle, landing sector, two compensated sums
+    dep = 22             # bearing error, altitude and speed deviations, three compensated sums
+    noise = 14 if p.w_noise != 0 else 0
+    pair = 8 + (9 if p.sep_mode != 0 else 0)
+    frac_arr = float(np.mean(p.aircraft["type"] == 0))
+    return base + wind + turb + euler + frac_arr * arr + (1 - frac_arr) * dep + noise + \
+        pair * (p.N - 1) / 2.0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples of one GPU during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Maximum of a float over all ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_problem(rank, base_seed=None):
+    """Rank r solves an independent replica of the workload with its own seed."""
+    import scenarios as S
+    p = S.config2() if base_seed is None else S.config2(seed=base_seed)
+    return p.copy(seed=p.seed + 1000003 * rank)
+
+
+def units_per_solve(p):
+    return p.L * p.M * p.N * p.H * p.J_max
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample(L_sample, nthreads):
+    """The FP64 oracle's full solve on the workload's traffic with L_sample
+    particles (all other sizes full); returns (units/s, seconds, units)."""
+    import oracle as O
+    import scenarios as S
+    p = S.config2().copy(L=L_sample)
+    t0 = time.perf_counter()
+    O.smc_solve(p, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    u = units_per_solve(p)
+    return u / dt, dt, u
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    Ls = args.reference_particles
+    for _ in range(args.warmup):
+        oracle_sample(Ls, cores)
+    times, units = [], 0
+    for _ in range(args.steps):
+        _, dt, units = oracle_sample(Ls, cores)
+        times.append(dt)
+    tot = sum(times)
+    value = units * args.steps / tot
+    sample = (f"oracle smc_solve of the workload's traffic with L={Ls} particles "
+              f"(M=32, N=8, H=60, J_max=30, 64x64x8 wind incl.), {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_particles": Ls, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args, world, rank, local):
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    pkg.build()
+    lib = pkg.lib()
+    p = replica_problem(rank)
+    solver = pkg.Solver(p, device=device)
+    h = solver.h
+    stream = torch.cuda.current_stream(device)
+    best_u = torch.empty((p.N, p.S, 3), dtype=torch.float32, device=device)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier(device_ids=[local])
+
+    # warm-up (also builds the wind-covariance factors)
+    for _ in range(args.warmup):
+        pkg.tma_solve(h, best_u, want_cost=False)
+    torch.cuda.synchronize(device)
+
+    # ---- timed region: K solves with inputs resident on the device
+    pkg.tma_profile_enable(h, True)
+    pkg.tma_profile_read(h, reset=True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid) if uuid else None
+    barrier()
+    torch.cuda.synchronize(device)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    n0 = lib.tma_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        pkg.tma_solve(h, best_u, want_cost=False)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    launches = lib.tma_launch_count() - n0
+    clocks = sampler.stop() if sampler else None
+    barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    prof = pkg.tma_profile_read(h, reset=True)
+    pkg.tma_profile_enable(h, False)
+    live_per_solve = pkg.tma_live_steps(h)
+    elapsed_max = max_over_ranks(elapsed_ms, world, device)
+    units = units_per_solve(p)
+    value = units * args.steps * world / (elapsed_max * 1e-3)
+
+    # ---- end to end: host state in, host controls out, through the C-ABI
+    x0 = torch.tensor([[float(a[k]) for k in ("x", "y", "z", "v", "chi", "m")] for a in p.aircraft],
+                      dtype=torch.float64).pin_memory()
+    out_h = torch.empty((p.N, p.S, 3), dtype=torch.float32).pin_memory()
+    cost = C.c_double()
+    statuses = set()
+    barrier()
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        st = lib.tma_solve_host(h, C.cast(C.c_void_p(x0.data_ptr()), C.POINTER(pkg.TmaState)),
+                                p.mpc_step, C.c_void_p(out_h.data_ptr()), C.byref(cost),
+                                pkg._stream(stream))
+        statuses.add(st)
+    torch.cuda.synchronize(device)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_max = max_over_ranks(e2e_s, world, device)
+    if statuses - {pkg.TMA_OK, pkg.TMA_WARN_DEGENERATE}:
+        raise RuntimeError(f"tma_solve_host failed: {statuses}")
+    e2e_value = units * args.steps * world / e2e_max
+
+    # ---- roofline of the rollout kernel (the dominant kernel)
+    roll_ms, roll_n = prof["rollout"]
+    fpu = flops_per_unit(p)
+    live_per_launch = live_per_solve / p.J_max
+    achieved = fpu * live_per_launch / (roll_ms / roll_n * 1e-3) / 1e12 if roll_n else None
+    sm_clock = 2070.0
+    peak = fp32_peak_tflops(sm_clock)
+    total_ms = sum(v[0] for v in prof.values())
+    roofline = {
+        "bound": "alu", "kernel": "rollout_kernel", "achieved": achieved, "peak": peak,
+        "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+        "flops_per_unit": fpu, "live_units_per_launch": live_per_launch,
+        "units_per_launch": p.L * p.M * p.N * p.H, "launch_ms": roll_ms / roll_n if roll_n else None,
+        "stage_ms_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items() if total_ms},
+    }
+    pk = measured_peaks()
+    if pk:
+        roofline["hbm_peak_gbs_measured"] = pk.get("hbm_gbs")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": p.L, "M": p.M, "N": p.N, "H": p.H, "J_max": p.J_max,
+                   "grid": list(p.grid), "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (wind field 503 MB per solve)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x0.numel() * 8),
+                "d2h_bytes_per_step": int(out_h.numel() * 4 + 8 + 4)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, dt, u = oracle_sample(args.cpu_particles, cores)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one oracle smc_solve of the workload's traffic with L={args.cpu_particles} "
+                       f"particles (full M, N, H, J_max; wind generation included): "
+                       f"{u:.3g} units in {dt:.1f} s")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-particles", type=int, default=128)
+    ap.add_argument("--reference-particles", type=int, default=64)
+    args = ap.parse_args(argv)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * tma_smc.h -- C-ABI of the GB300 (sm_103a) implementation of the data-parallel
+ * hot path of Sequential Monte Carlo optimisation inside Model Predictive
+ * Control for multi-aircraft Terminal Manoeuvring Area trajectories
+ * (Eele & Maciejowski, CUED/F-INFENG/TR.693, 2015).
+ *
+ * Conventions shared by every entry point
+ *   - Units are SI (m, s, kg, N, rad); headings use the mathematical
+ *     convention (0 = +x, counter-clockwise positive).
+ *   - "d_" pointers are device pointers on the current CUDA device, "h_"
+ *     pointers are host pointers.  All device pointers are caller-owned unless
+ *     stated otherwise; the library never frees them.
+ *   - Every launch goes on the caller's stream (`tma_stream_t` is a
+ *     cudaStream_t; NULL is the legacy default stream) and is stream-ordered;
+ *     nothing synchronises unless the entry point writes a host output.
+ *   - The ABI never aborts, throws or prints; it returns a tma_status.  Invalid
+ *     sizes or NULL required pointers give TMA_ERR_INVALID_ARG before any
+ *     launch; a failed CUDA call gives TMA_ERR_CUDA (the CUDA error string is
+ *     available from tma_last_error_string()).
+ *   - Layouts are row-major C arrays:
+ *       controls  u[L][N][S][3] float32, per segment (turn rate w [rad/s],
+ *                 climb rate hdot [m/s], speed change a [m/s^2]), piecewise
+ *                 constant over S equal segments of the horizon;
+ *       costs     cbar[N][L] float32 (aircraft-major, one segment per aircraft);
+ *       weights   wtilde[N][L] float64;  ancestors anc[N][L] int32;
+ *       wind      W[M][H][P][2] float32, P = nx*ny*nz grid nodes, node index
+ *                 (ix*ny + iy)*nz + iz, components (x, y).
+ */
+#ifndef TMA_SMC_H
+#define TMA_SMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tma_stream_t;
+typedef struct tma_solver tma_solver;
+
+typedef enum {
+    TMA_OK = 0,
+    TMA_ERR_INVALID_ARG = 1,
+    TMA_ERR_OOM = 2,
+    TMA_ERR_CUDA = 3,
+    TMA_ERR_BOUNDS = 4,
+    TMA_ERR_TIMEOUT = 5,
+    TMA_WARN_DEGENERATE = 6,   /* a weight segment was all zero; identity ancestors were used */
+    TMA_ERR_UNSUPPORTED = 7
+} tma_status;
+
+/* Limits of this build. */
+#define TMA_MAX_AIRCRAFT 32          /* N: one warp lane per aircraft */
+#define TMA_MAX_PARTICLES (1 << 22)  /* L: keeps the fixed-point CDF products in 128 bits */
+#define TMA_MAX_GRID_Z 16
+
+/* Scenario: the optimal-control problem of Sec. 2 and Sec. 3 (all host values). */
+typedef struct {
+    int32_t N;                /* aircraft (Sec. 2), 1..TMA_MAX_AIRCRAFT */
+    int32_t H;                /* prediction horizon in steps (Sec. 2) */
+    int32_t S;                /* control segments over the horizon */
+    int32_t L;                /* particles (Sec. 3.2), 1..TMA_MAX_PARTICLES */
+    int32_t M;                /* wind samples per particle (Sec. 3.3, inner loop) */
+    int32_t J_max;            /* SMC iterations (Algorithm 1) */
+    double dt;                /* step length delta t [s] (Eq. (hor)) */
+    uint64_t seed;            /* key of every random stream */
+    uint32_t scenario_id;     /* mixed into the key: seed + scenario_id * 0x9E3779B97F4A7C15 */
+    uint32_t mpc_step;        /* receding-horizon step (Sec. 2), part of every counter */
+    double box_lo[3], box_hi[3];  /* wind grid box (x, y, z) */
+    int32_t grid[3];          /* wind grid nodes nx, ny, nz (each >= 2, nz <= 16) */
+    double wind_sigma;        /* std of the forecast error [m/s] (Eq. (cov)) */
+    double turb_sigma;        /* std of white turbulence per step [m/s] */
+    double lam_t;             /* time correlation rate [1/s]: a = exp(-dt*lam_t) */
+    double beta_xy, gam_z;    /* horizontal / vertical correlation rates [1/m] */
+    double sep_h, sep_v;      /* separation minima 2P_r, 2P_h (Eq. (avoidance)) */
+    int32_t sep_mode;         /* 0 hard, 1 softplus, 2 both (weights use hard) */
+    double sp_beta, mu_sep;   /* softplus sharpness and weight */
+    double z_min, z_max, gamma_max, phi_max, v_min, v_max;  /* envelope (Sec. 3.4) */
+    double ctrl_lo[3], ctrl_hi[3];  /* control box (initial uniform draw, clipping) */
+    double move_sigma[3];     /* std of the Gaussian perturbation (Algorithm 1) */
+    double alpha_dep[4];      /* departure weights: bearing, fuel, altitude, speed (Table coeff) */
+    double alpha_arr[3];      /* arrival weights: flow heading, glide path, fuel (Table coeff) */
+    double w_noise, A_c;      /* noise-cost weight and altitude cut-off (Sec. 7.1) */
+    int32_t pop_n[2];         /* population grid nodes (0 = no noise map) */
+    double pop_lo[2], pop_hi[2];
+    const double *popdense;   /* host [pop_n[0]][pop_n[1]]; copied by tma_create */
+    double P_runway, P_beta, P_chi, P_vs, beta_f;  /* landing sector (Eq. (TO_init)), glide angle */
+} tma_problem;
+
+typedef struct {
+    double x, y, z, v, chi, m;   /* X_0 of Sec. 3.3: position, airspeed, heading, mass */
+} tma_state;
+
+typedef struct {
+    int32_t type;             /* 0 arrival, 1 departure */
+    int32_t pad_;
+    tma_state x0;             /* initial state */
+    double theta_F, Z, v_D;   /* departure targets: bearing, altitude, airspeed (Sec. 3.5) */
+    double m_empty;           /* minimum mass m_Aircraft (Sec. 3.4) */
+    double S, CD0, CD2;       /* wing area and drag polar */
+    double Cf1, Cf2;          /* fuel flow eta = Cf1 (1 + v/Cf2) (Sec. 6.2, Eq. (blah)) */
+    double Tmin, Tmax;        /* thrust limits (Sec. 3.4) */
+} tma_aircraft;
+
+const char *tma_status_str(tma_status s);
+/* Text of the last CUDA error seen by this thread's last failing call ("" if none). */
+const char *tma_last_error_string(void);
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t tma_launch_count(void);
+
+/* ---------------------------------------------------------------- solver */
+
+/* Create a solver for one scenario on the current device.  Copies `prob`,
+ * `aircraft[prob->N]` and the population map; factorises the wind covariance
+ * of Eq. (cov) (host FP64 Cholesky of the Kronecker factors, Sec. 3.9.1) and
+ * allocates the device buffers it owns (wind field, controls, costs, weights,
+ * ancestors, scratch).  Errors: TMA_ERR_INVALID_ARG (sizes, limits above),
+ * TMA_ERR_OOM, TMA_ERR_CUDA.  On error *out is NULL. */
+tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma_solver **out);
+void tma_destroy(tma_solver *s);
+
+/* Set the measured states X_0 (host, N entries; NULL keeps the current ones)
+ * and the receding-horizon step (Sec. 2, Fig. 1).  Stream-ordered copy. */
+tma_status tma_set_state(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step,
+                         tma_stream_t stream);
+
+/* Generate the solver's wind field for its current mpc_step (Sec. 3.9.1):
+ * W(0) = Qhat v(0), W(k+1) = a W(k) + Q v(k+1) with Qhat = sigma (L_xy kron L_z),
+ * Q = sqrt(1 - a^2) Qhat.  If d_W is not NULL the field is also copied there
+ * (float32 [M][H][P][2]).  Uses solver-owned scratch. */
+tma_status tma_wind_field(tma_solver *s, float *d_W, tma_stream_t stream);
+
+/* Rollout and costs (Algorithm 1 inner loop; Sec. 3.3-3.6, Sec. 7.1): for every
+ * particle l < L of d_u (u[L][N][S][3]), every wind sample m < M of the
+ * solver's current field and every aircraft, simulate H steps of Eq. (hor)
+ * under wind + turbulence, check constraints (Sec. 3.4), landing (Eq. (TO_init))
+ * and separation (Eq. (avoidance)), and score -ln J_T.  Outputs the sample
+ * means d_cbar[N][L] (+inf when the aircraft violated a constraint in any
+ * sample), and, if d_cbar_soft is not NULL, the softplus-separation variant.
+ * J is the SMC iteration (keys the turbulence stream).  Particle l keys its
+ * streams with index l.  L <= the solver's L.  Uses solver-owned scratch. */
+tma_status tma_rollout_cost(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *d_cbar,
+                            float *d_cbar_soft, tma_stream_t stream);
+
+/* Per-sample costs of the last tma_rollout_cost call: d_out[L][M][N] float32. */
+tma_status tma_sample_costs(tma_solver *s, float *d_out, int64_t L, int soft, tma_stream_t stream);
+
+/* Number of simulated (not frozen) aircraft-steps in the last tma_rollout_cost
+ * call, or summed over all rollouts of the last tma_solve; syncs. */
+tma_status tma_live_steps(tma_solver *s, uint64_t *h_live, tma_stream_t stream);
+
+/* Perturbation (Algorithm 1): d_u_out[l][i] = clip(d_u[d_anc[i][l]][i] + sigma xi)
+ * with xi from random stream 1 of iteration J.  d_u_out must not alias d_u.
+ * Ancestors must lie in [0, L); an out-of-range ancestor is replaced by l. */
+tma_status tma_move(tma_solver *s, const float *d_u, const int32_t *d_anc, int64_t L, int32_t J,
+                    float *d_u_out, tma_stream_t stream);
+
+/* Uniform initial controls (Sec. 3.2) from random stream 4: d_u[L][N][S][3]. */
+tma_status tma_init_controls(tma_solver *s, float *d_u, int64_t L, tma_stream_t stream);
+
+/* One SMC optimisation (Algorithm 1) from the solver's current state: wind
+ * field, uniform initialisation, J_max rollouts with annealed weighting, FP64
+ * normalisation, systematic resampling and perturbation between them, and the
+ * final selection (Sec. 3.8).  Writes the chosen controls d_best_u[N][S][3]
+ * (device, caller-owned, may be NULL) and, if h_best_cost is not NULL, syncs
+ * the stream and writes the chosen particle's cost sum (host).  Returns
+ * TMA_WARN_DEGENERATE when some weight segment was all zero. */
+tma_status tma_solve(tma_solver *s, float *d_best_u, double *h_best_cost, tma_stream_t stream);
+
+/* The same solve through host buffers: copies h_x0[N] in, solves, copies the
+ * chosen controls h_best_u[N][S][3] and their cost out; syncs the stream. */
+tma_status tma_solve_host(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step, float *h_best_u,
+                          double *h_best_cost, tma_stream_t stream);
+
+/* Index of the particle chosen by the last tma_solve (host); syncs. */
+tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
+
+/* Per-stage device time of the solver's launches (CUDA events recorded on the
+ * launching stream around each stage when profiling is on).  Stages:
+ * 0 wind generation, 1 initial controls, 2 rollout, 3 sample means, 4 LSE,
+ * 5 resampling, 6 move, 7 selection.  tma_profile_read synchronises on the
+ * recorded events, adds their durations to the totals and, if reset != 0,
+ * clears the totals after copying them out. */
+typedef struct {
+    double ms[8];
+    uint64_t launches[8];
+} tma_profile;
+tma_status tma_profile_enable(tma_solver *s, int on);
+tma_status tma_profile_read(tma_solver *s, tma_profile *h_out, int reset);
+
+/* ------------------------------------------------------ stateless stages */
+
+/* Annealed log-weights and their FP64 normalisation per segment (Sec. 3.6,
+ * schedule of Sec. 5.1): l_j = -kappa * (double)cbar_j, lmax = max over finite
+ * l_j, d_wtilde[s][j] = exp(l_j - lmax) (0 for +inf cost), d_lmax[s], d_wsum[s]
+ * = sum_j wtilde.  A segment with no finite cost gets lmax = -inf, wtilde = 0.
+ * d_lmax / d_wsum may be NULL.  Scratch: d_work of tma_lse_workspace() bytes. */
+size_t tma_lse_workspace(int32_t nseg, int64_t L);
+tma_status tma_lse(const float *d_cbar, int32_t nseg, int64_t L, double kappa, double *d_wtilde,
+                   double *d_lmax, double *d_wsum, void *d_work, size_t work_bytes,
+                   tma_stream_t stream);
+
+/* Systematic resampling per segment (Sec. 3.7) on a fixed-point CDF:
+ * q_j = floor(wtilde_j 2^40), S = inclusive prefix sum, Q = S_{L-1},
+ * t_l = floor((l 2^32 + r) Q / (L 2^32)), d_anc[s][l] = min{j : S_j > t_l}.
+ * r is word 0 of Philox4x32-10 under key seed + scenario_id*0x9E3779B97F4A7C15
+ * and counter (0, s, 2<<24, J | mpc_step<<16).  A segment with Q = 0 gets
+ * identity ancestors and the call returns TMA_WARN_DEGENERATE.  wtilde must
+ * lie in [0, 1] (values above 1 count as 1, NaN and negatives as 0).
+ * Scratch: d_work of tma_resample_workspace() bytes. */
+size_t tma_resample_workspace(int32_t nseg, int64_t L);
+tma_status tma_resample(const double *d_wtilde, int32_t nseg, int64_t L, uint64_t seed,
+                        uint32_t scenario_id, uint32_t J, uint32_t mpc_step, int32_t *d_anc,
+                        void *d_work, size_t work_bytes, tma_stream_t stream);
+
+/* Final selection (Sec. 3.8): over particles l < L, the fewest aircraft with
+ * infinite cost, then the smallest sum_i (double)cbar[i][l] summed in order
+ * i = 0..N-1, ties to the lowest l.  Writes d_best (int64), d_best_sum (double;
+ * +inf when the chosen particle has an infeasible aircraft), d_ninf (int32).
+ * Scratch: d_work of tma_select_workspace() bytes. */
+size_t tma_select_workspace(int64_t L);
+tma_status tma_select(const float *d_cbar, int32_t N, int64_t L, int64_t *d_best, double *d_best_sum,
+                      int32_t *d_ninf, void *d_work, size_t work_bytes, tma_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMA_SMC_H */

@@ -1,0 +1,447 @@
+"""Python binding of the GB300 SMC-MPC hot path (include/tma_smc.h).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels
+of `_lib/libtma_smc.so`.  Functions carry the names of the C-ABI entry
+points; PyTorch provides device memory and streams.  If the library has not
+been built, every call raises -- there is no CPU fallback.
+
+A problem is any object (or dict) with the fields of `tma_problem` plus an
+`aircraft` record array with the fields type, x, y, z, v, chi, m, theta_F,
+Z, v_D, m_empty, S, CD0, CD2, Cf1, Cf2, Tmin, Tmax.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "_lib", "libtma_smc.so")
+
+TMA_OK, TMA_ERR_INVALID_ARG, TMA_ERR_OOM, TMA_ERR_CUDA = 0, 1, 2, 3
+TMA_ERR_BOUNDS, TMA_ERR_TIMEOUT, TMA_WARN_DEGENERATE, TMA_ERR_UNSUPPORTED = 4, 5, 6, 7
+TMA_MAX_AIRCRAFT = 32
+TMA_MAX_PARTICLES = 1 << 22
+
+EXPORTS = [
+    "tma_status_str", "tma_last_error_string", "tma_launch_count", "tma_create", "tma_destroy",
+    "tma_set_state", "tma_wind_field", "tma_rollout_cost", "tma_sample_costs", "tma_live_steps",
+    "tma_move", "tma_init_controls", "tma_solve", "tma_solve_host", "tma_best_index",
+    "tma_lse_workspace", "tma_lse", "tma_resample_workspace", "tma_resample",
+    "tma_select_workspace", "tma_select", "tma_profile_enable", "tma_profile_read",
+]
+
+
+class TmaError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{msg}: status {status} ({_status_str(status)})")
+        self.status = status
+
+
+class TmaProblem(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("H", C.c_int32), ("S", C.c_int32), ("L", C.c_int32), ("M", C.c_int32),
+        ("J_max", C.c_int32), ("dt", C.c_double), ("seed", C.c_uint64),
+        ("scenario_id", C.c_uint32), ("mpc_step", C.c_uint32),
+        ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3), ("grid", C.c_int32 * 3),
+        ("wind_sigma", C.c_double), ("turb_sigma", C.c_double), ("lam_t", C.c_double),
+        ("beta_xy", C.c_double), ("gam_z", C.c_double), ("sep_h", C.c_double),
+        ("sep_v", C.c_double), ("sep_mode", C.c_int32), ("sp_beta", C.c_double),
+        ("mu_sep", C.c_double), ("z_min", C.c_double), ("z_max", C.c_double),
+        ("gamma_max", C.c_double), ("phi_max", C.c_double), ("v_min", C.c_double),
+        ("v_max", C.c_double), ("ctrl_lo", C.c_double * 3), ("ctrl_hi", C.c_double * 3),
+        ("move_sigma", C.c_double * 3), ("alpha_dep", C.c_double * 4),
+        ("alpha_arr", C.c_double * 3), ("w_noise", C.c_double), ("A_c", C.c_double),
+        ("pop_n", C.c_int32 * 2), ("pop_lo", C.c_double * 2), ("pop_hi", C.c_double * 2),
+        ("popdense", C.POINTER(C.c_double)), ("P_runway", C.c_double), ("P_beta", C.c_double),
+        ("P_chi", C.c_double), ("P_vs", C.c_double), ("beta_f", C.c_double),
+    ]
+
+
+class TmaState(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("x", "y", "z", "v", "chi", "m")]
+
+
+class TmaProfile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_uint64 * 8)]
+
+
+STAGES = ("wind", "init", "rollout", "sample_mean", "lse", "resample", "move", "select")
+
+
+class TmaAircraft(C.Structure):
+    _fields_ = [("type", C.c_int32), ("pad_", C.c_int32), ("x0", TmaState)] + [
+        (n, C.c_double) for n in ("theta_F", "Z", "v_D", "m_empty", "S", "CD0", "CD2", "Cf1",
+                                  "Cf2", "Tmin", "Tmax")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force=False, verbose=False):
+    """Compile the CUDA library for sm_103a (in-tree)."""
+    from . import buildlib as _b
+    return _b.build(force=force, verbose=verbose)
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIBPATH):
+                raise RuntimeError(f"CUDA library not built ({LIBPATH}); run build() first")
+            L = C.CDLL(LIBPATH)
+            P, vp, st = C.POINTER, C.c_void_p, C.c_void_p
+            i32, i64, u32, u64, d, sz = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double, C.c_size_t
+            sig = {
+                "tma_status_str": ([C.c_int], C.c_char_p),
+                "tma_last_error_string": ([], C.c_char_p),
+                "tma_launch_count": ([], u64),
+                "tma_create": ([P(TmaProblem), P(TmaAircraft), P(vp)], C.c_int),
+                "tma_destroy": ([vp], None),
+                "tma_set_state": ([vp, P(TmaState), u32, st], C.c_int),
+                "tma_wind_field": ([vp, vp, st], C.c_int),
+                "tma_rollout_cost": ([vp, vp, i64, i32, vp, vp, st], C.c_int),
+                "tma_sample_costs": ([vp, vp, i64, C.c_int, st], C.c_int),
+                "tma_live_steps": ([vp, P(u64), st], C.c_int),
+                "tma_move": ([vp, vp, vp, i64, i32, vp, st], C.c_int),
+                "tma_init_controls": ([vp, vp, i64, st], C.c_int),
+                "tma_solve": ([vp, vp, P(d), st], C.c_int),
+                "tma_solve_host": ([vp, P(TmaState), u32, vp, P(d), st], C.c_int),
+                "tma_best_index": ([vp, P(i64), st], C.c_int),
+                "tma_lse_workspace": ([i32, i64], sz),
+                "tma_lse": ([vp, i32, i64, d, vp, vp, vp, vp, sz, st], C.c_int),
+                "tma_resample_workspace": ([i32, i64], sz),
+                "tma_resample": ([vp, i32, i64, u64, u32, u32, u32, vp, vp, sz, st], C.c_int),
+                "tma_select_workspace": ([i64], sz),
+                "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
+                "tma_profile_enable": ([vp, C.c_int], C.c_int),
+                "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _status_str(s):
+    try:
+        return lib().tma_status_str(s).decode()
+    except Exception:
+        return "?"
+
+
+def _check(status, what, allow=(TMA_OK,)):
+    if status not in allow:
+        extra = ""
+        if status == TMA_ERR_CUDA:
+            extra = " / " + lib().tma_last_error_string().decode()
+        raise TmaError(status, what + extra)
+    return status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _get(p, name, default=None):
+    if isinstance(p, dict):
+        return p.get(name, default)
+    return getattr(p, name, default)
+
+
+def problem_struct(p):
+    """Marshal a problem object into (TmaProblem, TmaAircraft[N], keep-alive)."""
+    s = TmaProblem()
+    for n in ("N", "H", "S", "L", "M", "J_max"):
+        setattr(s, n, int(_get(p, n)))
+    s.dt = float(_get(p, "dt"))
+    s.seed = int(_get(p, "seed")) & 0xFFFFFFFFFFFFFFFF
+    s.scenario_id = int(_get(p, "scenario_id", 0))
+    s.mpc_step = int(_get(p, "mpc_step", 0))
+    s.box_lo[:] = [float(v) for v in _get(p, "box_lo")]
+    s.box_hi[:] = [float(v) for v in _get(p, "box_hi")]
+    s.grid[:] = [int(v) for v in _get(p, "grid")]
+    for n in ("wind_sigma", "turb_sigma", "lam_t", "beta_xy", "gam_z", "sep_h", "sep_v",
+              "sp_beta", "mu_sep", "z_min", "z_max", "gamma_max", "phi_max", "v_min", "v_max",
+              "w_noise", "A_c", "P_runway", "P_beta", "P_chi", "P_vs", "beta_f"):
+        setattr(s, n, float(_get(p, n)))
+    s.sep_mode = int(_get(p, "sep_mode"))
+    s.ctrl_lo[:] = [float(v) for v in _get(p, "ctrl_lo")]
+    s.ctrl_hi[:] = [float(v) for v in _get(p, "ctrl_hi")]
+    s.move_sigma[:] = [float(v) for v in _get(p, "move_sigma")]
+    s.alpha_dep[:] = [float(v) for v in _get(p, "alpha_dep")]
+    s.alpha_arr[:] = [float(v) for v in _get(p, "alpha_arr")]
+    keep = []
+    pd = _get(p, "popdense")
+    if pd is not None:
+        pd = np.ascontiguousarray(pd, np.float64)
+        keep.append(pd)
+        s.pop_n[:] = list(pd.shape)
+        s.pop_lo[:] = [float(v) for v in _get(p, "pop_lo")]
+        s.pop_hi[:] = [float(v) for v in _get(p, "pop_hi")]
+        s.popdense = pd.ctypes.data_as(C.POINTER(C.c_double))
+    ac = _get(p, "aircraft")
+    arr = (TmaAircraft * s.N)()
+    for i in range(s.N):
+        r = ac[i]
+        a = arr[i]
+        a.type = int(r["type"])
+        for n in ("x", "y", "z", "v", "chi", "m"):
+            setattr(a.x0, n, float(r[n]))
+        for n in ("theta_F", "Z", "v_D", "m_empty", "S", "CD0", "CD2", "Cf1", "Cf2", "Tmin", "Tmax"):
+            setattr(a, n, float(r[n]))
+    return s, arr, keep
+
+
+def states_struct(x0):
+    """x0: array-like [N][6] (x, y, z, v, chi, m) -> TmaState[N]."""
+    x0 = np.asarray(x0, np.float64).reshape(-1, 6)
+    arr = (TmaState * len(x0))()
+    for i, r in enumerate(x0):
+        arr[i].x, arr[i].y, arr[i].z, arr[i].v, arr[i].chi, arr[i].m = (float(v) for v in r)
+    return arr
+
+
+# ---------------------------------------------------------------- solver
+
+def tma_create(problem):
+    """Create a solver on the current CUDA device; returns an opaque handle."""
+    s, arr, keep = problem_struct(problem)
+    h = C.c_void_p()
+    _check(lib().tma_create(C.byref(s), arr, C.byref(h)), "tma_create")
+    return h
+
+
+def tma_destroy(h):
+    if h:
+        lib().tma_destroy(h)
+
+
+def tma_set_state(h, x0=None, mpc_step=0, stream=None):
+    arr = states_struct(x0) if x0 is not None else None
+    _check(lib().tma_set_state(h, arr, int(mpc_step), _stream(stream)), "tma_set_state")
+
+
+def tma_wind_field(h, out=None, stream=None):
+    _check(lib().tma_wind_field(h, _dptr(out), _stream(stream)), "tma_wind_field")
+    return out
+
+
+def tma_rollout_cost(h, u, J, cbar, cbar_soft=None, stream=None):
+    """u: cuda float32 [L][N][S][3]; writes cbar (and cbar_soft) [N][L]."""
+    L = u.shape[0]
+    _check(lib().tma_rollout_cost(h, _dptr(u), L, int(J), _dptr(cbar), _dptr(cbar_soft),
+                                  _stream(stream)), "tma_rollout_cost")
+
+
+def tma_sample_costs(h, out, soft=False, stream=None):
+    _check(lib().tma_sample_costs(h, _dptr(out), out.shape[0], int(soft), _stream(stream)),
+           "tma_sample_costs")
+
+
+def tma_live_steps(h, stream=None):
+    v = C.c_uint64()
+    _check(lib().tma_live_steps(h, C.byref(v), _stream(stream)), "tma_live_steps")
+    return v.value
+
+
+def tma_move(h, u, anc, J, u_out, stream=None):
+    _check(lib().tma_move(h, _dptr(u), _dptr(anc), u.shape[0], int(J), _dptr(u_out),
+                          _stream(stream)), "tma_move")
+
+
+def tma_init_controls(h, u, stream=None):
+    _check(lib().tma_init_controls(h, _dptr(u), u.shape[0], _stream(stream)), "tma_init_controls")
+
+
+def tma_solve(h, best_u=None, stream=None, want_cost=True):
+    """One SMC solve; returns (status, best cost or None)."""
+    c = C.c_double()
+    st = lib().tma_solve(h, _dptr(best_u), C.byref(c) if want_cost else None, _stream(stream))
+    _check(st, "tma_solve", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+    return st, (c.value if want_cost else None)
+
+
+def tma_solve_host(h, x0, mpc_step, best_u_host, stream=None):
+    """Solve through host buffers; best_u_host: float32 numpy [N][S][3] (written)."""
+    assert best_u_host.dtype == np.float32 and best_u_host.flags.c_contiguous
+    c = C.c_double()
+    arr = states_struct(x0)
+    st = lib().tma_solve_host(h, arr, int(mpc_step), best_u_host.ctypes.data_as(C.c_void_p),
+                              C.byref(c), _stream(stream))
+    _check(st, "tma_solve_host", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+    return st, c.value
+
+
+def tma_best_index(h, stream=None):
+    v = C.c_int64()
+    _check(lib().tma_best_index(h, C.byref(v), _stream(stream)), "tma_best_index")
+    return v.value
+
+
+def tma_profile_enable(h, on=True):
+    _check(lib().tma_profile_enable(h, int(bool(on))), "tma_profile_enable")
+
+
+def tma_profile_read(h, reset=True):
+    """Per-stage device time {stage: (ms, launches)} since the last reset."""
+    prof = TmaProfile()
+    _check(lib().tma_profile_read(h, C.byref(prof), int(bool(reset))), "tma_profile_read")
+    return {name: (prof.ms[k], prof.launches[k]) for k, name in enumerate(STAGES)}
+
+
+# --------------------------------------------------------- stateless stages
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def tma_lse(cbar, kappa, wtilde, lmax=None, wsum=None, work=None, stream=None):
+    """cbar: cuda float32 [nseg][L] -> wtilde float64 [nseg][L] (+ lmax, wsum [nseg])."""
+    nseg, L = cbar.shape
+    need = lib().tma_lse_workspace(nseg, L)
+    if work is None:
+        work = _workspace(need, cbar.device)
+    _check(lib().tma_lse(_dptr(cbar), nseg, L, float(kappa), _dptr(wtilde), _dptr(lmax),
+                         _dptr(wsum), _dptr(work), work.numel(), _stream(stream)), "tma_lse")
+
+
+def tma_resample(wtilde, seed, scenario_id, J, mpc_step, anc, work=None, stream=None):
+    """wtilde: cuda float64 [nseg][L] -> anc int32 [nseg][L]; returns the status
+    (TMA_WARN_DEGENERATE when a segment was all zero)."""
+    nseg, L = wtilde.shape
+    need = lib().tma_resample_workspace(nseg, L)
+    if work is None:
+        work = _workspace(need, wtilde.device)
+    return _check(lib().tma_resample(_dptr(wtilde), nseg, L, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                     int(scenario_id), int(J), int(mpc_step), _dptr(anc),
+                                     _dptr(work), work.numel(), _stream(stream)),
+                  "tma_resample", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+
+
+def tma_select(cbar, best, best_sum=None, ninf=None, work=None, stream=None):
+    """cbar: cuda float32 [N][L] -> best int64 [1], best_sum float64 [1], ninf int32 [1]."""
+    N, L = cbar.shape
+    need = lib().tma_select_workspace(L)
+    if work is None:
+        work = _workspace(need, cbar.device)
+    _check(lib().tma_select(_dptr(cbar), N, L, _dptr(best), _dptr(best_sum), _dptr(ninf),
+                            _dptr(work), work.numel(), _stream(stream)), "tma_select")
+
+
+# ------------------------------------------------------------ convenience
+
+class Solver:
+    """Owns a tma_solver handle and allocates outputs with torch."""
+
+    def __init__(self, problem, device=None):
+        torch = _torch()
+        self.problem = problem
+        self.N, self.S, self.L, self.M, self.H = (int(_get(problem, n)) for n in ("N", "S", "L", "M", "H"))
+        self.sep_mode = int(_get(problem, "sep_mode"))
+        self.grid = tuple(int(v) for v in _get(problem, "grid"))
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.h = tma_create(problem)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tma_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_state(self, x0=None, mpc_step=0):
+        tma_set_state(self.h, x0, mpc_step)
+
+    def wind_field(self):
+        torch = _torch()
+        P = self.grid[0] * self.grid[1] * self.grid[2]
+        out = torch.empty((self.M, self.H, P, 2), dtype=torch.float32, device=self.device)
+        tma_wind_field(self.h, out)
+        return out
+
+    def rollout_cost(self, u, J, soft=False):
+        torch = _torch()
+        L = u.shape[0]
+        cbar = torch.empty((self.N, L), dtype=torch.float32, device=self.device)
+        cs = torch.empty_like(cbar) if soft else None
+        tma_rollout_cost(self.h, u, J, cbar, cs)
+        return cbar, cs
+
+    def sample_costs(self, L, soft=False):
+        torch = _torch()
+        out = torch.empty((L, self.M, self.N), dtype=torch.float32, device=self.device)
+        tma_sample_costs(self.h, out, soft)
+        return out
+
+    def live_steps(self):
+        return tma_live_steps(self.h)
+
+    def move(self, u, anc, J):
+        torch = _torch()
+        out = torch.empty_like(u)
+        tma_move(self.h, u, anc, J, out)
+        return out
+
+    def init_controls(self, L=None):
+        torch = _torch()
+        L = self.L if L is None else L
+        u = torch.empty((L, self.N, self.S, 3), dtype=torch.float32, device=self.device)
+        tma_init_controls(self.h, u)
+        return u
+
+    def solve(self):
+        torch = _torch()
+        best_u = torch.empty((self.N, self.S, 3), dtype=torch.float32, device=self.device)
+        st, cost = tma_solve(self.h, best_u)
+        return best_u, cost, st
+
+    def best_index(self):
+        return tma_best_index(self.h)
+
+
+def lse(cbar, kappa):
+    torch = _torch()
+    nseg, L = cbar.shape
+    wt = torch.empty((nseg, L), dtype=torch.float64, device=cbar.device)
+    lm = torch.empty(nseg, dtype=torch.float64, device=cbar.device)
+    ws = torch.empty(nseg, dtype=torch.float64, device=cbar.device)
+    tma_lse(cbar, kappa, wt, lm, ws)
+    return wt, lm, ws
+
+
+def resample(wtilde, seed, scenario_id, J, mpc_step):
+    torch = _torch()
+    anc = torch.empty(wtilde.shape, dtype=torch.int32, device=wtilde.device)
+    st = tma_resample(wtilde, seed, scenario_id, J, mpc_step, anc)
+    return anc, st
+
+
+def select(cbar):
+    torch = _torch()
+    dev = cbar.device
+    best = torch.empty(1, dtype=torch.int64, device=dev)
+    bs = torch.empty(1, dtype=torch.float64, device=dev)
+    ni = torch.empty(1, dtype=torch.int32, device=dev)
+    tma_select(cbar, best, bs, ni)
+    return int(best.item()), float(bs.item()), int(ni.item())

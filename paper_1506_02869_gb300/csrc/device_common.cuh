@@ -1,0 +1,84 @@
+// Device utilities of the CUDA path: counter-based random numbers and
+// compensated accumulation.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tma {
+
+// Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 bit
+// multiplies with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Counter layout of every random stream: (c0, c1, q | stream << 24, J | mpc << 16).
+__device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                      uint32_t q, uint32_t stream, uint32_t J, uint32_t mpc)
+{
+    return philox4x32_10(make_uint4(c0, c1, (q & 0xFFFFFFu) | (stream << 24),
+                                    (J & 0xFFFFu) | (mpc << 16)),
+                         k0, k1);
+}
+
+// Uniform in (0, 1) from the top 23 bits: ((x >> 9) + 1/2) / 2^23, exact in FP32.
+__device__ __forceinline__ float uniform23(uint32_t x)
+{
+    return __fmaf_rn((float)(x >> 9), 1.0f / 8388608.0f, 1.0f / 16777216.0f);
+}
+
+// Box-Muller transform of two words into two independent standard normals.
+__device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb)
+{
+    const float r = sqrtf(-2.0f * logf(uniform23(xa)));
+    float s, c;
+    sincospif(2.0f * uniform23(xb), &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// Kahan-compensated FP32 accumulator.
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float y)
+    {
+        const float yy = y - c;
+        const float t = s + yy;
+        c = (t - s) - yy;
+        s = t;
+    }
+};
+
+// Absolute angular distance of an angle difference, in [0, pi].
+__device__ __forceinline__ float angdist(float a)
+{
+    const float twopi = 6.28318530717958647692f;
+    const float r = a - twopi * rintf(a * (1.0f / twopi));
+    return fabsf(r);
+}
+
+// 128-bit unsigned product and comparison helpers (fixed-point CDF).
+struct U128 {
+    unsigned long long hi, lo;
+};
+__device__ __forceinline__ U128 mul64x64(unsigned long long a, unsigned long long b)
+{
+    return U128{__umul64hi(a, b), a * b};
+}
+__device__ __forceinline__ bool lt128(U128 a, U128 b)
+{
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+}  // namespace tma

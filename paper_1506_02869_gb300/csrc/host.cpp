@@ -1,0 +1,827 @@
+// Host runtime of the CUDA path: scenario validation, derived constants, the
+// FP64 Cholesky factors of the wind covariance, the solver object and every
+// entry point of include/tma_smc.h.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tma_internal.h"
+
+namespace tma {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+static thread_local std::string g_last_error;
+
+static tma_status cuda_fail(cudaError_t e)
+{
+    g_last_error = cudaGetErrorString(e);
+    return TMA_ERR_CUDA;
+}
+
+#define TMA_CUDA(expr)                             \
+    do {                                           \
+        cudaError_t e_ = (expr);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+// ------------------------------------------------------------------ Cholesky
+
+// Right-looking blocked Cholesky, lower triangle, row-major; the panel solve
+// and the trailing update are split over threads by rows.
+bool cholesky_lower(std::vector<double> &A, int n)
+{
+    const int NB = 64;
+    unsigned hw = std::thread::hardware_concurrency();
+    const int nth = (int)std::max(1u, std::min(hw ? hw : 1u, 32u));
+    auto at = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+    auto parallel_rows = [&](int r0, int r1, auto &&fn) {
+        const int rows = r1 - r0;
+        if (rows <= 0) return;
+        const int T = std::min(nth, std::max(1, rows / 16));
+        if (T == 1) {
+            for (int i = r0; i < r1; ++i) fn(i);
+            return;
+        }
+        std::vector<std::thread> th;
+        for (int t = 0; t < T; ++t)
+            th.emplace_back([&, t]() {
+                for (int i = r0 + t; i < r1; i += T) fn(i);
+            });
+        for (auto &x : th) x.join();
+    };
+    bool ok = true;
+    for (int kb = 0; kb < n && ok; kb += NB) {
+        const int ke = std::min(n, kb + NB);
+        for (int j = kb; j < ke; ++j) {
+            double d = at(j, j);
+            for (int t = kb; t < j; ++t) d -= at(j, t) * at(j, t);
+            if (!(d > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double ljj = std::sqrt(d);
+            at(j, j) = ljj;
+            for (int i = j + 1; i < ke; ++i) {
+                double s = at(i, j);
+                for (int t = kb; t < j; ++t) s -= at(i, t) * at(j, t);
+                at(i, j) = s / ljj;
+            }
+        }
+        if (!ok) break;
+        parallel_rows(ke, n, [&](int i) {
+            for (int j = kb; j < ke; ++j) {
+                double s = at(i, j);
+                for (int t = kb; t < j; ++t) s -= at(i, t) * at(j, t);
+                at(i, j) = s / at(j, j);
+            }
+        });
+        parallel_rows(ke, n, [&](int i) {
+            const double *ri = &A[(size_t)i * n + kb];
+            for (int j = ke; j <= i; ++j) {
+                const double *rj = &A[(size_t)j * n + kb];
+                double s = 0.0;
+                for (int t = 0; t < ke - kb; ++t) s += ri[t] * rj[t];
+                at(i, j) -= s;
+            }
+        });
+    }
+    if (!ok) return false;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) at(i, j) = 0.0;
+    return true;
+}
+
+// Horizontal factor L_xy (FP32, zero-padded) cached per grid and rate.
+struct LxyEntry {
+    std::vector<float> L;
+    int lda;
+};
+static std::mutex g_lxy_mu;
+static std::map<std::string, std::shared_ptr<LxyEntry>> g_lxy;
+
+static std::shared_ptr<LxyEntry> horizontal_factor(const tma_problem &p)
+{
+    char key[256];
+    snprintf(key, sizeof key, "%d %d %.17g %.17g %.17g %.17g %.17g", p.grid[0], p.grid[1],
+             p.box_lo[0], p.box_hi[0], p.box_lo[1], p.box_hi[1], p.beta_xy);
+    {
+        std::lock_guard<std::mutex> g(g_lxy_mu);
+        auto it = g_lxy.find(key);
+        if (it != g_lxy.end()) return it->second;
+    }
+    const int nx = p.grid[0], ny = p.grid[1], n = nx * ny;
+    std::vector<double> xs(nx), ys(ny);
+    for (int i = 0; i < nx; ++i) xs[i] = p.box_lo[0] + (p.box_hi[0] - p.box_lo[0]) * i / (nx - 1);
+    for (int i = 0; i < ny; ++i) ys[i] = p.box_lo[1] + (p.box_hi[1] - p.box_lo[1]) * i / (ny - 1);
+    std::vector<double> R((size_t)n * n);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b <= a; ++b) {
+            const double dx = xs[a / ny] - xs[b / ny], dy = ys[a % ny] - ys[b % ny];
+            R[(size_t)a * n + b] = std::exp(-p.beta_xy * std::sqrt(dx * dx + dy * dy));
+        }
+    if (!cholesky_lower(R, n)) return nullptr;
+    auto e = std::make_shared<LxyEntry>();
+    e->lda = ((n + 127) / 128) * 128;
+    e->L.assign((size_t)e->lda * e->lda, 0.0f);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b <= a; ++b) e->L[(size_t)a * e->lda + b] = (float)R[(size_t)a * n + b];
+    std::lock_guard<std::mutex> g(g_lxy_mu);
+    g_lxy[key] = e;
+    return e;
+}
+
+static int next_pow2(int n)
+{
+    int g = 1;
+    while (g < n) g <<= 1;
+    return g;
+}
+
+static bool finite(double x) { return std::isfinite(x); }
+
+static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
+{
+    if (!p || !ac) return TMA_ERR_INVALID_ARG;
+    if (p->N < 1 || p->N > TMA_MAX_AIRCRAFT || p->H < 1 || p->S < 1 || p->S > p->H ||
+        p->L < 1 || p->L > TMA_MAX_PARTICLES || p->M < 1 || p->M >= (1 << 24) ||
+        p->J_max < 1 || p->J_max > 0xFFFF || p->H > (1 << 25) || p->mpc_step > 0xFFFF)
+        return TMA_ERR_INVALID_ARG;
+    if (!(p->dt > 0) || !finite(p->dt)) return TMA_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (p->grid[d] < 2 || !(p->box_hi[d] > p->box_lo[d])) return TMA_ERR_INVALID_ARG;
+    if (p->grid[2] > TMA_MAX_GRID_Z) return TMA_ERR_INVALID_ARG;
+    if ((long long)p->grid[0] * p->grid[1] > 16384) return TMA_ERR_INVALID_ARG;
+    if (!(p->sep_h > 0) || !(p->sep_v > 0) || p->sep_mode < 0 || p->sep_mode > 2)
+        return TMA_ERR_INVALID_ARG;
+    if (!(p->lam_t >= 0) || !(p->wind_sigma >= 0) || !(p->turb_sigma >= 0)) return TMA_ERR_INVALID_ARG;
+    if (!(p->gamma_max > 0 && p->gamma_max < M_PI / 2) || !(p->phi_max > 0 && p->phi_max < M_PI / 2))
+        return TMA_ERR_INVALID_ARG;
+    if (!(p->v_max > p->v_min) || !(p->v_min > 0)) return TMA_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c)
+        if (!(p->ctrl_hi[c] >= p->ctrl_lo[c])) return TMA_ERR_INVALID_ARG;
+    if (p->w_noise != 0.0 && !(p->A_c > 0)) return TMA_ERR_INVALID_ARG;
+    if (p->pop_n[0] != 0 || p->pop_n[1] != 0) {
+        if (p->pop_n[0] < 2 || p->pop_n[1] < 2 || !p->popdense || !(p->pop_hi[0] > p->pop_lo[0]) ||
+            !(p->pop_hi[1] > p->pop_lo[1]))
+            return TMA_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < p->N; ++i) {
+        const tma_aircraft &a = ac[i];
+        if (a.type != 0 && a.type != 1) return TMA_ERR_INVALID_ARG;
+        if (!(a.x0.v > 0) || !(a.x0.m > 0) || !(a.S > 0) || !(a.Cf1 > 0) || !(a.Cf2 > 0) ||
+            !(a.Tmax > 0))
+            return TMA_ERR_INVALID_ARG;
+    }
+    return TMA_OK;
+}
+
+static void derive(tma_solver *s)
+{
+    const tma_problem &p = s->prob;
+    ProblemC &P = s->P;
+    std::memset(&P, 0, sizeof P);
+    P.N = p.N;
+    P.H = p.H;
+    P.S = p.S;
+    P.M = p.M;
+    P.G = next_pow2(p.N);
+    P.P = p.grid[0] * p.grid[1] * p.grid[2];
+    for (int d = 0; d < 3; ++d) {
+        P.grid[d] = p.grid[d];
+        P.box_lo[d] = (float)p.box_lo[d];
+        P.box_hi[d] = (float)p.box_hi[d];
+        P.inv_h[d] = (float)((p.grid[d] - 1) / (p.box_hi[d] - p.box_lo[d]));
+    }
+    P.dt = (float)p.dt;
+    P.turb_sigma = (float)p.turb_sigma;
+    P.sgmax = (float)std::sin(p.gamma_max);
+    P.tpmax = (float)std::tan(p.phi_max);
+    P.Sh2 = (float)(p.sep_h * p.sep_h);
+    P.Sh_inv = (float)(1.0 / p.sep_h);
+    P.Sv = (float)p.sep_v;
+    P.Sv_inv = (float)(1.0 / p.sep_v);
+    P.sep_mode = p.sep_mode;
+    P.sp_beta = (float)p.sp_beta;
+    P.sp_inv_beta = (float)(p.sp_beta != 0 ? 1.0 / p.sp_beta : 0.0);
+    P.mu_sep = (float)p.mu_sep;
+    P.z_min = (float)p.z_min;
+    P.z_max = (float)p.z_max;
+    P.v_min = (float)p.v_min;
+    P.v_max = (float)p.v_max;
+    for (int j = 0; j < 4; ++j) P.a_dep[j] = (float)p.alpha_dep[j];
+    for (int j = 0; j < 3; ++j) P.a_arr[j] = (float)p.alpha_arr[j];
+    P.w_noise = (float)p.w_noise;
+    P.Ac_inv = (float)(p.A_c > 0 ? 1.0 / p.A_c : 0.0);
+    P.popdense = s->d_popdense;
+    for (int d = 0; d < 2; ++d) {
+        P.pop_n[d] = p.pop_n[d];
+        P.pop_lo[d] = (float)p.pop_lo[d];
+        P.pop_hi[d] = (float)p.pop_hi[d];
+        P.pop_inv_h[d] = p.pop_n[d] >= 2 ? (float)((p.pop_n[d] - 1) / (p.pop_hi[d] - p.pop_lo[d])) : 0.f;
+    }
+    P.P_runway = (float)p.P_runway;
+    P.P_beta = (float)p.P_beta;
+    P.P_chi = (float)p.P_chi;
+    P.P_vs = (float)p.P_vs;
+    P.beta_f = (float)p.beta_f;
+    const uint64_t key = p.seed + (uint64_t)p.scenario_id * 0x9E3779B97F4A7C15ull;
+    P.key0 = (uint32_t)key;
+    P.key1 = (uint32_t)(key >> 32);
+    const double sgmax = std::sin(p.gamma_max);
+    for (int i = 0; i < p.N; ++i) {
+        const tma_aircraft &a = s->aircraft[i];
+        AircraftC &c = P.ac[i];
+        c.type = a.type;
+        c.halfS = (float)(0.5 * a.S);
+        c.CD0 = (float)a.CD0;
+        c.CD2 = (float)a.CD2;
+        c.Cf1 = (float)a.Cf1;
+        c.invCf2 = (float)(1.0 / a.Cf2);
+        c.Tmin = (float)a.Tmin;
+        c.Tmax = (float)a.Tmax;
+        c.m_empty = (float)a.m_empty;
+        c.thF = (float)a.theta_F;
+        c.Z = (float)a.Z;
+        c.vD = (float)a.v_D;
+        const double Fmax = p.H * p.dt * a.Tmax * a.Cf1 * (1.0 + p.v_max / a.Cf2);
+        c.invFmax = (float)(1.0 / Fmax);
+        // departure altitude term: per-step means of d0 +/- k dt vmax sin(gamma_max)
+        const double d0 = std::fabs(a.Z - a.x0.z), cl = p.v_max * sgmax * p.dt;
+        double sup = 0.0, inf = 0.0;
+        for (int k = 1; k <= p.H; ++k) {
+            sup += d0 + k * cl;
+            inf += std::max(d0 - k * cl, 0.0);
+        }
+        sup /= p.H;
+        inf /= p.H;
+        c.supB = (float)sup;
+        c.invSupInf = (float)(1.0 / (sup - inf));
+        c.invCmax = (float)(1.0 / std::max(p.v_max - a.v_D, a.v_D - p.v_min));
+    }
+}
+
+static void upload_x0(tma_solver *s, DynState &d)
+{
+    std::memset(&d, 0, sizeof d);
+    for (int i = 0; i < s->prob.N; ++i) {
+        const tma_state &x = s->aircraft[i].x0;
+        d.x0[i][0] = (float)x.x;
+        d.x0[i][1] = (float)x.y;
+        d.x0[i][2] = (float)x.z;
+        d.x0[i][3] = (float)x.v;
+        d.x0[i][4] = (float)x.chi;
+        d.x0[i][5] = (float)x.m;
+    }
+    d.mpc_step = s->mpc_step;
+}
+
+static void free_all(tma_solver *s)
+{
+    void *ptrs[] = {s->d_dyn, s->d_Lxy, s->d_Btmp, s->d_W, s->d_u[0], s->d_u[1], s->d_cost_ms,
+                    s->d_cost_ms_soft, s->d_cbar, s->d_cbar_soft, s->d_wtilde, s->d_anc,
+                    s->d_popdense, s->d_work, s->d_best, s->d_best_sum, s->d_ninf, s->d_flags,
+                    s->d_live, s->d_best_u};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+static cudaError_t alloc(T **p, size_t bytes)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes > 0 ? bytes : 16);
+}
+
+// Static (FP32) copies of the control box and move sigma.
+static void ctrl_f(const tma_problem &p, float lo[3], float hi[3], float sg[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = (float)p.ctrl_lo[c];
+        hi[c] = (float)p.ctrl_hi[c];
+        sg[c] = (float)p.move_sigma[c];
+    }
+}
+
+// Optional CUDA-event timing of one stage on the launching stream.
+struct StageTimer {
+    tma_solver *s;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    static cudaEvent_t take(tma_solver *s)
+    {
+        if (!s->event_pool.empty()) {
+            cudaEvent_t e = s->event_pool.back();
+            s->event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    StageTimer(tma_solver *s_, int stage_, cudaStream_t st_) : s(s_), stage(stage_), st(st_)
+    {
+        if (s->prof && (a = take(s)) != nullptr) cudaEventRecord(a, st);
+    }
+    void done()
+    {
+        if (!a) return;
+        cudaEvent_t b = take(s);
+        if (!b) return;
+        cudaEventRecord(b, st);
+        s->pending.push_back({stage, a, b});
+        a = nullptr;
+    }
+    ~StageTimer() { done(); }
+};
+
+static int kappa_of(int J) { return (int)std::floor(3.0 + 5.0 * std::exp(0.05 * J)); }
+
+// device address of DynState::mpc_step (pointer arithmetic only)
+static const uint32_t *dyn_mpc(const tma_solver *s)
+{
+    return reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(s->d_dyn) +
+                                              offsetof(DynState, mpc_step));
+}
+
+}  // namespace tma
+
+using namespace tma;
+
+extern "C" {
+
+const char *tma_status_str(tma_status s)
+{
+    switch (s) {
+    case TMA_OK: return "ok";
+    case TMA_ERR_INVALID_ARG: return "invalid argument";
+    case TMA_ERR_OOM: return "out of memory";
+    case TMA_ERR_CUDA: return "CUDA error";
+    case TMA_ERR_BOUNDS: return "index out of bounds";
+    case TMA_ERR_TIMEOUT: return "timeout";
+    case TMA_WARN_DEGENERATE: return "degenerate weights (identity resampling used)";
+    case TMA_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *tma_last_error_string(void) { return g_last_error.c_str(); }
+
+uint64_t tma_launch_count(void) { return g_launches.load(); }
+
+tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma_solver **out)
+{
+    if (!out) return TMA_ERR_INVALID_ARG;
+    *out = nullptr;
+    tma_status v = validate(prob, aircraft);
+    if (v != TMA_OK) return v;
+    tma_solver *s = nullptr;
+    try {
+        s = new tma_solver();
+        s->prob = *prob;
+        s->aircraft.assign(aircraft, aircraft + prob->N);
+        if (prob->pop_n[0] >= 2) {
+            s->popdense_host.assign(prob->popdense,
+                                    prob->popdense + (size_t)prob->pop_n[0] * prob->pop_n[1]);
+        }
+        s->prob.popdense = nullptr;
+        s->mpc_step = prob->mpc_step;
+        cudaGetDevice(&s->device);
+        const tma_problem &p = s->prob;
+        const size_t L = (size_t)p.L, N = (size_t)p.N, M = (size_t)p.M, H = (size_t)p.H;
+        const int nx = p.grid[0], ny = p.grid[1], nz = p.grid[2];
+        const int nxy = nx * ny;
+        const size_t P = (size_t)nxy * nz;
+        auto fail = [&](cudaError_t e) {
+            free_all(s);
+            delete s;
+            return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : cuda_fail(e);
+        };
+        cudaError_t e;
+        // popdense to device (FP32)
+        if (!s->popdense_host.empty()) {
+            std::vector<float> pf(s->popdense_host.begin(), s->popdense_host.end());
+            if ((e = alloc(&s->d_popdense, pf.size() * 4))) return fail(e);
+            if ((e = cudaMemcpy(s->d_popdense, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice)))
+                return fail(e);
+        }
+        derive(s);
+        // wind factors
+        auto lxy = horizontal_factor(p);
+        if (!lxy) {
+            free_all(s);
+            delete s;
+            return TMA_ERR_INVALID_ARG;
+        }
+        std::vector<double> Rz((size_t)nz * nz);
+        for (int a = 0; a < nz; ++a)
+            for (int b = 0; b <= a; ++b) {
+                const double za = p.box_lo[2] + (p.box_hi[2] - p.box_lo[2]) * a / (nz - 1);
+                const double zb = p.box_lo[2] + (p.box_hi[2] - p.box_lo[2]) * b / (nz - 1);
+                Rz[(size_t)a * nz + b] = std::exp(-p.gam_z * std::fabs(za - zb));
+            }
+        if (!cholesky_lower(Rz, nz)) {
+            free_all(s);
+            delete s;
+            return TMA_ERR_INVALID_ARG;
+        }
+        WindC &w = s->wind;
+        std::memset(&w, 0, sizeof w);
+        w.M = p.M;
+        w.H = p.H;
+        w.nxy = nxy;
+        w.nz = nz;
+        w.ncol = (int)(M * H * 2 * nz);
+        w.ldb = ((w.ncol + 127) / 128) * 128;
+        const double a = std::exp(-p.dt * p.lam_t);
+        w.a = (float)a;
+        w.b = (float)std::sqrt(std::max(0.0, 1.0 - a * a));
+        w.sigma = (float)p.wind_sigma;
+        for (int r = 0; r < nz; ++r)
+            for (int c = 0; c <= r; ++c) w.Lz[r * TMA_MAX_GRID_Z + c] = (float)Rz[(size_t)r * nz + c];
+        w.key0 = s->P.key0;
+        w.key1 = s->P.key1;
+        s->lda = lxy->lda;
+        if ((e = alloc(&s->d_Lxy, lxy->L.size() * 4))) return fail(e);
+        if ((e = cudaMemcpy(s->d_Lxy, lxy->L.data(), lxy->L.size() * 4, cudaMemcpyHostToDevice)))
+            return fail(e);
+        const size_t brows = (size_t)s->lda;
+        if ((e = alloc(&s->d_Btmp, brows * w.ldb * 4))) return fail(e);
+        if ((e = cudaMemset(s->d_Btmp, 0, brows * w.ldb * 4))) return fail(e);
+        if ((e = alloc(&s->d_W, M * H * P * 2 * 4))) return fail(e);
+        const size_t ubytes = L * N * p.S * 3 * 4;
+        if ((e = alloc(&s->d_u[0], ubytes))) return fail(e);
+        if ((e = alloc(&s->d_u[1], ubytes))) return fail(e);
+        if ((e = alloc(&s->d_cost_ms, L * M * N * 4))) return fail(e);
+        if (p.sep_mode != 0 && (e = alloc(&s->d_cost_ms_soft, L * M * N * 4))) return fail(e);
+        if ((e = alloc(&s->d_cbar, L * N * 4))) return fail(e);
+        if (p.sep_mode != 0 && (e = alloc(&s->d_cbar_soft, L * N * 4))) return fail(e);
+        if ((e = alloc(&s->d_wtilde, L * N * 8))) return fail(e);
+        if ((e = alloc(&s->d_anc, L * N * 4))) return fail(e);
+        s->work_bytes = std::max({lse_workspace(p.N, p.L), resample_workspace(p.N, p.L),
+                                  select_workspace(p.L)});
+        if ((e = alloc(&s->d_work, s->work_bytes))) return fail(e);
+        if ((e = alloc(&s->d_best, 8))) return fail(e);
+        if ((e = alloc(&s->d_best_sum, 8))) return fail(e);
+        if ((e = alloc(&s->d_ninf, 4))) return fail(e);
+        if ((e = alloc(&s->d_flags, 4))) return fail(e);
+        if ((e = alloc(&s->d_live, 8))) return fail(e);
+        if ((e = alloc(&s->d_best_u, N * p.S * 3 * 4))) return fail(e);
+        if ((e = alloc(&s->d_dyn, sizeof(DynState)))) return fail(e);
+        DynState d;
+        upload_x0(s, d);
+        if ((e = cudaMemcpy(s->d_dyn, &d, sizeof d, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaMemset(s->d_flags, 0, 4))) return fail(e);
+        if ((e = cudaMemset(s->d_live, 0, 8))) return fail(e);
+    } catch (const std::bad_alloc &) {
+        if (s) {
+            free_all(s);
+            delete s;
+        }
+        return TMA_ERR_OOM;
+    }
+    *out = s;
+    return TMA_OK;
+}
+
+static void release_events(tma_solver *s)
+{
+    for (auto &p : s->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    s->pending.clear();
+    for (auto e : s->event_pool) cudaEventDestroy(e);
+    s->event_pool.clear();
+}
+
+void tma_destroy(tma_solver *s)
+{
+    if (!s) return;
+    release_events(s);
+    free_all(s);
+    delete s;
+}
+
+tma_status tma_profile_enable(tma_solver *s, int on)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    s->prof = on != 0;
+    return TMA_OK;
+}
+
+tma_status tma_profile_read(tma_solver *s, tma_profile *h_out, int reset)
+{
+    if (!s || !h_out) return TMA_ERR_INVALID_ARG;
+    for (auto &p : s->pending) {
+        TMA_CUDA(cudaEventSynchronize(p.b));
+        float ms = 0.0f;
+        TMA_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        s->prof_ms[p.stage] += ms;
+        s->prof_n[p.stage] += 1;
+        s->event_pool.push_back(p.a);
+        s->event_pool.push_back(p.b);
+    }
+    s->pending.clear();
+    for (int k = 0; k < 8; ++k) {
+        h_out->ms[k] = s->prof_ms[k];
+        h_out->launches[k] = s->prof_n[k];
+        if (reset) {
+            s->prof_ms[k] = 0.0;
+            s->prof_n[k] = 0;
+        }
+    }
+    return TMA_OK;
+}
+
+tma_status tma_set_state(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step, tma_stream_t stream)
+{
+    if (!s || mpc_step > 0xFFFF) return TMA_ERR_INVALID_ARG;
+    if (h_x0) {
+        for (int i = 0; i < s->prob.N; ++i)
+            if (!(h_x0[i].v > 0) || !(h_x0[i].m > 0)) return TMA_ERR_INVALID_ARG;
+        for (int i = 0; i < s->prob.N; ++i) s->aircraft[i].x0 = h_x0[i];
+        derive(s);   // departure altitude normalisation depends on the initial altitude
+    }
+    s->mpc_step = mpc_step;
+    // a pageable-memory copy would be unsafe to reuse before it runs; stage it
+    // through a per-call host buffer that the stream finishes before return
+    DynState d;
+    upload_x0(s, d);
+    TMA_CUDA(cudaMemcpyAsync(s->d_dyn, &d, sizeof d, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    s->wind_ready = false;
+    return TMA_OK;
+}
+
+static tma_status gen_wind(tma_solver *s, cudaStream_t st)
+{
+    StageTimer t(s, 0, st);
+    TMA_CUDA(launch_wind_normals_ar(s->wind, s->d_dyn, s->d_Btmp, st));
+    TMA_CUDA(launch_wind_gemm(s->wind, s->d_Lxy, s->lda, s->d_Btmp, s->d_W, st));
+    s->wind_ready = true;
+    return TMA_OK;
+}
+
+tma_status tma_wind_field(tma_solver *s, float *d_W, tma_stream_t stream)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    tma_status r = gen_wind(s, st);
+    if (r != TMA_OK) return r;
+    if (d_W) {
+        const size_t n = (size_t)s->prob.M * s->prob.H * s->P.P * 2;
+        TMA_CUDA(cudaMemcpyAsync(d_W, s->d_W, n * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    return TMA_OK;
+}
+
+static tma_status rollout_into(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *cbar,
+                               float *cbar_soft, cudaStream_t st, bool reset_live)
+{
+    if (!s->wind_ready) {
+        tma_status r = gen_wind(s, st);
+        if (r != TMA_OK) return r;
+    }
+    const bool soft = cbar_soft != nullptr;
+    if (reset_live) TMA_CUDA(cudaMemsetAsync(s->d_live, 0, 8, st));
+    {
+        StageTimer t(s, 2, st);
+        TMA_CUDA(launch_rollout(s->P, s->d_dyn, d_u, s->d_W, L, J, s->d_cost_ms,
+                                soft ? s->d_cost_ms_soft : nullptr, s->d_live, st));
+    }
+    {
+        StageTimer t(s, 3, st);
+        TMA_CUDA(launch_sample_mean(s->d_cost_ms, L, s->prob.M, s->prob.N, cbar, st));
+        if (soft)
+            TMA_CUDA(launch_sample_mean(s->d_cost_ms_soft, L, s->prob.M, s->prob.N, cbar_soft, st));
+    }
+    s->last_L = L;
+    return TMA_OK;
+}
+
+tma_status tma_rollout_cost(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *d_cbar,
+                            float *d_cbar_soft, tma_stream_t stream)
+{
+    if (!s || !d_u || !d_cbar || L < 0 || L > s->prob.L || J < 0 || J > 0xFFFF)
+        return TMA_ERR_INVALID_ARG;
+    if (d_cbar_soft && s->prob.sep_mode == 0) return TMA_ERR_INVALID_ARG;
+    return rollout_into(s, d_u, L, J, d_cbar, d_cbar_soft, (cudaStream_t)stream, true);
+}
+
+tma_status tma_sample_costs(tma_solver *s, float *d_out, int64_t L, int soft, tma_stream_t stream)
+{
+    if (!s || !d_out || L < 0 || L > s->last_L) return TMA_ERR_INVALID_ARG;
+    const float *src = soft ? s->d_cost_ms_soft : s->d_cost_ms;
+    if (!src) return TMA_ERR_INVALID_ARG;
+    TMA_CUDA(cudaMemcpyAsync(d_out, src, (size_t)L * s->prob.M * s->prob.N * 4,
+                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return TMA_OK;
+}
+
+tma_status tma_live_steps(tma_solver *s, uint64_t *h_live, tma_stream_t stream)
+{
+    if (!s || !h_live) return TMA_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    TMA_CUDA(cudaMemcpyAsync(&v, s->d_live, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    *h_live = v;
+    return TMA_OK;
+}
+
+tma_status tma_move(tma_solver *s, const float *d_u, const int32_t *d_anc, int64_t L, int32_t J,
+                    float *d_u_out, tma_stream_t stream)
+{
+    if (!s || !d_u || !d_anc || !d_u_out || d_u == d_u_out || L < 0 || L > s->prob.L || J < 0 ||
+        J > 0xFFFF)
+        return TMA_ERR_INVALID_ARG;
+    float lo[3], hi[3], sg[3];
+    ctrl_f(s->prob, lo, hi, sg);
+    TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, sg, d_u, d_anc, L, J, d_u_out, (cudaStream_t)stream));
+    return TMA_OK;
+}
+
+tma_status tma_init_controls(tma_solver *s, float *d_u, int64_t L, tma_stream_t stream)
+{
+    if (!s || !d_u || L < 0 || L > s->prob.L) return TMA_ERR_INVALID_ARG;
+    float lo[3], hi[3], sg[3];
+    ctrl_f(s->prob, lo, hi, sg);
+    TMA_CUDA(launch_init_controls(s->P, s->d_dyn, lo, hi, d_u, L, (cudaStream_t)stream));
+    return TMA_OK;
+}
+
+static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
+{
+    const tma_problem &p = s->prob;
+    float lo[3], hi[3], sg[3];
+    ctrl_f(p, lo, hi, sg);
+    tma_status r = gen_wind(s, st);
+    if (r != TMA_OK) return r;
+    TMA_CUDA(cudaMemsetAsync(s->d_flags, 0, 4, st));
+    TMA_CUDA(cudaMemsetAsync(s->d_live, 0, 8, st));
+    {
+        StageTimer t(s, 1, st);
+        TMA_CUDA(launch_init_controls(s->P, s->d_dyn, lo, hi, s->d_u[0], p.L, st));
+    }
+    int cur = 0;
+    const bool use_soft = p.sep_mode == 1;
+    float *cb = use_soft ? s->d_cbar_soft : s->d_cbar;
+    for (int J = 0; J < p.J_max; ++J) {
+        r = rollout_into(s, s->d_u[cur], p.L, J, s->d_cbar, p.sep_mode != 0 ? s->d_cbar_soft : nullptr,
+                         st, false);
+        if (r != TMA_OK) return r;
+        if (J < p.J_max - 1) {
+            {
+                StageTimer t(s, 4, st);
+                TMA_CUDA(launch_lse(cb, p.N, p.L, (double)kappa_of(J), s->d_wtilde, nullptr, nullptr,
+                                    s->d_work, st));
+            }
+            {
+                StageTimer t(s, 5, st);
+                TMA_CUDA(launch_resample(s->d_wtilde, p.N, p.L, s->P.key0, s->P.key1, (uint32_t)J,
+                                         dyn_mpc(s), 0u, s->d_anc, s->d_work, s->d_flags, st));
+            }
+            {
+                StageTimer t(s, 6, st);
+                TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, sg, s->d_u[cur], s->d_anc, p.L, J,
+                                     s->d_u[cur ^ 1], st));
+            }
+            cur ^= 1;
+        }
+    }
+    s->cur_u = cur;
+    {
+        StageTimer t(s, 7, st);
+        TMA_CUDA(launch_select(cb, p.N, p.L, s->d_best, s->d_best_sum, s->d_ninf, s->d_work, st));
+        TMA_CUDA(launch_gather_best(s->d_u[cur], s->d_best, p.N * p.S * 3, s->d_best_u, st));
+    }
+    (void)degenerate;
+    return TMA_OK;
+}
+
+tma_status tma_solve(tma_solver *s, float *d_best_u, double *h_best_cost, tma_stream_t stream)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool deg = false;
+    tma_status r = solve_device(s, st, &deg);
+    if (r != TMA_OK) return r;
+    if (d_best_u)
+        TMA_CUDA(cudaMemcpyAsync(d_best_u, s->d_best_u, (size_t)s->prob.N * s->prob.S * 3 * 4,
+                                 cudaMemcpyDeviceToDevice, st));
+    if (h_best_cost) {
+        unsigned int flags = 0;
+        TMA_CUDA(cudaMemcpyAsync(h_best_cost, s->d_best_sum, 8, cudaMemcpyDeviceToHost, st));
+        TMA_CUDA(cudaMemcpyAsync(&flags, s->d_flags, 4, cudaMemcpyDeviceToHost, st));
+        TMA_CUDA(cudaStreamSynchronize(st));
+        if (flags & 1u) return TMA_WARN_DEGENERATE;
+    }
+    return TMA_OK;
+}
+
+tma_status tma_solve_host(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step, float *h_best_u,
+                          double *h_best_cost, tma_stream_t stream)
+{
+    if (!s || !h_best_u) return TMA_ERR_INVALID_ARG;
+    tma_status r = tma_set_state(s, h_x0, mpc_step, stream);
+    if (r != TMA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool deg = false;
+    r = solve_device(s, st, &deg);
+    if (r != TMA_OK) return r;
+    unsigned int flags = 0;
+    double cost = 0.0;
+    TMA_CUDA(cudaMemcpyAsync(h_best_u, s->d_best_u, (size_t)s->prob.N * s->prob.S * 3 * 4,
+                             cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaMemcpyAsync(&cost, s->d_best_sum, 8, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaMemcpyAsync(&flags, s->d_flags, 4, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    if (h_best_cost) *h_best_cost = cost;
+    return (flags & 1u) ? TMA_WARN_DEGENERATE : TMA_OK;
+}
+
+tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream)
+{
+    if (!s || !h_best) return TMA_ERR_INVALID_ARG;
+    TMA_CUDA(cudaMemcpyAsync(h_best, s->d_best, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return TMA_OK;
+}
+
+size_t tma_lse_workspace(int32_t nseg, int64_t L)
+{
+    return (nseg < 0 || L < 0) ? 0 : lse_workspace(nseg, L);
+}
+
+tma_status tma_lse(const float *d_cbar, int32_t nseg, int64_t L, double kappa, double *d_wtilde,
+                   double *d_lmax, double *d_wsum, void *d_work, size_t work_bytes, tma_stream_t stream)
+{
+    if (nseg < 0 || L < 0 || L > TMA_MAX_PARTICLES || !(kappa > 0) || !std::isfinite(kappa))
+        return TMA_ERR_INVALID_ARG;
+    if (nseg == 0 || L == 0) {
+        if (nseg > 0 && (d_lmax || d_wsum)) {
+            std::vector<double> lm(nseg, -INFINITY), ws(nseg, 0.0);
+            if (d_lmax) TMA_CUDA(cudaMemcpyAsync(d_lmax, lm.data(), nseg * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+            if (d_wsum) TMA_CUDA(cudaMemcpyAsync(d_wsum, ws.data(), nseg * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+            TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        }
+        return TMA_OK;
+    }
+    if (!d_cbar || !d_wtilde || !d_work || work_bytes < lse_workspace(nseg, L)) return TMA_ERR_INVALID_ARG;
+    TMA_CUDA(launch_lse(d_cbar, nseg, L, kappa, d_wtilde, d_lmax, d_wsum, d_work, (cudaStream_t)stream));
+    return TMA_OK;
+}
+
+size_t tma_resample_workspace(int32_t nseg, int64_t L)
+{
+    return (nseg < 0 || L < 0) ? 0 : resample_workspace(nseg, L) + 16;
+}
+
+tma_status tma_resample(const double *d_wtilde, int32_t nseg, int64_t L, uint64_t seed,
+                        uint32_t scenario_id, uint32_t J, uint32_t mpc_step, int32_t *d_anc,
+                        void *d_work, size_t work_bytes, tma_stream_t stream)
+{
+    if (nseg < 0 || L < 0 || L > TMA_MAX_PARTICLES || J > 0xFFFF || mpc_step > 0xFFFF)
+        return TMA_ERR_INVALID_ARG;
+    if (nseg == 0 || L == 0) return TMA_OK;
+    if (!d_wtilde || !d_anc || !d_work || work_bytes < tma_resample_workspace(nseg, L))
+        return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t key = seed + (uint64_t)scenario_id * 0x9E3779B97F4A7C15ull;
+    // the last 16 bytes of the workspace hold the degenerate flag
+    char *base = reinterpret_cast<char *>(d_work);
+    const size_t rw = resample_workspace(nseg, L);
+    unsigned int *flags = reinterpret_cast<unsigned int *>(
+        (reinterpret_cast<uintptr_t>(base + rw) + 3) & ~uintptr_t(3));
+    TMA_CUDA(cudaMemsetAsync(flags, 0, 4, st));
+    TMA_CUDA(launch_resample(d_wtilde, nseg, L, (uint32_t)key, (uint32_t)(key >> 32), J, nullptr,
+                             mpc_step, d_anc, d_work, flags, st));
+    unsigned int h = 0;
+    TMA_CUDA(cudaMemcpyAsync(&h, flags, 4, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    return (h & 1u) ? TMA_WARN_DEGENERATE : TMA_OK;
+}
+
+size_t tma_select_workspace(int64_t L) { return L < 0 ? 0 : select_workspace(L); }
+
+tma_status tma_select(const float *d_cbar, int32_t N, int64_t L, int64_t *d_best, double *d_best_sum,
+                      int32_t *d_ninf, void *d_work, size_t work_bytes, tma_stream_t stream)
+{
+    if (N < 1 || L < 1 || !d_cbar || !d_best || !d_work || work_bytes < select_workspace(L))
+        return TMA_ERR_INVALID_ARG;
+    TMA_CUDA(launch_select(d_cbar, N, L, d_best, d_best_sum, d_ninf, d_work, (cudaStream_t)stream));
+    return TMA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Perturbation of the resampled controls (Algorithm 1) and their uniform
+// initialisation (Sec. 3.2).
+//
+// One thread per (particle l, aircraft i), aircraft fastest, so that a warp
+// writes a contiguous run of u_out[l][i][S*3].  The parent record
+// u[anc[i][l]][i] is gathered with 16-byte loads (S*3 = 12 floats = 3 x float4
+// when S = 4); the Gaussian noise comes from random stream 1.
+#include "device_common.cuh"
+#include "tma_internal.h"
+
+namespace tma {
+
+namespace {
+
+struct MoveC {
+    int N, nc;             // nc = S*3 controls per (particle, aircraft)
+    float lo[3], hi[3], sigma[3];
+    uint32_t key0, key1;
+};
+
+__device__ __forceinline__ float clip(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+template <bool kVec>
+__global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState *__restrict__ dyn,
+                                                   const float *__restrict__ u,
+                                                   const int32_t *__restrict__ anc, long long L,
+                                                   int J, float *__restrict__ u_out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L * C.N) return;
+    const long long l = t / C.N;
+    const int i = (int)(t - l * C.N);
+    int a = __ldg(anc + (size_t)i * L + l);
+    if ((unsigned long long)a >= (unsigned long long)L) a = (int)l;   // out-of-range ancestor: keep own record
+    const uint32_t mpc = dyn ? dyn->mpc_step : 0u;
+    const float *src = u + ((size_t)a * C.N + i) * C.nc;
+    float *dst = u_out + ((size_t)l * C.N + i) * C.nc;
+    const int nq = (C.nc + 3) / 4;
+    for (int q = 0; q < nq; ++q) {
+        const uint4 r = draw(C.key0, C.key1, (uint32_t)l, (uint32_t)i, (uint32_t)q, 1u, (uint32_t)J, mpc);
+        const float2 z01 = box_muller(r.x, r.y), z23 = box_muller(r.z, r.w);
+        const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+        if (kVec) {
+            const float4 p = __ldg(reinterpret_cast<const float4 *>(src) + q);
+            const float pv[4] = {p.x, p.y, p.z, p.w};
+            float ov[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = (4 * q + e) % 3;
+                ov[e] = clip(fmaf(C.sigma[c], z[e], pv[e]), C.lo[c], C.hi[c]);
+            }
+            reinterpret_cast<float4 *>(dst)[q] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int n = 4 * q + e;
+                if (n < C.nc) {
+                    const int c = n % 3;
+                    dst[n] = clip(fmaf(C.sigma[c], z[e], __ldg(src + n)), C.lo[c], C.hi[c]);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) init_kernel(const MoveC C, const DynState *__restrict__ dyn,
+                                                   long long L, float *__restrict__ u)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L * C.N) return;
+    const long long l = t / C.N;
+    const int i = (int)(t - l * C.N);
+    const uint32_t mpc = dyn ? dyn->mpc_step : 0u;
+    float *dst = u + ((size_t)l * C.N + i) * C.nc;
+    const int nq = (C.nc + 3) / 4;
+    for (int q = 0; q < nq; ++q) {
+        const uint4 r = draw(C.key0, C.key1, (uint32_t)l, (uint32_t)i, (uint32_t)q, 4u, 0u, mpc);
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int n = 4 * q + e;
+            if (n < C.nc) {
+                const int c = n % 3;
+                dst[n] = fmaf(C.hi[c] - C.lo[c], uniform23(w[e]), C.lo[c]);
+            }
+        }
+    }
+}
+
+MoveC make_move(const ProblemC &P, const float lo[3], const float hi[3], const float sigma[3])
+{
+    MoveC C;
+    C.N = P.N;
+    C.nc = P.S * 3;
+    for (int c = 0; c < 3; ++c) {
+        C.lo[c] = lo[c];
+        C.hi[c] = hi[c];
+        C.sigma[c] = sigma ? sigma[c] : 0.0f;
+    }
+    C.key0 = P.key0;
+    C.key1 = P.key1;
+    return C;
+}
+
+}  // namespace
+
+cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
+                        const float ctrl_hi[3], const float sigma[3], const float *u,
+                        const int32_t *anc, int64_t L, int J, float *u_out, cudaStream_t st)
+{
+    if (L <= 0) return cudaSuccess;
+    const MoveC C = make_move(P, ctrl_lo, ctrl_hi, sigma);
+    const long long n = (long long)L * P.N;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, J, u_out);
+    else move_kernel<false><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, J, u_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_controls(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
+                                 const float ctrl_hi[3], float *u, int64_t L, cudaStream_t st)
+{
+    if (L <= 0) return cudaSuccess;
+    const MoveC C = make_move(P, ctrl_lo, ctrl_hi, nullptr);
+    const long long n = (long long)L * P.N;
+    init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(C, dyn, L, u);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tma

@@ -1,0 +1,312 @@
+// Annealed weights, FP64 normalisation (Sec. 3.6, schedule of Sec. 5.1) and
+// systematic resampling on a fixed-point CDF (Sec. 3.7).
+//
+// Each segment (one aircraft of one scenario) of length L is cut into chunks
+// of kChunk particles; one 256-thread block handles one (chunk, segment).
+//
+//   LSE:      (1) chunk minima of the finite costs; (2) every block reduces its
+//             segment's minima to lmax = -kappa * min c (exact: multiplying by
+//             kappa > 0 is monotone), writes wtilde = exp(-kappa c - lmax) in
+//             FP64 and a chunk partial sum; (3) the partial sums are added in
+//             chunk order into wsum.
+//   Resample: (1) chunk sums of q = floor(wtilde 2^40) (uint64, exact);
+//             (2) every block forms its chunk's inclusive prefix S_j in shared
+//             memory, finds the range of particles l whose threshold
+//             t_l = floor((l 2^32 + r) Q / (L 2^32)) falls in the chunk, and
+//             assigns a_l = min{j : S_j > t_l} by binary search.  Because
+//             S_j > floor(y) <=> S_j > y for integer S_j, both searches compare
+//             128-bit products S_j * L 2^32 against (l 2^32 + r) * Q and need no
+//             division.  Integer arithmetic makes the result independent of the
+//             summation order.
+#include <cfloat>
+
+#include "device_common.cuh"
+#include "tma_internal.h"
+
+namespace tma {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPer = 8;
+constexpr int kChunk = kThreads * kPer;  // 2048
+
+__device__ __forceinline__ unsigned long long qfix(double w)
+{
+    // q = floor(w 2^40) for w in (0, 1); >= 1 counts as 1; NaN and <= 0 as 0
+    if (w >= 1.0) return 1ull << 40;
+    if (w > 0.0) return (unsigned long long)(w * 1099511627776.0);
+    return 0ull;
+}
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : sh[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) sh[0] = v;
+    }
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+struct MinOp {
+    __device__ float operator()(float a, float b) const { return fminf(a, b); }
+};
+struct AddU64 {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const
+    {
+        return a + b;
+    }
+};
+
+__global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restrict__ cbar, long long L,
+                                                          int nchunk, float *__restrict__ cmin)
+{
+    __shared__ float sh[32];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const float *row = cbar + (size_t)s * L;
+    const long long base = (long long)c * kChunk;
+    float mn = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const long long idx = base + threadIdx.x + j * kThreads;
+        if (idx < L) {
+            const float v = __ldg(row + idx);
+            if (v < mn) mn = v;             // +inf and NaN never lower the minimum
+        }
+    }
+    mn = block_reduce(mn, MinOp(), sh);
+    if (threadIdx.x == 0) cmin[(size_t)s * nchunk + c] = mn;
+}
+
+__global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cbar, long long L,
+                                                    int nchunk, double kappa,
+                                                    const float *__restrict__ cmin,
+                                                    double *__restrict__ wtilde,
+                                                    double *__restrict__ csum)
+{
+    __shared__ float shf[32];
+    const int s = blockIdx.y, c = blockIdx.x;
+    float mn = __int_as_float(0x7f800000);
+    for (int j = threadIdx.x; j < nchunk; j += kThreads) mn = fminf(mn, cmin[(size_t)s * nchunk + j]);
+    mn = block_reduce(mn, MinOp(), shf);
+    const bool any = !isinf(mn);
+    const double lmax = -kappa * (double)mn;
+    const float *row = cbar + (size_t)s * L;
+    double *out = wtilde + (size_t)s * L;
+    const long long base = (long long)c * kChunk;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const long long idx = base + threadIdx.x + j * kThreads;
+        if (idx < L) {
+            const float v = __ldg(row + idx);
+            double w = 0.0;
+            if (any && !isinf(v) && !isnan(v)) w = exp(-kappa * (double)v - lmax);
+            out[idx] = w;
+            acc += w;
+        }
+    }
+    // fixed-order block sum: per-thread partials through shared memory
+    __shared__ double part[kThreads];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) csum[(size_t)s * nchunk + c] = part[0];
+}
+
+__global__ void lse_finish(const float *__restrict__ cmin, const double *__restrict__ csum, int nseg,
+                           int nchunk, double kappa, double *__restrict__ lmax,
+                           double *__restrict__ wsum)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    float mn = __int_as_float(0x7f800000);
+    double sum = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+        mn = fminf(mn, cmin[(size_t)s * nchunk + c]);
+        sum += csum[(size_t)s * nchunk + c];
+    }
+    if (lmax) lmax[s] = isinf(mn) ? -__longlong_as_double(0x7ff0000000000000ll) : -kappa * (double)mn;
+    if (wsum) wsum[s] = sum;
+}
+
+__global__ void __launch_bounds__(kThreads) res_chunk_sum(const double *__restrict__ wtilde,
+                                                          long long L, int nchunk,
+                                                          unsigned long long *__restrict__ cq)
+{
+    __shared__ unsigned long long sh[32];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const double *row = wtilde + (size_t)s * L;
+    const long long base = (long long)c * kChunk;
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const long long idx = base + threadIdx.x + j * kThreads;
+        if (idx < L) acc += qfix(__ldg(row + idx));
+    }
+    acc = block_reduce(acc, AddU64(), sh);
+    if (threadIdx.x == 0) cq[(size_t)s * nchunk + c] = acc;
+}
+
+// number of particles l in [0, L) with (l 2^32 + r) Q < X D, D = L 2^32
+__device__ long long count_below(unsigned long long X, unsigned long long Q, unsigned long long D,
+                                 uint32_t r, long long L)
+{
+    const U128 rhs = mul64x64(X, D);
+    long long lo = 0, hi = L;  // answer in [lo, hi]
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        const U128 lhs = mul64x64(((unsigned long long)mid << 32) + r, Q);
+        if (lt128(lhs, rhs)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict__ wtilde, long long L,
+                                                       int nchunk,
+                                                       const unsigned long long *__restrict__ cq,
+                                                       uint32_t key0, uint32_t key1, uint32_t J,
+                                                       const uint32_t *__restrict__ d_mpc,
+                                                       uint32_t mpc_host, int32_t *__restrict__ anc,
+                                                       unsigned int *__restrict__ flags)
+{
+    __shared__ unsigned long long Ssm[kChunk];
+    __shared__ unsigned long long wtot[kThreads / 32];
+    __shared__ unsigned long long sh[32];
+    __shared__ long long range[2];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const long long base = (long long)c * kChunk;
+    const int len = (int)min((long long)kChunk, L - base);
+
+    // offset of this chunk and the segment total (integer, order-free)
+    unsigned long long before = 0, total = 0;
+    for (int j = threadIdx.x; j < nchunk; j += kThreads) {
+        const unsigned long long v = cq[(size_t)s * nchunk + j];
+        total += v;
+        if (j < c) before += v;
+    }
+    before = block_reduce(before, AddU64(), sh);
+    total = block_reduce(total, AddU64(), sh);
+    int32_t *a = anc + (size_t)s * L;
+
+    if (total == 0) {
+        // degenerate segment: identity ancestors
+        for (int j = threadIdx.x; j < len; j += kThreads) a[base + j] = (int32_t)(base + j);
+        if (c == 0 && threadIdx.x == 0 && flags) atomicOr(flags, 1u);
+        return;
+    }
+
+    // inclusive prefix of q over the chunk: load, per-thread serial scan of kPer
+    // consecutive values, warp scan of thread totals, block scan of warp totals
+    const double *row = wtilde + (size_t)s * L;
+    for (int j = threadIdx.x; j < kChunk; j += kThreads)
+        Ssm[j] = j < len ? qfix(__ldg(row + base + j)) : 0ull;
+    __syncthreads();
+    unsigned long long run = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        run += Ssm[threadIdx.x * kPer + j];
+        Ssm[threadIdx.x * kPer + j] = run;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    unsigned long long woff = 0;
+    for (int w = 0; w < wid; ++w) woff += wtot[w];
+    const unsigned long long add = before + woff + (incl - run);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) Ssm[threadIdx.x * kPer + j] += add;
+    __syncthreads();
+
+    const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
+    const uint32_t r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
+    const unsigned long long D = (unsigned long long)L << 32;
+    if (threadIdx.x == 0) range[0] = count_below(before, total, D, r, L);
+    if (threadIdx.x == 32) range[1] = count_below(Ssm[len - 1], total, D, r, L);
+    __syncthreads();
+    const long long lo = range[0], hi = range[1];
+    for (long long l = lo + threadIdx.x; l < hi; l += kThreads) {
+        const U128 target = mul64x64(((unsigned long long)l << 32) + r, total);
+        int jlo = 0, jhi = len - 1;  // smallest j with S_j * D > target
+        while (jlo < jhi) {
+            const int mid = (jlo + jhi) >> 1;
+            if (lt128(target, mul64x64(Ssm[mid], D))) jhi = mid;
+            else jlo = mid + 1;
+        }
+        a[l] = (int32_t)(base + jlo);
+    }
+}
+
+}  // namespace
+
+static int n_chunks(int64_t L) { return (int)((L + kChunk - 1) / kChunk); }
+
+size_t lse_workspace(int nseg, int64_t L)
+{
+    const size_t n = (size_t)nseg * (size_t)n_chunks(L);
+    return n * sizeof(float) + 16 + n * sizeof(double) + 16;
+}
+
+size_t resample_workspace(int nseg, int64_t L)
+{
+    return (size_t)nseg * (size_t)n_chunks(L) * sizeof(unsigned long long) + 16;
+}
+
+cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, double *wtilde,
+                       double *lmax, double *wsum, void *work, cudaStream_t st)
+{
+    if (nseg <= 0 || L <= 0) return cudaSuccess;
+    const int nc = n_chunks(L);
+    const size_t n = (size_t)nseg * nc;
+    float *cmin = reinterpret_cast<float *>(work);
+    double *csum = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(cmin + n) + 15) & ~uintptr_t(15));
+    dim3 grid(nc, nseg);
+    lse_chunk_min<<<grid, kThreads, 0, st>>>(cbar, L, nc, cmin);
+    lse_exp<<<grid, kThreads, 0, st>>>(cbar, L, nc, kappa, cmin, wtilde, csum);
+    count_launch(2);
+    if (lmax || wsum) {
+        lse_finish<<<(nseg + 127) / 128, 128, 0, st>>>(cmin, csum, nseg, nc, kappa, lmax, wsum);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t key0,
+                            uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
+                            int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st)
+{
+    if (nseg <= 0 || L <= 0) return cudaSuccess;
+    const int nc = n_chunks(L);
+    auto *cq = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(work) + 15) & ~uintptr_t(15));
+    dim3 grid(nc, nseg);
+    res_chunk_sum<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq);
+    res_expand<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq, key0, key1, J, d_mpc, mpc_host, anc,
+                                          d_flags);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+}  // namespace tma

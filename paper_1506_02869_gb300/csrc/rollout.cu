@@ -1,0 +1,299 @@
+// Particle-parallel rollout and costing: the inner loop of Algorithm 1
+// (Sec. 3.3-3.6, Sec. 7.1) for every (particle, wind sample, aircraft).
+//
+// Thread mapping: a group of G = next_pow2(N) consecutive lanes simulates one
+// (particle l, wind sample m); lane i is aircraft i and keeps its state
+// (position, airspeed, heading, fuel burned) and cost accumulators in
+// registers for the whole horizon.  The pairwise separation check of
+// Eq. (avoidance) at every step exchanges positions inside the group with
+// G-1 shuffle rotations.  Groups are ordered with the wind sample fastest, so
+// a warp reads one particle's controls (broadcast) and 32/G wind fields.
+#include "device_common.cuh"
+#include "tma_internal.h"
+
+namespace tma {
+
+namespace {
+
+constexpr float kG0 = 9.80665f;
+constexpr float kPi = 3.14159265358979323846f;
+
+// Trilinear interpolation of one wind field Wk[P] (float2 per node) at a
+// position clamped into the grid box (Sec. 3.9.1).
+__device__ __forceinline__ float2 wind_at(const ProblemC &P, const float2 *__restrict__ Wk,
+                                          float x, float y, float z)
+{
+    const float pos[3] = {x, y, z};
+    int idx[3];
+    float t[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float c = fminf(fmaxf(pos[d], P.box_lo[d]), P.box_hi[d]);
+        const float f = (c - P.box_lo[d]) * P.inv_h[d];
+        const int i = min((int)f, P.grid[d] - 2);
+        idx[d] = i;
+        t[d] = f - (float)i;
+    }
+    const int nz = P.grid[2];
+    const int nyz = P.grid[1] * nz;
+    const int p = (idx[0] * P.grid[1] + idx[1]) * nz + idx[2];
+    const float2 c000 = __ldg(Wk + p), c001 = __ldg(Wk + p + 1);
+    const float2 c010 = __ldg(Wk + p + nz), c011 = __ldg(Wk + p + nz + 1);
+    const float2 c100 = __ldg(Wk + p + nyz), c101 = __ldg(Wk + p + nyz + 1);
+    const float2 c110 = __ldg(Wk + p + nyz + nz), c111 = __ldg(Wk + p + nyz + nz + 1);
+    const float tz = t[2], ty = t[1], tx = t[0];
+    float2 c00, c01, c10, c11, c0, c1, r;
+    c00.x = fmaf(tz, c001.x - c000.x, c000.x); c00.y = fmaf(tz, c001.y - c000.y, c000.y);
+    c01.x = fmaf(tz, c011.x - c010.x, c010.x); c01.y = fmaf(tz, c011.y - c010.y, c010.y);
+    c10.x = fmaf(tz, c101.x - c100.x, c100.x); c10.y = fmaf(tz, c101.y - c100.y, c100.y);
+    c11.x = fmaf(tz, c111.x - c110.x, c110.x); c11.y = fmaf(tz, c111.y - c110.y, c110.y);
+    c0.x = fmaf(ty, c01.x - c00.x, c00.x); c0.y = fmaf(ty, c01.y - c00.y, c00.y);
+    c1.x = fmaf(ty, c11.x - c10.x, c10.x); c1.y = fmaf(ty, c11.y - c10.y, c10.y);
+    r.x = fmaf(tx, c1.x - c0.x, c0.x);
+    r.y = fmaf(tx, c1.y - c0.y, c0.y);
+    return r;
+}
+
+// Population density of Sec. 7.1: bilinear between grid nodes, 0 outside.
+__device__ __forceinline__ float popdense_at(const ProblemC &P, float x, float y)
+{
+    if (P.popdense == nullptr) return 0.0f;
+    if (!(x >= P.pop_lo[0] && x <= P.pop_hi[0] && y >= P.pop_lo[1] && y <= P.pop_hi[1]))
+        return 0.0f;
+    const float f0 = (x - P.pop_lo[0]) * P.pop_inv_h[0];
+    const float f1 = (y - P.pop_lo[1]) * P.pop_inv_h[1];
+    const int i0 = min((int)f0, P.pop_n[0] - 2), i1 = min((int)f1, P.pop_n[1] - 2);
+    const float t0 = f0 - (float)i0, t1 = f1 - (float)i1;
+    const float *g = P.popdense + (size_t)i0 * P.pop_n[1] + i1;
+    const float g00 = __ldg(g), g01 = __ldg(g + 1);
+    const float g10 = __ldg(g + P.pop_n[1]), g11 = __ldg(g + P.pop_n[1] + 1);
+    const float a = fmaf(t1, g01 - g00, g00), b = fmaf(t1, g11 - g10, g10);
+    return fmaf(t0, b - a, a);
+}
+
+__device__ __forceinline__ float softplus(float g, float beta, float inv_beta)
+{
+    const float bg = beta * g;
+    return bg > 0.0f ? (bg + log1pf(__expf(-bg))) * inv_beta : log1pf(__expf(bg)) * inv_beta;
+}
+
+__global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
+                                                      const DynState *__restrict__ dyn,
+                                                      const float *__restrict__ u,
+                                                      const float2 *__restrict__ W, long long L,
+                                                      int J, float *__restrict__ cost_ms,
+                                                      float *__restrict__ cost_ms_soft,
+                                                      unsigned long long *__restrict__ live)
+{
+    const int G = P.G;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = threadIdx.x & (G - 1);
+    const long long pair = tid / G;
+    const long long l = pair / P.M;
+    const int m = (int)(pair - l * P.M);
+    const bool exists = (l < L) && (i < P.N);
+    const int ia = i < P.N ? i : 0;
+    const AircraftC A = P.ac[ia];
+    const uint32_t mpc = dyn->mpc_step;
+    const float dt = P.dt;
+
+    float x = 0.0f, y = 0.0f, z = 0.0f, v = 100.0f, chi = 0.0f, m0 = 1.0f;
+    if (exists) {
+        x = dyn->x0[i][0]; y = dyn->x0[i][1]; z = dyn->x0[i][2];
+        v = dyn->x0[i][3]; chi = dyn->x0[i][4]; m0 = dyn->x0[i][5];
+    }
+    Kahan F, sA, sB, sC;
+    float sN = 0.0f, soft = 0.0f;
+    bool dead = !exists, landed = false, sepv = false;
+    int seg = -1;
+    float uw = 0.0f, uh = 0.0f, ua = 0.0f;
+    const float *ul = u + ((size_t)(l < L ? l : 0) * P.N + ia) * (size_t)(P.S * 3);
+    float2 turb_next = make_float2(0.0f, 0.0f);
+    unsigned int nlive = 0;
+    const float2 *Wm = W + (size_t)m * P.H * P.P;
+    const bool soft_on = cost_ms_soft != nullptr;
+
+    for (int k = 0; k < P.H; ++k) {
+        if (!dead && !landed) {
+            ++nlive;
+            const int s = (k * P.S) / P.H;
+            if (s != seg) {
+                seg = s;
+                uw = __ldg(ul + 3 * s);
+                uh = __ldg(ul + 3 * s + 1);
+                ua = __ldg(ul + 3 * s + 2);
+            }
+            const float mass = m0 - F.s;
+            // control-derived quantities and their limits (Sec. 3.4)
+            const float sg = uh / v;
+            bool ok = fabsf(sg) <= P.sgmax;
+            const float cg = sqrtf(fmaxf(1.0f - sg * sg, 0.0f));
+            const float tp = uw * v / (kG0 * cg);
+            ok = ok && (fabsf(tp) < P.tpmax);
+            const float secphi = sqrtf(fmaf(tp, tp, 1.0f));
+            const float rho = 1.225f * exp2f(4.2559f * log2f(fmaxf(fmaf(-2.2558e-5f, z, 1.0f), 1e-30f)));
+            const float qS = A.halfS * rho * v * v;
+            const float CL = mass * kG0 * cg * secphi / qS;
+            const float D = qS * fmaf(A.CD2, CL * CL, A.CD0);
+            const float T = fmaf(mass, fmaf(kG0, sg, ua), D);
+            ok = ok && (T >= A.Tmin) && (T <= A.Tmax);
+            if (!ok) {
+                dead = true;
+            } else {
+                // disturbance: wind field of sample m plus white turbulence
+                float2 w = wind_at(P, Wm + (size_t)k * P.P, x, y, z);
+                float2 n;
+                if ((k & 1) == 0) {
+                    const uint4 r = draw(P.key0, P.key1, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8),
+                                         (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
+                    n = box_muller(r.x, r.y);
+                    turb_next = box_muller(r.z, r.w);
+                } else {
+                    n = turb_next;
+                }
+                w.x = fmaf(P.turb_sigma, n.x, w.x);
+                w.y = fmaf(P.turb_sigma, n.y, w.y);
+                // explicit Euler step of Eq. (hor); v sin(gamma) = hdot, the
+                // speed equation reduces to v += dt a and the heading equation
+                // to chi += dt w (coordinated turn)
+                float sc, cc;
+                sincosf(chi, &sc, &cc);
+                const float vh = v * cg;
+                x = fmaf(dt, fmaf(vh, cc, w.x), x);
+                y = fmaf(dt, fmaf(vh, sc, w.y), y);
+                z = fmaf(dt, uh, z);
+                const float eta = A.Cf1 * fmaf(v, A.invCf2, 1.0f);
+                F.add(dt * eta * T);
+                v = fmaf(dt, ua, v);
+                chi = fmaf(dt, uw, chi);
+                const float mass1 = m0 - F.s;
+                if (!(z >= P.z_min && z <= P.z_max && v >= P.v_min && v <= P.v_max &&
+                      mass1 >= A.m_empty)) {
+                    dead = true;
+                } else {
+                    const float th = atan2f(y, x);
+                    if (A.type == 0) {
+                        // arrival: flow-field arc, glide angle and landing sector
+                        const float r = sqrtf(fmaf(x, x, y * y));
+                        const float ath = fabsf(th);
+                        const float ratio = ath < 1e-3f ? fmaf(th * th, 1.0f / 6.0f, 1.0f)
+                                                        : ath / fmaxf(sinf(ath), 0.25f * ath);
+                        const float beta = atan2f(z, r * ratio);
+                        const float hdg = angdist(chi - kPi);
+                        if (r <= P.P_runway && beta <= P.P_beta && x > 0.0f && ath <= P.P_chi &&
+                            hdg <= P.P_chi && v <= P.P_vs) {
+                            landed = true;
+                        } else {
+                            sA.add(angdist(chi - fmaf(2.0f, th, kPi)));
+                            sB.add(fabsf(beta - P.beta_f));
+                        }
+                    } else {
+                        sA.add(angdist(th - A.thF));
+                        sB.add(fabsf(A.Z - z));
+                        sC.add(fabsf(v - A.vD));
+                    }
+                    if (P.w_noise != 0.0f && !landed) {
+                        const float za = z * P.Ac_inv;
+                        const float h = fmaxf(fmaf(-za, za, 1.0f), 0.0f);
+                        sN = fmaf(h, popdense_at(P, x, y), sN);
+                    }
+                }
+            }
+        }
+        // binary separation constraints at step k+1 among flying aircraft
+        const bool act = !dead && !landed;
+        for (int r = 1; r < G; ++r) {
+            const int src = (i + r) & (G - 1);
+            const float ox = __shfl_sync(0xffffffffu, x, src, G);
+            const float oy = __shfl_sync(0xffffffffu, y, src, G);
+            const float oz = __shfl_sync(0xffffffffu, z, src, G);
+            const int oact = __shfl_sync(0xffffffffu, (int)act, src, G);
+            if (act && oact) {
+                const float dx = x - ox, dy = y - oy;
+                const float dh2 = fmaf(dx, dx, dy * dy);
+                const float adz = fabsf(z - oz);
+                if (dh2 < P.Sh2 && adz < P.Sv) sepv = true;
+                if (soft_on) {
+                    const float g = fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f),
+                                          fmaf(-adz, P.Sv_inv, 1.0f));
+                    soft += softplus(g, P.sp_beta, P.sp_inv_beta);
+                }
+            }
+        }
+    }
+
+    // objectives (Sec. 3.5, Sec. 7.1) and the per-sample cost -ln J_T
+    const float invH = 1.0f / (float)P.H;
+    const float Jf = fmaf(-F.s, A.invFmax, 1.0f);
+    float Jsum;
+    if (A.type == 1) {
+        const float J1 = fmaf(-sA.s * invH, 1.0f / kPi, 1.0f);
+        const float J3 = (A.supB - sB.s * invH) * A.invSupInf;
+        const float J4 = fmaf(-sC.s * invH, A.invCmax, 1.0f);
+        Jsum = P.a_dep[0] * J1 + P.a_dep[1] * Jf + P.a_dep[2] * J3 + P.a_dep[3] * J4;
+    } else {
+        const float J1 = fmaf(-sA.s * invH, 1.0f / kPi, 1.0f);
+        const float J3 = fmaf(-sB.s * invH, 2.0f / kPi, 1.0f);
+        Jsum = P.a_arr[0] * J1 + P.a_arr[1] * J3 + P.a_arr[2] * Jf;
+    }
+    const float JT = (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-sN, invH, 1.0f);
+    const float c = -logf(fmaxf(JT, 1e-30f));
+    if (exists) {
+        const size_t o = ((size_t)l * P.M + m) * P.N + i;
+        cost_ms[o] = (dead || sepv) ? __int_as_float(0x7f800000) : c;
+        if (soft_on) cost_ms_soft[o] = dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
+    }
+    if (live != nullptr) {
+        const unsigned int tot = __reduce_add_sync(0xffffffffu, exists ? nlive : 0u);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(live, (unsigned long long)tot);
+    }
+}
+
+// Mean over wind samples: cbar[i][l] = (1/M) sum_m cost_ms[l][m][i], +inf when any
+// sample was infeasible.  Samples are summed in order with compensation.
+__global__ void __launch_bounds__(256) sample_mean_kernel(const float *__restrict__ cost_ms,
+                                                          long long L, int M, int N,
+                                                          float *__restrict__ cbar)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L * N) return;
+    const long long l = t / N;
+    const int i = (int)(t - l * N);
+    Kahan s;
+    bool inf = false;
+    const float *c = cost_ms + (size_t)l * M * N + i;
+    for (int m = 0; m < M; ++m) {
+        const float v = __ldg(c + (size_t)m * N);
+        if (isinf(v)) inf = true;
+        else s.add(v);
+    }
+    cbar[(size_t)i * L + l] = inf ? __int_as_float(0x7f800000) : s.s / (float)M;
+}
+
+}  // namespace
+
+cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
+                           int64_t L, int J, float *cost_ms, float *cost_ms_soft,
+                           unsigned long long *live, cudaStream_t st)
+{
+    if (L <= 0) return cudaSuccess;
+    const long long threads = (long long)L * P.M * P.G;
+    const int block = 256;
+    const long long grid = (threads + block - 1) / block;
+    rollout_kernel<<<(unsigned)grid, block, 0, st>>>(P, dyn, u, reinterpret_cast<const float2 *>(W),
+                                                      L, J, cost_ms, cost_ms_soft, live);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_mean(const float *cost_ms, int64_t L, int M, int N, float *cbar,
+                               cudaStream_t st)
+{
+    if (L <= 0) return cudaSuccess;
+    const long long n = (long long)L * N;
+    sample_mean_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cost_ms, L, M, N, cbar);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tma

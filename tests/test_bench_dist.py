@@ -1,0 +1,55 @@
+"""Host logic of the N > 1 benchmark path on CPU ranks (gloo, world size 2):
+every rank solves its own replica, the reported time is the maximum over
+ranks, and only rank 0 of the reference arm does any work."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, r, l = bench.dist_setup()
+        assert (w, r, l) == (world, rank, rank)
+        elapsed = 10.0 + 5.0 * rank
+        out[rank] = bench.max_over_ranks(elapsed, world)
+        p = bench.replica_problem(rank)
+        out[world + rank] = p.seed
+        args = type("A", (), {"steps": 1, "warmup": 0, "gpus": world, "reference_particles": 8})()
+        if rank != 0:
+            assert bench.run_reference(args, world, rank) == 0   # returns at once
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_cpu_ranks_take_max_time_and_distinct_replicas():
+    world = 2
+    port = _free_port()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
+    assert out[0] == out[1] == 15.0
+    assert out[2] != out[3]
+
+
+def test_units_and_flops_per_unit():
+    import scenarios as S
+    p = S.config2()
+    assert bench.units_per_solve(p) == 65536 * 32 * 8 * 60 * 30
+    f = bench.flops_per_unit(p)
+    assert 150 < f < 260
+    assert bench.flops_per_unit(S.config3()) > f          # more pairs, soft form, noise
+    assert bench.fp32_peak_tflops(2070) == pytest.approx(80.54, rel=1e-3)

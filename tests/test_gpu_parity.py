@@ -1,0 +1,345 @@
+"""GPU parity: every stage of the CUDA path, called through the C-ABI, against
+the FP64 oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import scenarios as S
+from gpu_helpers import COST_FLOOR, COST_TOL, compare_costs, cuda, oracle_wind
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda()
+
+
+@pytest.fixture(scope="module")
+def pkg(torch):
+    import paper_1506_02869_gb300 as pkg
+    return pkg
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ------------------------------------------------------------------- wind
+
+@pytest.mark.parametrize("cfg,M,H", [(1, None, None), (2, 2, 60), (4, 3, None)])
+def test_wind_field_matches_oracle(torch, pkg, cfg, M, H):
+    p = S.make_config(cfg)
+    p = S.shrink(p, L=64, M=M, H=H).copy(mpc_step=3)
+    solver = pkg.Solver(p)
+    solver.set_state(mpc_step=3)
+    got = solver.wind_field().double().cpu().numpy()
+    ref = O.wind_field(p)
+    err = np.abs(got - ref).max() / p.wind_sigma
+    assert err < 2e-5, err
+    solver.close()
+
+
+# ---------------------------------------------------------------- rollout
+
+def _rollout_case(torch, pkg, p, u, J, pidx=None, soft=False, what=""):
+    solver = pkg.Solver(p)
+    ud = torch.from_numpy(u).cuda()
+    cbar, cs = solver.rollout_cost(ud, J, soft=soft)
+    got = cbar.cpu().numpy().astype(np.float64)
+    got_s = cs.cpu().numpy().astype(np.float64) if soft else None
+    samp = solver.sample_costs(u.shape[0]).cpu().numpy().astype(np.float64)
+    solver.close()
+    idx = np.arange(u.shape[0]) if pidx is None else np.asarray(pidx)
+    ref = O.rollout(p, u[idx], J, pidx=idx, W=oracle_wind(p), soft=soft)
+    out = {"hard": compare_costs(got[:, idx], ref["cbar"], ref["margin"], ref["smargin"], what + " hard")}
+    if soft:
+        out["soft"] = compare_costs(got_s[:, idx], ref["cbar_soft"], ref["margin"], ref["smargin"],
+                                    what + " soft")
+    # per-sample costs of the particles without near-threshold decisions
+    keep = (ref["smargin"] >= 1e-5) & (ref["margin"].min(0) >= 1e-5)
+    g = samp[idx][keep]
+    r = ref["cost"][keep]
+    fin = np.isfinite(r)
+    assert (np.isfinite(g) == fin).all(), what + " per-sample feasibility"
+    err = np.abs(g[fin] - r[fin]) / np.maximum(np.abs(r[fin]), COST_FLOOR)
+    assert err.size == 0 or err.max() <= COST_TOL, (what, err.max())
+    return out
+
+
+@pytest.mark.parametrize("kind", ["uniform", "mild"])
+def test_rollout_config1_all_particles(torch, pkg, kind):
+    p = S.config1()
+    rng = _rng(11)
+    u = (S.random_controls if kind == "uniform" else S.mild_controls)(p, p.L, rng)
+    for J in (0, 7):
+        res = _rollout_case(torch, pkg, p, u, J, what=f"c1 {kind} J={J}")
+        assert res["hard"][1] > 50
+
+
+def test_rollout_config2_full_size_sampled(torch, pkg):
+    # the launch configuration of the benchmark: L = 65536, M = 32, N = 8, H = 60
+    p = S.config2()
+    rng = _rng(12)
+    u = S.random_controls(p, p.L, rng)
+    half = p.L // 2
+    u[half:] = S.mild_controls(p, p.L - half, rng)
+    pidx = np.r_[rng.choice(half, 24, replace=False), half + rng.choice(p.L - half, 40, replace=False),
+                 [0, p.L - 1]]
+    res = _rollout_case(torch, pkg, p, u, 3, pidx=np.unique(pidx), what="c2")
+    assert res["hard"][1] > 100
+
+
+def test_rollout_config3_noise_soft_and_hard(torch, pkg):
+    p = S.shrink(S.config3(), L=1024, M=3)
+    rng = _rng(13)
+    u = S.mild_controls(p, p.L, rng)
+    pidx = np.unique(np.r_[rng.choice(p.L, 24, replace=False), [p.L - 1]])
+    res = _rollout_case(torch, pkg, p, u, 1, pidx=pidx, soft=True, what="c3")
+    assert res["soft"][1] > 100
+
+
+def test_rollout_config4_soft(torch, pkg):
+    p = S.shrink(S.config4(), L=2048)
+    rng = _rng(14)
+    u = S.mild_controls(p, p.L, rng)
+    pidx = np.unique(np.r_[rng.choice(p.L, 32, replace=False), [0]])
+    _rollout_case(torch, pkg, p, u, 2, pidx=pidx, soft=True, what="c4")
+
+
+@pytest.mark.parametrize("sid", [0, 1, 2, 3])
+def test_rollout_config5_uneven_aircraft_counts(torch, pkg, sid):
+    ps = S.config5(n_scen=8)
+    order = sorted(range(8), key=lambda s: ps[s].N)
+    p = S.shrink(ps[order[[0, 3, 6, 7][sid]]], L=512, M=4)
+    rng = _rng(15 + sid)
+    u = S.mild_controls(p, p.L, rng)
+    pidx = np.unique(np.r_[rng.choice(p.L, 32, replace=False)])
+    _rollout_case(torch, pkg, p, u, 0, pidx=pidx, what=f"c5 N={p.N}")
+
+
+@pytest.mark.parametrize("change", [dict(L=1), dict(L=1000), dict(H=1, S=1), dict(S=20),
+                                    dict(grid=(2, 2, 2)), dict(M=1), dict(M=5, L=333)])
+def test_rollout_edge_shapes(torch, pkg, change):
+    p = S.config1().copy(**change)
+    rng = _rng(16)
+    u = S.mild_controls(p, p.L, rng)
+    _rollout_case(torch, pkg, p, u, 0, what=str(change))
+
+
+@pytest.mark.parametrize("n", [1, 3, 17, 32])
+def test_rollout_aircraft_counts(torch, pkg, n):
+    base = S.config5(n_scen=1)[0]
+    rng = _rng(17)
+    ac = S._traffic(rng, max(1, n // 2), n - max(1, n // 2), ring=45000.0, z_top=9000.0,
+                    sep_h=base.sep_h, sep_v=base.sep_v)
+    p = base.copy(N=n, L=256, M=2, H=30)
+    p.aircraft = ac
+    u = S.mild_controls(p, p.L, rng)
+    _rollout_case(torch, pkg, p, u, 0, what=f"N={n}")
+
+
+def test_rollout_live_steps_counts_flying_aircraft(torch, pkg):
+    p = S.config1()
+    rng = _rng(18)
+    u = S.random_controls(p, p.L, rng)
+    solver = pkg.Solver(p)
+    solver.rollout_cost(torch.from_numpy(u).cuda(), 0)
+    live = solver.live_steps()
+    solver.close()
+    ref = O.rollout(p, u, 0, W=oracle_wind(p))
+    assert abs(live - ref["live"]) <= 0.001 * ref["live"]
+
+
+# -------------------------------------------------------------------- LSE
+
+@pytest.mark.parametrize("nseg,L", [(8, 65536), (24, 262144), (3, 1), (5, 2049), (1, 4097), (2, 2048)])
+@pytest.mark.parametrize("kappa", [8, 24, 708])
+def test_lse_matches_oracle(torch, pkg, nseg, L, kappa):
+    rng = _rng(nseg * 1000 + L % 977 + kappa)
+    c = S.random_cbar(nseg, L, rng, frac_inf=0.2)
+    if nseg > 2:
+        c[1] = np.inf                                    # a degenerate segment
+    wt, lm, ws = pkg.lse(torch.from_numpy(c).cuda(), kappa)
+    wt, lm, ws = wt.cpu().numpy(), lm.cpu().numpy(), ws.cpu().numpy()
+    rwt, rlm, rws = O.lse(c.astype(np.float64), kappa)
+    assert np.array_equal(lm, rlm)
+    nz = rwt > 1e-300
+    assert np.array_equal(wt == 0, rwt == 0) or np.all(np.abs(wt[~nz]) < 1e-290)
+    assert np.all(np.abs(wt[nz] - rwt[nz]) <= 1e-12 * rwt[nz])
+    assert np.allclose(ws, rws, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------------------- resampling
+
+@pytest.mark.parametrize("nseg,L", [(8, 65536), (24, 262144), (1, 1), (3, 5), (2, 2049), (4, 6144),
+                                    (1, 1 << 22)])
+def test_resample_bit_exact(torch, pkg, nseg, L):
+    rng = _rng(nseg + L)
+    w = S.random_wtilde(nseg, L, rng)
+    seed, sid, J, mpc = 20150601 + L, nseg % 3, L % 50, 7
+    anc, st = pkg.resample(torch.from_numpy(w).cuda(), seed, sid, J, mpc)
+    anc = anc.cpu().numpy()
+    p = S.config1().copy(seed=seed, scenario_id=sid, mpc_step=mpc)
+    r = [O.resample_uniform(p, s, J) for s in range(nseg)]
+    ref, nd = O.resample(w, r)
+    assert np.array_equal(anc, ref)
+    assert (st == pkg.TMA_WARN_DEGENERATE) == (nd > 0)
+
+
+def test_resample_concentrated_and_degenerate(torch, pkg):
+    L = 50000
+    w = np.zeros((4, L))
+    w[0, 12345] = 1.0                                    # all mass on one particle
+    w[1] = 1e-3                                          # equal weights: identity
+    w[2, ::7] = 1.0                                      # sparse support
+    # w[3] stays zero: degenerate
+    anc, st = pkg.resample(torch.from_numpy(w).cuda(), 5, 0, 2, 0)
+    anc = anc.cpu().numpy()
+    assert (anc[0] == 12345).all()
+    assert (anc[1] == np.arange(L)).all()
+    assert (anc[2] % 7 == 0).all()
+    assert (anc[3] == np.arange(L)).all() and st == pkg.TMA_WARN_DEGENERATE
+    p = S.config1().copy(seed=5)
+    ref, _ = O.resample(w, [O.resample_uniform(p, s, 2) for s in range(4)])
+    assert np.array_equal(anc, ref)
+
+
+def test_lse_then_resample_chain(torch, pkg):
+    # the two stateless stages composed as in one SMC iteration
+    rng = _rng(21)
+    c = S.random_cbar(8, 65536, rng)
+    wt, _, _ = pkg.lse(torch.from_numpy(c).cuda(), 16)
+    anc, _ = pkg.resample(wt, 99, 0, 4, 1)
+    rwt, _, _ = O.lse(c.astype(np.float64), 16)
+    p = S.config1().copy(seed=99, mpc_step=1)
+    ref, _ = O.resample(wt.cpu().numpy(), [O.resample_uniform(p, s, 4) for s in range(8)])
+    assert np.array_equal(anc.cpu().numpy(), ref)
+    # against the oracle's own weights the ancestors agree except at rounding-level CDF ties
+    ref2, _ = O.resample(rwt, [O.resample_uniform(p, s, 4) for s in range(8)])
+    assert (anc.cpu().numpy() != ref2).mean() < 1e-4
+
+
+# ------------------------------------------------------------ move / init
+
+@pytest.mark.parametrize("cfg,L", [(1, 1024), (2, 65536), (1, 777)])
+def test_move_matches_oracle(torch, pkg, cfg, L):
+    p = S.shrink(S.make_config(cfg), L=L).copy(mpc_step=2)
+    rng = _rng(cfg * 7 + L)
+    u = S.random_controls(p, L, rng)
+    anc = S.random_ancestors(p.N, L, rng)
+    solver = pkg.Solver(p)
+    solver.set_state(mpc_step=2)
+    out = solver.move(torch.from_numpy(u).cuda(), torch.from_numpy(anc).cuda(), 5).cpu().numpy()
+    solver.close()
+    ref = O.move(p, u.astype(np.float64), anc, 5)
+    sig = np.array(p.move_sigma)
+    lo, hi = np.array(p.ctrl_lo), np.array(p.ctrl_hi)
+    near = (np.abs(ref - lo) < 1e-5 * sig) | (np.abs(ref - hi) < 1e-5 * sig)
+    d = np.abs(out - ref)
+    tol = 2e-6 * sig + 2.5e-7 * np.abs(ref)
+    assert (d[~near] <= np.broadcast_to(tol, d.shape)[~near]).all(), d.max()
+
+
+def test_init_controls_match_oracle(torch, pkg):
+    p = S.config2().copy(mpc_step=4)
+    solver = pkg.Solver(p)
+    solver.set_state(mpc_step=4)
+    got = solver.init_controls(4096).cpu().numpy()
+    solver.close()
+    ref = O.init_controls(p, 4096)
+    w = np.array(p.ctrl_hi) - np.array(p.ctrl_lo)
+    assert (np.abs(got - ref) <= 2e-7 * w + 1.2e-7 * np.abs(ref)).all()
+
+
+# -------------------------------------------------------------- selection
+
+@pytest.mark.parametrize("N,L,frac", [(8, 65536, 0.3), (24, 262144, 0.05), (2, 1, 0.0), (3, 1000, 1.0),
+                                      (32, 16384, 0.5)])
+def test_select_matches_oracle(torch, pkg, N, L, frac):
+    rng = _rng(N * L)
+    c = S.random_cbar(N, L, rng, frac_inf=frac)
+    best, bs, ni = pkg.select(torch.from_numpy(c).cuda())
+    rb, rbs, rni = O.select(c.astype(np.float64))
+    assert best == rb and ni == rni
+    assert (bs == rbs) or (math.isinf(bs) and math.isinf(rbs))
+
+
+def test_select_ties_lowest_index(torch, pkg):
+    c = np.ones((4, 10000), np.float32)
+    c[:, 17] = 0.5
+    c[:, 9000] = 0.5
+    assert pkg.select(torch.from_numpy(c).cuda())[0] == 17
+
+
+# ------------------------------------------------------------------ solve
+
+def test_first_iteration_agrees_with_oracle_chain(torch, pkg):
+    """Both sides run iteration 0 of Algorithm 1 from their own initialisation
+    (random stream 4): costs agree, and so do almost all ancestors."""
+    p = S.config1()
+    solver = pkg.Solver(p)
+    u0 = solver.init_controls()
+    cbar, _ = solver.rollout_cost(u0, 0)
+    wt, _, _ = pkg.lse(cbar, O.kappa(0))
+    anc, _ = pkg.resample(wt, p.seed, p.scenario_id, 0, p.mpc_step)
+    u1 = solver.move(u0, anc, 0)
+    solver.close()
+    ru0 = O.init_controls(p)
+    rr = O.rollout(p, ru0, 0, W=oracle_wind(p))
+    compare_costs(cbar.cpu().numpy().astype(np.float64), rr["cbar"], rr["margin"], rr["smargin"], "J0")
+    rwt, _, _ = O.lse(rr["cbar"], O.kappa(0))
+    ranc, _ = O.resample(rwt, [O.resample_uniform(p, s, 0) for s in range(p.N)])
+    same = anc.cpu().numpy() == ranc
+    assert same.mean() > 0.97, same.mean()
+    ru1 = O.move(p, ru0, ranc, 0)
+    g1 = u1.cpu().numpy()
+    for i in range(p.N):
+        ok = same[i]
+        assert np.allclose(g1[ok, i], ru1[ok, i], rtol=1e-5, atol=1e-5 * np.array(p.move_sigma).max())
+
+
+def test_solve_deterministic_and_host_path(torch, pkg):
+    p = S.config1()
+    solver = pkg.Solver(p)
+    b1, c1, _ = solver.solve()
+    i1 = solver.best_index()
+    b2, c2, _ = solver.solve()
+    assert torch.equal(b1, b2) and c1 == c2 and solver.best_index() == i1
+    host = np.empty((p.N, p.S, 3), np.float32)
+    x0 = np.array([[a[k] for k in ("x", "y", "z", "v", "chi", "m")] for a in p.aircraft])
+    st, ch = pkg.tma_solve_host(solver.h, x0, p.mpc_step, host)
+    assert ch == c1 and np.array_equal(host, b1.cpu().numpy())
+    solver.close()
+    assert np.isfinite(c1)
+
+
+def test_solve_best_cost_reproduced_by_oracle(torch, pkg):
+    # the chosen controls, re-evaluated by the oracle in the last iteration's
+    # streams, give the reported cost
+    p = S.config1()
+    solver = pkg.Solver(p)
+    b, c, _ = solver.solve()
+    best = solver.best_index()
+    solver.close()
+    r = O.rollout(p, b.cpu().numpy().astype(np.float64)[None], p.J_max - 1, pidx=[best],
+                  W=oracle_wind(p))
+    if (r["margin"] >= 1e-5).all() and (r["smargin"] >= 1e-5).all():
+        assert r["cbar"][:, 0].sum() == pytest.approx(c, rel=1e-4)
+
+
+def test_solve_quality_matches_oracle_statistically(torch, pkg):
+    gpu, orc = [], []
+    for step in range(4):
+        p = S.config1().copy(mpc_step=step)
+        solver = pkg.Solver(p)
+        solver.set_state(mpc_step=step)
+        _, c, _ = solver.solve()
+        solver.close()
+        gpu.append(c)
+        orc.append(O.smc_solve(p, nthreads=8)["best_sum"])
+    gpu, orc = np.array(gpu), np.array(orc)
+    assert np.isfinite(gpu).all() and np.isfinite(orc).all()
+    assert abs(np.median(gpu) - np.median(orc)) <= 0.1 * np.median(orc), (gpu, orc)
