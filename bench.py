@@ -337,6 +337,36 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_rollout_only(args, local):
+    """Small rollout-only case for kernel profiling: the workload's traffic and
+    wind field with `--particles` particles, uniform initial controls, K rollouts."""
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+    import scenarios as S
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    p = S.config2().copy(L=args.particles)
+    solver = pkg.Solver(p)
+    u = solver.init_controls()
+    for _ in range(args.warmup):
+        solver.rollout_cost(u, 0)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for j in range(args.steps):
+        solver.rollout_cost(u, j)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / max(args.steps, 1)
+    units = p.L * p.M * p.N * p.H
+    print(json.dumps({"mode": "rollout-only", "particles": p.L, "ms_per_rollout": ms,
+                      "units_per_s": units / (ms * 1e-3), "live_steps": solver.live_steps()}))
+    solver.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,8 +376,13 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-particles", type=int, default=128)
     ap.add_argument("--reference-particles", type=int, default=64)
+    ap.add_argument("--rollout-only", action="store_true",
+                    help="time only the rollout on --particles particles (profiling case)")
+    ap.add_argument("--particles", type=int, default=4096)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
+    if args.rollout_only:
+        return run_rollout_only(args, local)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local)

@@ -39,8 +39,9 @@ __device__ __forceinline__ unsigned long long qfix(double w)
     return 0ull;
 }
 
+// Block-wide reduction; `identity` pads the lanes beyond the number of warps.
 template <typename T, typename Op>
-__device__ __forceinline__ T block_reduce(T v, Op op, T *sh)
+__device__ __forceinline__ T block_reduce(T v, Op op, T *sh, T identity)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -48,7 +49,7 @@ __device__ __forceinline__ T block_reduce(T v, Op op, T *sh)
     if (lane == 0) sh[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : sh[0];
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : identity;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) sh[0] = v;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restric
             if (v < mn) mn = v;             // +inf and NaN never lower the minimum
         }
     }
-    mn = block_reduce(mn, MinOp(), sh);
+    mn = block_reduce(mn, MinOp(), sh, __int_as_float(0x7f800000));
     if (threadIdx.x == 0) cmin[(size_t)s * nchunk + c] = mn;
 }
 
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
     const int s = blockIdx.y, c = blockIdx.x;
     float mn = __int_as_float(0x7f800000);
     for (int j = threadIdx.x; j < nchunk; j += kThreads) mn = fminf(mn, cmin[(size_t)s * nchunk + j]);
-    mn = block_reduce(mn, MinOp(), shf);
+    mn = block_reduce(mn, MinOp(), shf, __int_as_float(0x7f800000));
     const bool any = !isinf(mn);
     const double lmax = -kappa * (double)mn;
     const float *row = cbar + (size_t)s * L;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) res_chunk_sum(const double *__restri
         const long long idx = base + threadIdx.x + j * kThreads;
         if (idx < L) acc += qfix(__ldg(row + idx));
     }
-    acc = block_reduce(acc, AddU64(), sh);
+    acc = block_reduce(acc, AddU64(), sh, 0ull);
     if (threadIdx.x == 0) cq[(size_t)s * nchunk + c] = acc;
 }
 
@@ -200,8 +201,8 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         total += v;
         if (j < c) before += v;
     }
-    before = block_reduce(before, AddU64(), sh);
-    total = block_reduce(total, AddU64(), sh);
+    before = block_reduce(before, AddU64(), sh, 0ull);
+    total = block_reduce(total, AddU64(), sh, 0ull);
     int32_t *a = anc + (size_t)s * L;
 
     if (total == 0) {

@@ -105,8 +105,11 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
     Kahan F, sA, sB, sC;
     float sN = 0.0f, soft = 0.0f;
     bool dead = !exists, landed = false, sepv = false;
-    int seg = -1;
+    int seg = -1, ks = 0;
     float uw = 0.0f, uh = 0.0f, ua = 0.0f;
+    // within a control segment z, v and chi are linear in time: evaluate them
+    // from the segment's start values so that rounding does not accumulate
+    float zb = 0.0f, vb = 0.0f, cb = 0.0f, dz = 0.0f, dv = 0.0f, dc = 0.0f;
     const float *ul = u + ((size_t)(l < L ? l : 0) * P.N + ia) * (size_t)(P.S * 3);
     float2 turb_next = make_float2(0.0f, 0.0f);
     unsigned int nlive = 0;
@@ -119,9 +122,16 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
             const int s = (k * P.S) / P.H;
             if (s != seg) {
                 seg = s;
+                ks = k;
                 uw = __ldg(ul + 3 * s);
                 uh = __ldg(ul + 3 * s + 1);
                 ua = __ldg(ul + 3 * s + 2);
+                zb = z;
+                vb = v;
+                cb = chi;
+                dz = dt * uh;
+                dv = dt * ua;
+                dc = dt * uw;
             }
             const float mass = m0 - F.s;
             // control-derived quantities and their limits (Sec. 3.4)
@@ -161,11 +171,12 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
                 const float vh = v * cg;
                 x = fmaf(dt, fmaf(vh, cc, w.x), x);
                 y = fmaf(dt, fmaf(vh, sc, w.y), y);
-                z = fmaf(dt, uh, z);
+                const float nk = (float)(k + 1 - ks);
+                z = fmaf(nk, dz, zb);
                 const float eta = A.Cf1 * fmaf(v, A.invCf2, 1.0f);
                 F.add(dt * eta * T);
-                v = fmaf(dt, ua, v);
-                chi = fmaf(dt, uw, chi);
+                v = fmaf(nk, dv, vb);
+                chi = fmaf(nk, dc, cb);
                 const float mass1 = m0 - F.s;
                 if (!(z >= P.z_min && z <= P.z_max && v >= P.v_min && v <= P.v_max &&
                       mass1 >= A.m_empty)) {
