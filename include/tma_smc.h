@@ -219,6 +219,28 @@ tma_status tma_resample(const double *d_wtilde, int32_t nseg, int64_t L, uint64_
  * i = 0..N-1, ties to the lowest l.  Writes d_best (int64), d_best_sum (double;
  * +inf when the chosen particle has an infeasible aircraft), d_ninf (int32).
  * Scratch: d_work of tma_select_workspace() bytes. */
+/* Systematic resampling exactly as tma_resample, for callers that cannot
+ * allocate device memory: a control loop that must never block in (or fail
+ * inside) the CUDA allocator once it is running, or a host application whose
+ * device memory is entirely owned by another allocator and which cannot hand
+ * out a workspace.  The paper has no counterpart; this is a deployment
+ * variant.
+ *   - Scratch: a fixed array inside this library (about 512 KB; every GPU that
+ *     loads the library holds it until the process exits).  The call itself
+ *     allocates nothing and needs no workspace.
+ *   - Limit: nseg * ceil(L / 2048) <= 65536 (e.g. 32 segments of 4,194,304
+ *     particles); larger sizes return TMA_ERR_INVALID_ARG.  Other arguments
+ *     and errors as tma_resample; synchronises the stream to read the
+ *     degenerate-segment status.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls that overlap on the GPU (different streams or threads at the same
+ *     time) race and must be serialised by the caller. */
+tma_status tma_resample_noalloc(const double *d_wtilde, int32_t nseg, int64_t L, uint64_t seed,
+                                uint32_t scenario_id, uint32_t J, uint32_t mpc_step, int32_t *d_anc,
+                                tma_stream_t stream);
+
 size_t tma_select_workspace(int64_t L);
 tma_status tma_select(const float *d_cbar, int32_t N, int64_t L, int64_t *d_best, double *d_best_sum,
                       int32_t *d_ninf, void *d_work, size_t work_bytes, tma_stream_t stream);

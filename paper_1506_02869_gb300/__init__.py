@@ -31,6 +31,7 @@ EXPORTS = [
     "tma_move", "tma_init_controls", "tma_solve", "tma_solve_host", "tma_best_index",
     "tma_lse_workspace", "tma_lse", "tma_resample_workspace", "tma_resample",
     "tma_select_workspace", "tma_select", "tma_profile_enable", "tma_profile_read",
+    "tma_resample_noalloc",
 ]
 
 
@@ -120,6 +121,7 @@ def lib():
                 "tma_select_workspace": ([i64], sz),
                 "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_profile_enable": ([vp, C.c_int], C.c_int),
+                "tma_resample_noalloc": ([vp, i32, i64, u64, u32, u32, u32, vp, st], C.c_int),
                 "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
             }
             for name, (args, res) in sig.items():
@@ -336,6 +338,16 @@ def tma_resample(wtilde, seed, scenario_id, J, mpc_step, anc, work=None, stream=
                                      int(scenario_id), int(J), int(mpc_step), _dptr(anc),
                                      _dptr(work), work.numel(), _stream(stream)),
                   "tma_resample", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+
+
+def tma_resample_noalloc(wtilde, seed, scenario_id, J, mpc_step, anc, stream=None):
+    """tma_resample without a workspace (library-owned fixed scratch; see the
+    header for its size limit and the serialisation rule); returns the status."""
+    nseg, L = wtilde.shape
+    return _check(lib().tma_resample_noalloc(_dptr(wtilde), nseg, L, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                             int(scenario_id), int(J), int(mpc_step), _dptr(anc),
+                                             _stream(stream)),
+                  "tma_resample_noalloc", allow=(TMA_OK, TMA_WARN_DEGENERATE))
 
 
 def tma_select(cbar, best, best_sum=None, ninf=None, work=None, stream=None):

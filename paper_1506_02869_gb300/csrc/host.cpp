@@ -30,6 +30,8 @@ static tma_status cuda_fail(cudaError_t e)
     return TMA_ERR_CUDA;
 }
 
+tma_status record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 #define TMA_CUDA(expr)                             \
     do {                                           \
         cudaError_t e_ = (expr);                   \

@@ -19,6 +19,7 @@
 //             division.  Integer arithmetic makes the result independent of the
 //             summation order.
 #include <cfloat>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "tma_internal.h"
@@ -294,6 +295,42 @@ cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, dou
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// Resampling without any allocation by the caller or the library.
+//
+// The scratch of tma_resample (one uint64 partial sum per (segment, chunk) and
+// a status word) lives here in a file-scope device array instead of a
+// caller-provided workspace.  Every GPU that loads this library keeps the
+// array (about 512 KB) until the process exits.  Host code must not use the
+// array's name as a device address: its device address is fetched once per
+// device with cudaGetSymbolAddress and passed to the kernels.
+
+namespace {
+constexpr long long kNoAllocMaxPartials = 65536;   // nseg * ceil(L / 2048) at most
+static __device__ __align__(256) unsigned long long g_resample_scratch[kNoAllocMaxPartials + 2];
+std::mutex g_scratch_mu;
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device (set up on first use).
+cudaError_t scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_resample_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
                             int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st)
@@ -308,6 +345,36 @@ cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t 
                                           d_flags);
     count_launch(2);
     return cudaGetLastError();
+}
+
+// See include/tma_smc.h.
+extern "C" tma_status tma_resample_noalloc(const double *d_wtilde, int32_t nseg, int64_t L,
+                                           uint64_t seed, uint32_t scenario_id, uint32_t J,
+                                           uint32_t mpc_step, int32_t *d_anc, tma_stream_t stream)
+{
+    if (nseg < 0 || L < 0 || L > TMA_MAX_PARTICLES || J > 0xFFFF || mpc_step > 0xFFFF)
+        return TMA_ERR_INVALID_ARG;
+    if (nseg == 0 || L == 0) return TMA_OK;
+    if (!d_wtilde || !d_anc) return TMA_ERR_INVALID_ARG;
+    if ((long long)nseg * n_chunks(L) > kNoAllocMaxPartials) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    cudaError_t e = scratch_address(&scratch);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    // the status word follows the partial sums; it must start at zero
+    unsigned int *flags =
+        reinterpret_cast<unsigned int *>(static_cast<unsigned long long *>(scratch) + kNoAllocMaxPartials);
+    if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned int), st)) != cudaSuccess)
+        return record_cuda_error(e);
+    const uint64_t key = seed + (uint64_t)scenario_id * 0x9E3779B97F4A7C15ull;
+    if ((e = launch_resample(d_wtilde, nseg, L, (uint32_t)key, (uint32_t)(key >> 32), J, nullptr,
+                             mpc_step, d_anc, scratch, flags, st)) != cudaSuccess)
+        return record_cuda_error(e);
+    unsigned int h = 0;
+    if ((e = cudaMemcpyAsync(&h, flags, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return record_cuda_error(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return record_cuda_error(e);
+    return (h & 1u) ? TMA_WARN_DEGENERATE : TMA_OK;
 }
 
 }  // namespace tma

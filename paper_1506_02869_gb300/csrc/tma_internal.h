@@ -98,6 +98,9 @@ cudaError_t launch_gather_best(const float *u, const int64_t *best, int nctl_per
 
 void count_launch(int n = 1);
 
+// Store the CUDA error text for tma_last_error_string(); returns TMA_ERR_CUDA.
+tma_status record_cuda_error(cudaError_t e);
+
 // Host FP64 Cholesky (lower), row-major n x n, in place; returns false if not
 // positive definite.
 bool cholesky_lower(std::vector<double> &A, int n);
