@@ -143,7 +143,8 @@ tma_status tma_wind_field(tma_solver *s, float *d_W, tma_stream_t stream);
 tma_status tma_rollout_cost(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *d_cbar,
                             float *d_cbar_soft, tma_stream_t stream);
 
-/* Per-sample costs of the last tma_rollout_cost call: d_out[L][M][N] float32. */
+/* Per-sample costs of the last tma_rollout_cost call: d_out[M][N][L] float32
+ * (wind sample, aircraft, particle), L <= the L of that call. */
 tma_status tma_sample_costs(tma_solver *s, float *d_out, int64_t L, int soft, tma_stream_t stream);
 
 /* Number of simulated (not frozen) aircraft-steps in the last tma_rollout_cost

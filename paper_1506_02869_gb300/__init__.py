@@ -255,7 +255,8 @@ def tma_rollout_cost(h, u, J, cbar, cbar_soft=None, stream=None):
 
 
 def tma_sample_costs(h, out, soft=False, stream=None):
-    _check(lib().tma_sample_costs(h, _dptr(out), out.shape[0], int(soft), _stream(stream)),
+    """out: cuda float32 [M][N][L]."""
+    _check(lib().tma_sample_costs(h, _dptr(out), out.shape[2], int(soft), _stream(stream)),
            "tma_sample_costs")
 
 
@@ -402,7 +403,7 @@ class Solver:
 
     def sample_costs(self, L, soft=False):
         torch = _torch()
-        out = torch.empty((L, self.M, self.N), dtype=torch.float32, device=self.device)
+        out = torch.empty((self.M, self.N, L), dtype=torch.float32, device=self.device)
         tma_sample_costs(self.h, out, soft)
         return out
 

@@ -627,8 +627,10 @@ tma_status tma_sample_costs(tma_solver *s, float *d_out, int64_t L, int soft, tm
     if (!s || !d_out || L < 0 || L > s->last_L) return TMA_ERR_INVALID_ARG;
     const float *src = soft ? s->d_cost_ms_soft : s->d_cost_ms;
     if (!src) return TMA_ERR_INVALID_ARG;
-    TMA_CUDA(cudaMemcpyAsync(d_out, src, (size_t)L * s->prob.M * s->prob.N * 4,
-                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    // the buffer holds [M][N][last_L]; copy out the first L particles of each row
+    TMA_CUDA(cudaMemcpy2DAsync(d_out, (size_t)L * 4, src, (size_t)s->last_L * 4, (size_t)L * 4,
+                               (size_t)s->prob.M * s->prob.N, cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
     return TMA_OK;
 }
 

@@ -1,13 +1,16 @@
 // Particle-parallel rollout and costing: the inner loop of Algorithm 1
 // (Sec. 3.3-3.6, Sec. 7.1) for every (particle, wind sample, aircraft).
 //
-// Thread mapping: a group of G = next_pow2(N) consecutive lanes simulates one
-// (particle l, wind sample m); lane i is aircraft i and keeps its state
-// (position, airspeed, heading, fuel burned) and cost accumulators in
-// registers for the whole horizon.  The pairwise separation check of
-// Eq. (avoidance) at every step exchanges positions inside the group with
-// G-1 shuffle rotations.  Groups are ordered with the wind sample fastest, so
-// a warp reads one particle's controls (broadcast) and 32/G wind fields.
+// Thread mapping: one block simulates 32 particles under one wind sample m;
+// warp i of the block is aircraft i, lane j is particle 32*b + j.  Every thread
+// keeps its aircraft's state (position, airspeed, heading, fuel burned) and
+// cost accumulators in registers for the whole horizon.  Aircraft type,
+// constants and the wind field are uniform over a warp, so warps do not
+// diverge on the arrival/departure terms and the constants are broadcast.
+// The pairwise separation check of Eq. (avoidance) reads the other aircraft's
+// positions of the same particle from shared memory (double-buffered by step,
+// one barrier per step).  Blocks are ordered with the wind sample slowest, so
+// the blocks resident at one time read the same wind field and share it in L2.
 #include "device_common.cuh"
 #include "tma_internal.h"
 
@@ -77,73 +80,72 @@ __device__ __forceinline__ float softplus(float g, float beta, float inv_beta)
     return bg > 0.0f ? (bg + log1pf(__expf(-bg))) * inv_beta : log1pf(__expf(bg)) * inv_beta;
 }
 
-__global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
-                                                      const DynState *__restrict__ dyn,
-                                                      const float *__restrict__ u,
-                                                      const float2 *__restrict__ W, long long L,
-                                                      int J, float *__restrict__ cost_ms,
-                                                      float *__restrict__ cost_ms_soft,
-                                                      unsigned long long *__restrict__ live)
+constexpr int kPB = 32;   // particles per block: one warp per aircraft
+
+__global__ void __launch_bounds__(1024) rollout_kernel(const ProblemC P,
+                                                       const DynState *__restrict__ dyn,
+                                                       const float *__restrict__ u,
+                                                       const float2 *__restrict__ W, long long L,
+                                                       int nLb, int J, float *__restrict__ cost_ms,
+                                                       float *__restrict__ cost_ms_soft,
+                                                       unsigned long long *__restrict__ live)
 {
-    const int G = P.G;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = threadIdx.x & (G - 1);
-    const long long pair = tid / G;
-    const long long l = pair / P.M;
-    const int m = (int)(pair - l * P.M);
-    const bool exists = (l < L) && (i < P.N);
-    const int ia = i < P.N ? i : 0;
-    const AircraftC A = P.ac[ia];
+    // positions published every step for the separation check: [2][3][N][32]
+    extern __shared__ float spos[];
+    const int N = P.N;
+    const int i = threadIdx.x >> 5;            // aircraft: warp-uniform
+    const int j = threadIdx.x & 31;            // particle slot
+    const int m = blockIdx.x / nLb;            // wind sample: block-uniform
+    const long long l = (long long)(blockIdx.x - m * nLb) * kPB + j;
+    const bool exists = l < L;
+    const AircraftC &A = P.ac[i];
     const uint32_t mpc = dyn->mpc_step;
     const float dt = P.dt;
 
-    float x = 0.0f, y = 0.0f, z = 0.0f, v = 100.0f, chi = 0.0f, m0 = 1.0f;
-    if (exists) {
-        x = dyn->x0[i][0]; y = dyn->x0[i][1]; z = dyn->x0[i][2];
-        v = dyn->x0[i][3]; chi = dyn->x0[i][4]; m0 = dyn->x0[i][5];
-    }
+    float x = dyn->x0[i][0], y = dyn->x0[i][1], z = dyn->x0[i][2];
+    float v = dyn->x0[i][3], chi = dyn->x0[i][4];
+    const float m0 = dyn->x0[i][5];
     Kahan F, sA, sB, sC;
     float sN = 0.0f, soft = 0.0f;
     bool dead = !exists, landed = false, sepv = false;
-    int seg = -1, ks = 0;
+    int seg = -1, ks = 0, knext = 0;
     float uw = 0.0f, uh = 0.0f, ua = 0.0f;
     // within a control segment z, v and chi are linear in time: evaluate them
     // from the segment's start values so that rounding does not accumulate
-    float zb = 0.0f, vb = 0.0f, cb = 0.0f, dz = 0.0f, dv = 0.0f, dc = 0.0f;
-    const float *ul = u + ((size_t)(l < L ? l : 0) * P.N + ia) * (size_t)(P.S * 3);
+    float zb = 0.0f, vb = 0.0f, cb = 0.0f;
+    const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
     float2 turb_next = make_float2(0.0f, 0.0f);
     unsigned int nlive = 0;
     const float2 *Wm = W + (size_t)m * P.H * P.P;
     const bool soft_on = cost_ms_soft != nullptr;
+    const int plane = N * kPB;
 
     for (int k = 0; k < P.H; ++k) {
         if (!dead && !landed) {
             ++nlive;
-            const int s = (k * P.S) / P.H;
-            if (s != seg) {
-                seg = s;
+            if (k >= knext) {
+                // segment s = floor(k S / H) starts at step ceil(s H / S)
+                seg = (k * P.S) / P.H;
+                knext = ((seg + 1) * P.H + P.S - 1) / P.S;
                 ks = k;
-                uw = __ldg(ul + 3 * s);
-                uh = __ldg(ul + 3 * s + 1);
-                ua = __ldg(ul + 3 * s + 2);
+                uw = __ldg(ul + 3 * seg);
+                uh = __ldg(ul + 3 * seg + 1);
+                ua = __ldg(ul + 3 * seg + 2);
                 zb = z;
                 vb = v;
                 cb = chi;
-                dz = dt * uh;
-                dv = dt * ua;
-                dc = dt * uw;
             }
             const float mass = m0 - F.s;
             // control-derived quantities and their limits (Sec. 3.4)
-            const float sg = uh / v;
+            const float sg = __fdividef(uh, v);
             bool ok = fabsf(sg) <= P.sgmax;
             const float cg = sqrtf(fmaxf(1.0f - sg * sg, 0.0f));
-            const float tp = uw * v / (kG0 * cg);
+            const float tp = __fdividef(uw * v, kG0 * cg);
             ok = ok && (fabsf(tp) < P.tpmax);
             const float secphi = sqrtf(fmaf(tp, tp, 1.0f));
-            const float rho = 1.225f * exp2f(4.2559f * log2f(fmaxf(fmaf(-2.2558e-5f, z, 1.0f), 1e-30f)));
+            const float rho = 1.225f * exp2f(4.2559f * __log2f(fmaxf(fmaf(-2.2558e-5f, z, 1.0f), 1e-30f)));
             const float qS = A.halfS * rho * v * v;
-            const float CL = mass * kG0 * cg * secphi / qS;
+            const float CL = __fdividef(mass * kG0 * cg * secphi, qS);
             const float D = qS * fmaf(A.CD2, CL * CL, A.CD0);
             const float T = fmaf(mass, fmaf(kG0, sg, ua), D);
             ok = ok && (T >= A.Tmin) && (T <= A.Tmax);
@@ -156,8 +158,8 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
                 if ((k & 1) == 0) {
                     const uint4 r = draw(P.key0, P.key1, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8),
                                          (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
-                    n = box_muller(r.x, r.y);
-                    turb_next = box_muller(r.z, r.w);
+                    n = box_muller_fast(r.x, r.y);
+                    turb_next = box_muller_fast(r.z, r.w);
                 } else {
                     n = turb_next;
                 }
@@ -167,16 +169,16 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
                 // speed equation reduces to v += dt a and the heading equation
                 // to chi += dt w (coordinated turn)
                 float sc, cc;
-                sincosf(chi, &sc, &cc);
+                sincos_reduced(chi, &sc, &cc);
                 const float vh = v * cg;
                 x = fmaf(dt, fmaf(vh, cc, w.x), x);
                 y = fmaf(dt, fmaf(vh, sc, w.y), y);
-                const float nk = (float)(k + 1 - ks);
-                z = fmaf(nk, dz, zb);
+                const float nk = (float)(k + 1 - ks) * dt;
+                z = fmaf(nk, uh, zb);
                 const float eta = A.Cf1 * fmaf(v, A.invCf2, 1.0f);
                 F.add(dt * eta * T);
-                v = fmaf(nk, dv, vb);
-                chi = fmaf(nk, dc, cb);
+                v = fmaf(nk, ua, vb);
+                chi = fmaf(nk, uw, cb);
                 const float mass1 = m0 - F.s;
                 if (!(z >= P.z_min && z <= P.z_max && v >= P.v_min && v <= P.v_max &&
                       mass1 >= A.m_empty)) {
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
                         const float r = sqrtf(fmaf(x, x, y * y));
                         const float ath = fabsf(th);
                         const float ratio = ath < 1e-3f ? fmaf(th * th, 1.0f / 6.0f, 1.0f)
-                                                        : ath / fmaxf(sinf(ath), 0.25f * ath);
+                                                        : __fdividef(ath, fmaxf(__sinf(ath), 0.25f * ath));
                         const float beta = atan2f(z, r * ratio);
                         const float hdg = angdist(chi - kPi);
                         if (r <= P.P_runway && beta <= P.P_beta && x > 0.0f && ath <= P.P_chi &&
@@ -211,18 +213,21 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
                 }
             }
         }
-        // binary separation constraints at step k+1 among flying aircraft
+        // binary separation constraints at step k+1 among flying aircraft: every
+        // thread publishes its position (a far-away altitude when not flying)
         const bool act = !dead && !landed;
-        for (int r = 1; r < G; ++r) {
-            const int src = (i + r) & (G - 1);
-            const float ox = __shfl_sync(0xffffffffu, x, src, G);
-            const float oy = __shfl_sync(0xffffffffu, y, src, G);
-            const float oz = __shfl_sync(0xffffffffu, z, src, G);
-            const int oact = __shfl_sync(0xffffffffu, (int)act, src, G);
-            if (act && oact) {
-                const float dx = x - ox, dy = y - oy;
+        float *buf = spos + (k & 1) * 3 * plane;
+        buf[i * kPB + j] = x;
+        buf[plane + i * kPB + j] = y;
+        buf[2 * plane + i * kPB + j] = act ? z : 1e30f;
+        __syncthreads();
+        if (act) {
+            for (int i2 = 0; i2 < N; ++i2) {
+                if (i2 == i) continue;
+                const float dx = x - buf[i2 * kPB + j];
+                const float dy = y - buf[plane + i2 * kPB + j];
+                const float adz = fabsf(z - buf[2 * plane + i2 * kPB + j]);
                 const float dh2 = fmaf(dx, dx, dy * dy);
-                const float adz = fabsf(z - oz);
                 if (dh2 < P.Sh2 && adz < P.Sv) sepv = true;
                 if (soft_on) {
                     const float g = fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f),
@@ -250,17 +255,17 @@ __global__ void __launch_bounds__(256) rollout_kernel(const ProblemC P,
     const float JT = (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-sN, invH, 1.0f);
     const float c = -logf(fmaxf(JT, 1e-30f));
     if (exists) {
-        const size_t o = ((size_t)l * P.M + m) * P.N + i;
+        const size_t o = ((size_t)m * N + i) * (size_t)L + l;
         cost_ms[o] = (dead || sepv) ? __int_as_float(0x7f800000) : c;
         if (soft_on) cost_ms_soft[o] = dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
     }
     if (live != nullptr) {
         const unsigned int tot = __reduce_add_sync(0xffffffffu, exists ? nlive : 0u);
-        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(live, (unsigned long long)tot);
+        if (j == 0 && tot) atomicAdd(live, (unsigned long long)tot);
     }
 }
 
-// Mean over wind samples: cbar[i][l] = (1/M) sum_m cost_ms[l][m][i], +inf when any
+// Mean over wind samples: cbar[i][l] = (1/M) sum_m cost_ms[m][i][l], +inf when any
 // sample was infeasible.  Samples are summed in order with compensation.
 __global__ void __launch_bounds__(256) sample_mean_kernel(const float *__restrict__ cost_ms,
                                                           long long L, int M, int N,
@@ -268,17 +273,15 @@ __global__ void __launch_bounds__(256) sample_mean_kernel(const float *__restric
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L * N) return;
-    const long long l = t / N;
-    const int i = (int)(t - l * N);
     Kahan s;
     bool inf = false;
-    const float *c = cost_ms + (size_t)l * M * N + i;
+    const size_t stride = (size_t)N * L;
     for (int m = 0; m < M; ++m) {
-        const float v = __ldg(c + (size_t)m * N);
+        const float v = __ldg(cost_ms + (size_t)m * stride + t);
         if (isinf(v)) inf = true;
         else s.add(v);
     }
-    cbar[(size_t)i * L + l] = inf ? __int_as_float(0x7f800000) : s.s / (float)M;
+    cbar[t] = inf ? __int_as_float(0x7f800000) : s.s / (float)M;
 }
 
 }  // namespace
@@ -288,11 +291,11 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
                            unsigned long long *live, cudaStream_t st)
 {
     if (L <= 0) return cudaSuccess;
-    const long long threads = (long long)L * P.M * P.G;
-    const int block = 256;
-    const long long grid = (threads + block - 1) / block;
-    rollout_kernel<<<(unsigned)grid, block, 0, st>>>(P, dyn, u, reinterpret_cast<const float2 *>(W),
-                                                      L, J, cost_ms, cost_ms_soft, live);
+    const long long nLb = (L + kPB - 1) / kPB;
+    const long long grid = nLb * P.M;
+    const size_t smem = (size_t)2 * 3 * P.N * kPB * sizeof(float);
+    rollout_kernel<<<(unsigned)grid, P.N * kPB, smem, st>>>(
+        P, dyn, u, reinterpret_cast<const float2 *>(W), L, (int)nLb, J, cost_ms, cost_ms_soft, live);
     count_launch();
     return cudaGetLastError();
 }

@@ -50,7 +50,7 @@ def _rollout_case(torch, pkg, p, u, J, pidx=None, soft=False, what=""):
     cbar, cs = solver.rollout_cost(ud, J, soft=soft)
     got = cbar.cpu().numpy().astype(np.float64)
     got_s = cs.cpu().numpy().astype(np.float64) if soft else None
-    samp = solver.sample_costs(u.shape[0]).cpu().numpy().astype(np.float64)
+    samp = solver.sample_costs(u.shape[0]).cpu().numpy().astype(np.float64).transpose(2, 0, 1)
     solver.close()
     idx = np.arange(u.shape[0]) if pidx is None else np.asarray(pidx)
     ref = O.rollout(p, u[idx], J, pidx=idx, W=oracle_wind(p), soft=soft)
