@@ -306,6 +306,9 @@ def run_ours(args, world, rank, local):
     pk = measured_peaks()
     if pk:
         roofline["hbm_peak_gbs_measured"] = pk.get("hbm_gbs")
+    variant, timed = pkg.tma_get_tuning(h)
+    roofline["launch_variant"] = {"chosen": variant,
+                                  "timed_ms": {str(k): round(v, 4) for k, v in timed.items()}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -31,7 +31,7 @@ EXPORTS = [
     "tma_move", "tma_init_controls", "tma_solve", "tma_solve_host", "tma_best_index",
     "tma_lse_workspace", "tma_lse", "tma_resample_workspace", "tma_resample",
     "tma_select_workspace", "tma_select", "tma_profile_enable", "tma_profile_read",
-    "tma_resample_noalloc",
+    "tma_resample_noalloc", "tma_get_tuning",
 ]
 
 
@@ -121,6 +121,7 @@ def lib():
                 "tma_select_workspace": ([i64], sz),
                 "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_profile_enable": ([vp, C.c_int], C.c_int),
+                "tma_get_tuning": ([vp, P(i32), P(i32), P(i32), P(C.c_float)], C.c_int),
                 "tma_resample_noalloc": ([vp, i32, i64, u64, u32, u32, u32, vp, st], C.c_int),
                 "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
             }
@@ -298,6 +299,14 @@ def tma_best_index(h, stream=None):
     v = C.c_int64()
     _check(lib().tma_best_index(h, C.byref(v), _stream(stream)), "tma_best_index")
     return v.value
+
+
+def tma_get_tuning(h):
+    """(chosen rollout variant, {variant: ms per rollout} timed by the autotuner)."""
+    v, n = C.c_int32(), C.c_int32()
+    vs, ms = (C.c_int32 * 8)(), (C.c_float * 8)()
+    _check(lib().tma_get_tuning(h, C.byref(v), C.byref(n), vs, ms), "tma_get_tuning")
+    return v.value, {vs[k]: ms[k] for k in range(n.value)}
 
 
 def tma_profile_enable(h, on=True):

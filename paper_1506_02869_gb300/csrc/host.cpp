@@ -357,11 +357,27 @@ static const uint32_t *dyn_mpc(const tma_solver *s)
                                               offsetof(DynState, mpc_step));
 }
 
+// ------------------------------------------------------------------ autotuner
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+static std::string tune_key(const tma_solver *s)
+{
+    cudaDeviceProp prop;
+    char key[320];
+    if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) prop.name[0] = 0;
+    snprintf(key, sizeof key, "%s|N=%d|pop=%d", prop.name, s->prob.N, s->prob.pop_n[0] > 0);
+    return key;
+}
+
 }  // namespace tma
 
 using namespace tma;
 
 extern "C" {
+
+static tma_status autotune_rollout(tma_solver *s);
 
 const char *tma_status_str(tma_status s)
 {
@@ -461,7 +477,7 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
         const size_t brows = (size_t)s->lda;
         if ((e = alloc(&s->d_Btmp, brows * w.ldb * 4))) return fail(e);
         if ((e = cudaMemset(s->d_Btmp, 0, brows * w.ldb * 4))) return fail(e);
-        if ((e = alloc(&s->d_W, M * H * P * 2 * 4))) return fail(e);
+        if ((e = alloc(&s->d_W, M * H * P * 4 * 4))) return fail(e);   // packed float4 per node
         const size_t ubytes = L * N * p.S * 3 * 4;
         if ((e = alloc(&s->d_u[0], ubytes))) return fail(e);
         if ((e = alloc(&s->d_u[1], ubytes))) return fail(e);
@@ -486,6 +502,12 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
         if ((e = cudaMemcpy(s->d_dyn, &d, sizeof d, cudaMemcpyHostToDevice))) return fail(e);
         if ((e = cudaMemset(s->d_flags, 0, 4))) return fail(e);
         if ((e = cudaMemset(s->d_live, 0, 8))) return fail(e);
+        const tma_status tr = autotune_rollout(s);
+        if (tr != TMA_OK) {
+            free_all(s);
+            delete s;
+            return tr;
+        }
     } catch (const std::bad_alloc &) {
         if (s) {
             free_all(s);
@@ -514,6 +536,19 @@ void tma_destroy(tma_solver *s)
     release_events(s);
     free_all(s);
     delete s;
+}
+
+tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int32_t *h_variants,
+                          float *h_ms)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    if (variant) *variant = s->rollout_variant;
+    if (n_timed) *n_timed = s->n_tuned;
+    for (int c = 0; c < s->n_tuned; ++c) {
+        if (h_variants) h_variants[c] = s->tuned_variant[c];
+        if (h_ms) h_ms[c] = s->tuned_ms[c];
+    }
+    return TMA_OK;
 }
 
 tma_status tma_profile_enable(tma_solver *s, int on)
@@ -567,6 +602,80 @@ tma_status tma_set_state(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step
     return TMA_OK;
 }
 
+static tma_status gen_wind(tma_solver *s, cudaStream_t st);
+
+// Choose the rollout kernel's launch-bound variant by timing every valid
+// candidate on this solver's workload (uniform initial controls, at most 8192
+// particles, all wind samples); the choice is cached per device and aircraft
+// count for the life of the process.
+static tma_status autotune_rollout(tma_solver *s)
+{
+    int cand[8];
+    const int nc = rollout_variants(s->prob.N, cand);
+    s->rollout_variant = cand[0];
+    s->n_tuned = 0;
+    if (nc <= 1) return TMA_OK;
+    const std::string key = tune_key(s);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            s->rollout_variant = it->second;
+            return TMA_OK;
+        }
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TMA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamDestroy(st);
+    };
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e);
+    }
+    tma_status r = gen_wind(s, st);
+    const int64_t Lp = std::min<int64_t>(s->prob.L, 8192);
+    float lo[3], hi[3], sg[3];
+    ctrl_f(s->prob, lo, hi, sg);
+    if (r == TMA_OK) {
+        e = launch_init_controls(s->P, s->d_dyn, lo, hi, s->d_u[0], Lp, st);
+        float best = 1e30f;
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            // one untimed launch, then three timed
+            e = launch_rollout(s->P, s->d_dyn, s->d_u[0], s->d_W, Lp, 0, s->d_cost_ms, nullptr,
+                               nullptr, st, cand[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+                e = launch_rollout(s->P, s->d_dyn, s->d_u[0], s->d_W, Lp, 0, s->d_cost_ms, nullptr,
+                                   nullptr, st, cand[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            s->tuned_variant[s->n_tuned] = cand[c];
+            s->tuned_ms[s->n_tuned] = ms / 3.0f;
+            ++s->n_tuned;
+            if (ms < best) {
+                best = ms;
+                s->rollout_variant = cand[c];
+            }
+        }
+        if (e != cudaSuccess) r = cuda_fail(e);
+    }
+    cleanup();
+    if (r == TMA_OK) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = s->rollout_variant;
+    }
+    return r;
+}
+
 static tma_status gen_wind(tma_solver *s, cudaStream_t st)
 {
     StageTimer t(s, 0, st);
@@ -583,8 +692,9 @@ tma_status tma_wind_field(tma_solver *s, float *d_W, tma_stream_t stream)
     tma_status r = gen_wind(s, st);
     if (r != TMA_OK) return r;
     if (d_W) {
-        const size_t n = (size_t)s->prob.M * s->prob.H * s->P.P * 2;
-        TMA_CUDA(cudaMemcpyAsync(d_W, s->d_W, n * 4, cudaMemcpyDeviceToDevice, st));
+        // the solver keeps float4 (own value, value one level up) per node; copy the own values
+        const size_t rows = (size_t)s->prob.M * s->prob.H * s->P.P;
+        TMA_CUDA(cudaMemcpy2DAsync(d_W, 8, s->d_W, 16, 8, rows, cudaMemcpyDeviceToDevice, st));
     }
     return TMA_OK;
 }
@@ -601,7 +711,8 @@ static tma_status rollout_into(tma_solver *s, const float *d_u, int64_t L, int32
     {
         StageTimer t(s, 2, st);
         TMA_CUDA(launch_rollout(s->P, s->d_dyn, d_u, s->d_W, L, J, s->d_cost_ms,
-                                soft ? s->d_cost_ms_soft : nullptr, s->d_live, st));
+                                soft ? s->d_cost_ms_soft : nullptr, s->d_live, st,
+                                s->rollout_variant));
     }
     {
         StageTimer t(s, 3, st);

@@ -21,10 +21,17 @@ namespace {
 constexpr float kG0 = 9.80665f;
 constexpr float kPi = 3.14159265358979323846f;
 
-// Trilinear interpolation of one wind field Wk[P] (float2 per node) at a
-// position clamped into the grid box (Sec. 3.9.1).
-__device__ __forceinline__ float2 wind_at(const ProblemC &P, const float2 *__restrict__ Wk,
-                                          float x, float y, float z)
+// Trilinear interpolation of one wind field (Sec. 3.9.1) at a position clamped
+// into the grid box: wind_fetch locates the cell and loads its four packed
+// columns (float4 per node: own (x, y) value and the value one level up),
+// wind_interp combines them.
+struct WindFetch {
+    float4 a00, a01, a10, a11;
+    float tx, ty, tz;
+};
+
+__device__ __forceinline__ WindFetch wind_fetch(const ProblemC &P, const float4 *__restrict__ Wk,
+                                                float x, float y, float z)
 {
     const float pos[3] = {x, y, z};
     int idx[3];
@@ -40,20 +47,28 @@ __device__ __forceinline__ float2 wind_at(const ProblemC &P, const float2 *__res
     const int nz = P.grid[2];
     const int nyz = P.grid[1] * nz;
     const int p = (idx[0] * P.grid[1] + idx[1]) * nz + idx[2];
-    const float2 c000 = __ldg(Wk + p), c001 = __ldg(Wk + p + 1);
-    const float2 c010 = __ldg(Wk + p + nz), c011 = __ldg(Wk + p + nz + 1);
-    const float2 c100 = __ldg(Wk + p + nyz), c101 = __ldg(Wk + p + nyz + 1);
-    const float2 c110 = __ldg(Wk + p + nyz + nz), c111 = __ldg(Wk + p + nyz + nz + 1);
-    const float tz = t[2], ty = t[1], tx = t[0];
+    WindFetch r;
+    r.a00 = __ldg(Wk + p);
+    r.a01 = __ldg(Wk + p + nz);
+    r.a10 = __ldg(Wk + p + nyz);
+    r.a11 = __ldg(Wk + p + nyz + nz);
+    r.tx = t[0];
+    r.ty = t[1];
+    r.tz = t[2];
+    return r;
+}
+
+__device__ __forceinline__ float2 wind_interp(const WindFetch &f)
+{
     float2 c00, c01, c10, c11, c0, c1, r;
-    c00.x = fmaf(tz, c001.x - c000.x, c000.x); c00.y = fmaf(tz, c001.y - c000.y, c000.y);
-    c01.x = fmaf(tz, c011.x - c010.x, c010.x); c01.y = fmaf(tz, c011.y - c010.y, c010.y);
-    c10.x = fmaf(tz, c101.x - c100.x, c100.x); c10.y = fmaf(tz, c101.y - c100.y, c100.y);
-    c11.x = fmaf(tz, c111.x - c110.x, c110.x); c11.y = fmaf(tz, c111.y - c110.y, c110.y);
-    c0.x = fmaf(ty, c01.x - c00.x, c00.x); c0.y = fmaf(ty, c01.y - c00.y, c00.y);
-    c1.x = fmaf(ty, c11.x - c10.x, c10.x); c1.y = fmaf(ty, c11.y - c10.y, c10.y);
-    r.x = fmaf(tx, c1.x - c0.x, c0.x);
-    r.y = fmaf(tx, c1.y - c0.y, c0.y);
+    c00.x = fmaf(f.tz, f.a00.z - f.a00.x, f.a00.x); c00.y = fmaf(f.tz, f.a00.w - f.a00.y, f.a00.y);
+    c01.x = fmaf(f.tz, f.a01.z - f.a01.x, f.a01.x); c01.y = fmaf(f.tz, f.a01.w - f.a01.y, f.a01.y);
+    c10.x = fmaf(f.tz, f.a10.z - f.a10.x, f.a10.x); c10.y = fmaf(f.tz, f.a10.w - f.a10.y, f.a10.y);
+    c11.x = fmaf(f.tz, f.a11.z - f.a11.x, f.a11.x); c11.y = fmaf(f.tz, f.a11.w - f.a11.y, f.a11.y);
+    c0.x = fmaf(f.ty, c01.x - c00.x, c00.x); c0.y = fmaf(f.ty, c01.y - c00.y, c00.y);
+    c1.x = fmaf(f.ty, c11.x - c10.x, c10.x); c1.y = fmaf(f.ty, c11.y - c10.y, c10.y);
+    r.x = fmaf(f.tx, c1.x - c0.x, c0.x);
+    r.y = fmaf(f.tx, c1.y - c0.y, c0.y);
     return r;
 }
 
@@ -82,10 +97,14 @@ __device__ __forceinline__ float softplus(float g, float beta, float inv_beta)
 
 constexpr int kPB = 32;   // particles per block: one warp per aircraft
 
-__global__ void __launch_bounds__(1024) rollout_kernel(const ProblemC P,
+// Launch-bound variants (block size cap, minimum resident blocks per SM): the
+// register budget per thread is 65536 / (cap * blocks); the autotuner picks
+// among the variants whose cap fits the block (32 * N threads).
+template <int kMaxThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const ProblemC P,
                                                        const DynState *__restrict__ dyn,
                                                        const float *__restrict__ u,
-                                                       const float2 *__restrict__ W, long long L,
+                                                       const float4 *__restrict__ W, long long L,
                                                        int nLb, int J, float *__restrict__ cost_ms,
                                                        float *__restrict__ cost_ms_soft,
                                                        unsigned long long *__restrict__ live)
@@ -116,7 +135,7 @@ __global__ void __launch_bounds__(1024) rollout_kernel(const ProblemC P,
     const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
     float2 turb_next = make_float2(0.0f, 0.0f);
     unsigned int nlive = 0;
-    const float2 *Wm = W + (size_t)m * P.H * P.P;
+    const float4 *Wm = W + (size_t)m * P.H * P.P;
     const bool soft_on = cost_ms_soft != nullptr;
     const int plane = N * kPB;
 
@@ -153,7 +172,7 @@ __global__ void __launch_bounds__(1024) rollout_kernel(const ProblemC P,
                 dead = true;
             } else {
                 // disturbance: wind field of sample m plus white turbulence
-                float2 w = wind_at(P, Wm + (size_t)k * P.P, x, y, z);
+                float2 w = wind_interp(wind_fetch(P, Wm + (size_t)k * P.P, x, y, z));
                 float2 n;
                 if ((k & 1) == 0) {
                     const uint4 r = draw(P.key0, P.key1, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8),
@@ -286,16 +305,42 @@ __global__ void __launch_bounds__(256) sample_mean_kernel(const float *__restric
 
 }  // namespace
 
+struct Variant {
+    int max_threads, min_blocks;
+};
+constexpr Variant kVariants[] = {{256, 4}, {256, 3}, {512, 2}, {512, 1}, {1024, 1}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int rollout_variants(int N, int *out)
+{
+    int n = 0;
+    for (int v = 0; v < kNumVariants; ++v)
+        if (kVariants[v].max_threads >= N * kPB) out[n++] = v;
+    return n;
+}
+
 cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
                            int64_t L, int J, float *cost_ms, float *cost_ms_soft,
-                           unsigned long long *live, cudaStream_t st)
+                           unsigned long long *live, cudaStream_t st, int variant)
 {
     if (L <= 0) return cudaSuccess;
+    if (variant < 0 || variant >= kNumVariants || kVariants[variant].max_threads < P.N * kPB) {
+        int cand[kNumVariants];
+        rollout_variants(P.N, cand);
+        variant = cand[0];
+    }
     const long long nLb = (L + kPB - 1) / kPB;
-    const long long grid = nLb * P.M;
+    const unsigned grid = (unsigned)(nLb * P.M);
+    const int block = P.N * kPB;
     const size_t smem = (size_t)2 * 3 * P.N * kPB * sizeof(float);
-    rollout_kernel<<<(unsigned)grid, P.N * kPB, smem, st>>>(
-        P, dyn, u, reinterpret_cast<const float2 *>(W), L, (int)nLb, J, cost_ms, cost_ms_soft, live);
+    const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    switch (variant) {
+    case 0: rollout_kernel<256, 4><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
+    case 1: rollout_kernel<256, 3><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
+    case 2: rollout_kernel<512, 2><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
+    case 3: rollout_kernel<512, 1><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
+    default: rollout_kernel<1024, 1><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -72,7 +72,10 @@ cudaError_t launch_wind_gemm(const WindC &w, const float *Lxy, int lda, const fl
 
 cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
                            int64_t L, int J, float *cost_ms, float *cost_ms_soft,
-                           unsigned long long *live, cudaStream_t st);
+                           unsigned long long *live, cudaStream_t st, int variant);
+// Launch-bound variants of the rollout kernel valid for N aircraft (indices
+// into the variant table); returns their number (at least 1).
+int rollout_variants(int N, int *out);
 cudaError_t launch_sample_mean(const float *cost_ms, int64_t L, int M, int N, float *cbar,
                                cudaStream_t st);
 
@@ -148,4 +151,9 @@ struct tma_solver {
     std::vector<cudaEvent_t> event_pool;
     double prof_ms[8] = {0};
     uint64_t prof_n[8] = {0};
+    // autotuned launch variant of the rollout kernel and the timings behind it
+    int rollout_variant = -1;
+    int n_tuned = 0;
+    int tuned_variant[8] = {0};
+    float tuned_ms[8] = {0};
 };

@@ -8,7 +8,8 @@
 // Btmp[q][((m H + k) nz + iz) 2 + c] for horizontal node q.
 // Kernel 2 applies the horizontal factor as one lower-triangular matrix
 // product over q (an FP32 register-tiled GEMM) and scatters into the
-// rollout's layout W[m][k][q][iz][c].
+// rollout's packed layout: float4 per node (its own value and the value one
+// level up), so that trilinear interpolation needs four aligned 16-byte loads.
 #include "device_common.cuh"
 #include "tma_internal.h"
 
@@ -110,18 +111,26 @@ __global__ void __launch_bounds__(256) wind_gemm_kernel(const WindC w, const flo
         }
         __syncthreads();
     }
+    // scatter into the packed layout: node q of field (m, k) holds
+    // (W_x(q), W_y(q), W_x(q + 1 level), W_y(q + 1 level)); the top level
+    // repeats its own value in the upper half (never read by interpolation)
     const int two_nz = 2 * w.nz;
+    const int P = w.nxy * w.nz;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
         const int row = row0 + ty * 8 + a;
         if (row >= w.nxy) continue;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < 8; b += 2) {
             const int col = col0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
-            if (col >= w.ncol) continue;
+            if (col >= w.ncol) continue;   // ncol is even: a pair (x, y) is never split
             const int mk = col / two_nz;
-            const int cc = col - mk * two_nz;
-            W[((size_t)mk * w.nxy + row) * two_nz + cc] = w.sigma * acc[a][b];
+            const int iz = (col - mk * two_nz) >> 1;
+            const float2 val = make_float2(w.sigma * acc[a][b], w.sigma * acc[a][b + 1]);
+            float2 *rec = reinterpret_cast<float2 *>(W + ((size_t)mk * P + (size_t)row * w.nz + iz) * 4);
+            rec[0] = val;
+            if (iz == w.nz - 1) rec[1] = val;
+            if (iz > 0) rec[-1] = val;      // upper half of the record one level below
         }
     }
 }

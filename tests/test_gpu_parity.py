@@ -141,6 +141,20 @@ def test_rollout_aircraft_counts(torch, pkg, n):
     _rollout_case(torch, pkg, p, u, 0, what=f"N={n}")
 
 
+def test_autotuner_choice_is_valid_and_cached(torch, pkg):
+    p = S.shrink(S.config2(), L=4096, M=4)
+    s1 = pkg.Solver(p)
+    v1, timed1 = pkg.tma_get_tuning(s1.h)
+    s2 = pkg.Solver(p.copy(seed=p.seed + 1))
+    v2, timed2 = pkg.tma_get_tuning(s2.h)
+    s1.close()
+    s2.close()
+    assert v1 == v2
+    if timed1:                       # timed in this process: the fastest candidate was kept
+        assert v1 in timed1 and timed1[v1] == min(timed1.values())
+        assert not timed2            # the second solver reused the cached choice
+
+
 def test_rollout_live_steps_counts_flying_aircraft(torch, pkg):
     p = S.config1()
     rng = _rng(18)
