@@ -350,7 +350,7 @@ def run_rollout_only(args, local):
 
     torch.cuda.set_device(local)
     pkg.build()
-    p = S.config2().copy(L=args.particles)
+    p = S.config2().copy(L=args.particles or 4096)
     solver = pkg.Solver(p)
     u = solver.init_controls()
     for _ in range(args.warmup):
@@ -370,6 +370,53 @@ def run_rollout_only(args, local):
     return 0
 
 
+def run_batched(args, local):
+    """Batched MPC workload: n scenarios with N_s ~ U{2..32}, L 16384, M 16,
+    H 60, J_max 20, 16x16x4 wind grid; every step = --mpc-steps receding-horizon
+    steps of all scenarios (solve + plant), captured as one CUDA graph."""
+    import numpy as np
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+    import scenarios as S
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    ps = S.config5(n_scen=args.scenarios)
+    if args.particles:
+        ps = [S.shrink(p, L=args.particles) for p in ps]
+    Ns = [p.N for p in ps]
+    b = pkg.tma_batch_create(ps)
+    units = sum(p.L * p.M * p.N * p.H * p.J_max for p in ps) * args.mpc_steps
+    stream = torch.cuda.current_stream()
+    out = {"mode": "batched", "scenarios": len(ps), "aircraft": int(sum(Ns)),
+           "mpc_steps_per_step": args.mpc_steps, "L": ps[0].L, "M": ps[0].M, "H": ps[0].H,
+           "J_max": ps[0].J_max, "metric": METRIC, "unit": UNIT}
+    for graph in (True, False):
+        for _ in range(args.warmup):
+            pkg.tma_batch_mpc(b, args.mpc_steps, use_graph=graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lat = []
+        ms_total = 0.0
+        for _ in range(args.steps):
+            e0.record(stream)
+            pkg.tma_batch_mpc(b, args.mpc_steps, use_graph=graph)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_total += e0.elapsed_time(e1)
+            lat.append(pkg.tma_batch_latency(b, len(ps)))
+        lat = np.concatenate(lat)
+        key = "graph" if graph else "eager"
+        out[key] = {"value": units * args.steps / (ms_total * 1e-3), "ms_per_step": ms_total / args.steps,
+                    "solve_latency_ms_p50": float(np.percentile(lat, 50)),
+                    "solve_latency_ms_p99": float(np.percentile(lat, 99))}
+    out["live_steps_last_solve"] = pkg.tma_batch_live_steps(b)
+    pkg.tma_batch_destroy(b)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,11 +428,18 @@ def main(argv=None):
     ap.add_argument("--reference-particles", type=int, default=64)
     ap.add_argument("--rollout-only", action="store_true",
                     help="time only the rollout on --particles particles (profiling case)")
-    ap.add_argument("--particles", type=int, default=4096)
+    ap.add_argument("--particles", type=int, default=0,
+                    help="particles of the profiling / batched cases (0: the workload's own)")
+    ap.add_argument("--batched", action="store_true",
+                    help="time the batched MPC workload (graph-captured receding-horizon steps)")
+    ap.add_argument("--scenarios", type=int, default=256)
+    ap.add_argument("--mpc-steps", type=int, default=10)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.rollout_only:
         return run_rollout_only(args, local)
+    if args.batched:
+        return run_batched(args, local)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local)

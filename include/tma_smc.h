@@ -200,6 +200,55 @@ typedef struct {
 tma_status tma_profile_enable(tma_solver *s, int on);
 tma_status tma_profile_read(tma_solver *s, tma_profile *h_out, int reset);
 
+/* ------------------------------------------------------------ MPC plant */
+
+/* The plant of Fig. 1 (Sec. 2): every aircraft flies the first-segment controls
+ * d_u[N][S][3] (device; only segment 0 is used) for one step dt from the
+ * solver's current state, under the wind field of sample 0 at step 0 plus white
+ * turbulence from random stream 7, thrust held within [Tmin, Tmax].  The new
+ * state replaces the solver's state on the device and the MPC step advances by
+ * one (the next solve draws new random numbers).  Syncs the stream. */
+tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream);
+/* The solver's current state h_x[N] (host) and MPC step; syncs. */
+tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream);
+
+/* --------------------------------------------------------------- batches */
+
+/* Many independent TMA scenarios solved together (receding-horizon MPC per
+ * scenario, Sec. 2; Algorithm 1 each).  Scenarios may differ in aircraft
+ * (N_s = 1..32, states, targets, coefficients), weights, control box and
+ * seeds; they must share L, M, H, S, J_max, dt, sep_mode and the wind model
+ * (grid, box, rates, sigma).  Weight segments are (scenario, aircraft) pairs,
+ * at most 65535 in total.  aircraft[s] points to probs[s].N records.
+ * The rollout of all scenarios is one persistent launch over a work queue. */
+typedef struct tma_batch tma_batch;
+tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const *aircraft,
+                            int32_t n_scen, tma_batch **out);
+void tma_batch_destroy(tma_batch *b);
+/* States h_x0 (sum of N_s entries, scenario-major; NULL keeps the device
+ * states) and MPC steps h_mpc[n_scen] (NULL keeps them); syncs. */
+tma_status tma_batch_set_state(tma_batch *b, const tma_state *h_x0, const uint32_t *h_mpc,
+                               tma_stream_t stream);
+/* One SMC solve of every scenario from its current state (device only). */
+tma_status tma_batch_solve(tma_batch *b, tma_stream_t stream);
+/* n_steps receding-horizon steps: each solves every scenario, then the plant
+ * advances every scenario by one step with its chosen first control (as
+ * tma_plant_step).  With use_graph != 0 the whole sequence is captured once
+ * into a CUDA graph (re-captured when n_steps changes) and launched; the
+ * results equal those without the graph. */
+tma_status tma_batch_mpc(tma_batch *b, int32_t n_steps, int32_t use_graph, tma_stream_t stream);
+/* Results of the last solve: chosen controls h_best_u (sum N_s x S x 3,
+ * scenario-major), cost sums h_best_cost[n_scen], particle indices
+ * h_best[n_scen]; current states h_x (sum N_s) and MPC steps h_mpc[n_scen].
+ * Any pointer may be NULL; syncs. */
+tma_status tma_batch_results(tma_batch *b, float *h_best_u, double *h_best_cost, int64_t *h_best,
+                             tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream);
+/* Per-scenario solve latency of the last solve in ms: device clock from the
+ * start of the solve to the end of that scenario's selection; syncs. */
+tma_status tma_batch_latency(tma_batch *b, double *h_ms, tma_stream_t stream);
+/* Simulated aircraft-steps of the last batched solve (all rollouts); syncs. */
+tma_status tma_batch_live_steps(tma_batch *b, uint64_t *h_live, tma_stream_t stream);
+
 /* ------------------------------------------------------ stateless stages */
 
 /* Annealed log-weights and their FP64 normalisation per segment (Sec. 3.6,

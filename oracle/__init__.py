@@ -87,6 +87,7 @@ def lib():
                                          P(i64), i32, i32, i32, P(d), P(d), P(d), P(d), P(i64)]
             _lib.orc_trajectory.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), i32, P(d), i64,
                                             i32, P(d), P(d), P(d)]
+            _lib.orc_plant_step.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), P(d), P(d)]
             _lib.orc_kappa.argtypes = [i32]
             _lib.orc_kappa.restype = i32
             _lib.orc_lse.argtypes = [P(d), i32, i32, d, P(d), P(d), P(d)]
@@ -339,6 +340,20 @@ def trajectory(p, u_l, W_m, l=0, m=0, J=0):
     lib().orc_trajectory(mm.ps, mm.ac, _ptr(Wm, C.c_double), m, _ptr(u, C.c_double), l, J,
                          _ptr(traj, C.c_double), _ptr(ch, C.c_double), _ptr(cs, C.c_double))
     return traj, ch, cs
+
+
+def plant_step(p, x, W0, u0):
+    """One step of the true system (Sec. 2, Fig. 1): states x[N][6] (x, y, z,
+    v, chi, m), wind field W0[P][2] of sample 0 at step 0, first-segment
+    controls u0[N][3]; returns the new states."""
+    xi = np.ascontiguousarray(x, np.float64).reshape(p.N, 6)
+    W = np.ascontiguousarray(W0, np.float64).reshape(p.n_grid, 2)
+    uu = np.ascontiguousarray(u0, np.float64).reshape(p.N, 3)
+    out = np.empty_like(xi)
+    mm = _Marshalled(p)
+    lib().orc_plant_step(mm.ps, mm.ac, _ptr(xi, C.c_double), _ptr(W, C.c_double),
+                         _ptr(uu, C.c_double), _ptr(out, C.c_double))
+    return out
 
 
 # ----------------------------------------------------------------------

@@ -509,6 +509,55 @@ void orc_trajectory(const orc_problem *P, const orc_aircraft *A, const double *W
 }
 
 /* ------------------------------------------------------------------ */
+/* the plant of the MPC loop (Sec. 2, Fig. 1)                            */
+/* ------------------------------------------------------------------ */
+
+/* One step dt of the true system under the first-segment controls u0[N][3]:
+ * Eq. (hor) with the climb angle kept below 90 degrees (|sin gamma| <= 0.999)
+ * and the thrust held within [Tmin, Tmax]; disturbance = wind field W0[P][2]
+ * (sample 0, step 0) plus white turbulence from random stream 7. */
+void orc_plant_step(const orc_problem *P, const orc_aircraft *A, const double *x_in,
+                    const double *W0, const double *u0, double *x_out)
+{
+    for (int i = 0; i < P->N; i++) {
+        const orc_aircraft *a = &A[i];
+        const double *s = x_in + 6 * i;
+        double x = s[0], y = s[1], z = s[2], v = s[3], chi = s[4], m = s[5];
+        double w = u0[3 * i], hd = u0[3 * i + 1], acc = u0[3 * i + 2];
+        double sg = hd / v;
+        if (sg > 0.999) sg = 0.999;
+        if (sg < -0.999) sg = -0.999;
+        double cg = sqrt(1.0 - sg * sg);
+        double tp = w * v / (G0 * cg);
+        double cphi = 1.0 / sqrt(1.0 + tp * tp), sphi = tp * cphi;
+        double base = 1.0 - 2.2558e-5 * z;
+        double rho = 1.225 * pow(base > 0.0 ? base : 0.0, 4.2559);
+        double qS = 0.5 * rho * v * v * a->S;
+        double CL = m * G0 * cg / (qS * cphi);
+        double D = qS * (a->CD0 + a->CD2 * CL * CL);
+        double T = m * (acc + G0 * sg) + D;
+        if (T < a->Tmin) T = a->Tmin;
+        if (T > a->Tmax) T = a->Tmax;
+        double Lift = CL * qS, eta = a->Cf1 * (1.0 + v / a->Cf2);
+        double wx, wy;
+        trilinear(P, W0, x, y, z, &wx, &wy);
+        uint32_t tb[4];
+        orc_draw(P, 0u, (uint32_t)i, 0u, 7u, 0u, tb);
+        double n0, n1;
+        orc_box_muller(tb[0], tb[1], &n0, &n1);
+        wx += P->turb_sigma * n0;
+        wy += P->turb_sigma * n1;
+        double *o = x_out + 6 * i;
+        o[0] = x + P->dt * (v * cos(chi) * cg) + wx * P->dt;
+        o[1] = y + P->dt * (v * sin(chi) * cg) + wy * P->dt;
+        o[2] = z + P->dt * (v * sg);
+        o[3] = v + P->dt * ((T - D) / m - G0 * sg);
+        o[4] = chi + P->dt * (Lift * sphi / (m * v));
+        o[5] = m - P->dt * (eta * T);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* weights (Sec. 3.6 with the schedule of Sec. 5.1)                      */
 /* ------------------------------------------------------------------ */
 

@@ -90,6 +90,11 @@ void orc_trajectory(const orc_problem *P, const orc_aircraft *A, const double *W
                     const double *ul, int64_t l, int J, double *traj, double *cost_hard,
                     double *cost_soft);
 
+/* One step of the true system (plant of the MPC loop): x_in/x_out[N][6]
+ * (x, y, z, v, chi, m), W0 = wind field of sample 0 at step 0, u0[N][3]. */
+void orc_plant_step(const orc_problem *P, const orc_aircraft *A, const double *x_in,
+                    const double *W0, const double *u0, double *x_out);
+
 /* Annealed log-weights and their segment-wise normalisation. */
 int orc_kappa(int J);
 void orc_lse(const double *cbar, int nseg, int L, double kappa, double *wtilde, double *lmax,

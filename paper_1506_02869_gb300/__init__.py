@@ -31,7 +31,9 @@ EXPORTS = [
     "tma_move", "tma_init_controls", "tma_solve", "tma_solve_host", "tma_best_index",
     "tma_lse_workspace", "tma_lse", "tma_resample_workspace", "tma_resample",
     "tma_select_workspace", "tma_select", "tma_profile_enable", "tma_profile_read",
-    "tma_resample_noalloc", "tma_get_tuning",
+    "tma_resample_noalloc", "tma_get_tuning", "tma_plant_step", "tma_get_state",
+    "tma_batch_create", "tma_batch_destroy", "tma_batch_set_state", "tma_batch_solve",
+    "tma_batch_mpc", "tma_batch_results", "tma_batch_latency", "tma_batch_live_steps",
 ]
 
 
@@ -122,6 +124,16 @@ def lib():
                 "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_profile_enable": ([vp, C.c_int], C.c_int),
                 "tma_get_tuning": ([vp, P(i32), P(i32), P(i32), P(C.c_float)], C.c_int),
+                "tma_plant_step": ([vp, vp, st], C.c_int),
+                "tma_get_state": ([vp, P(TmaState), P(u32), st], C.c_int),
+                "tma_batch_create": ([P(TmaProblem), P(P(TmaAircraft)), i32, P(vp)], C.c_int),
+                "tma_batch_destroy": ([vp], None),
+                "tma_batch_set_state": ([vp, P(TmaState), P(u32), st], C.c_int),
+                "tma_batch_solve": ([vp, st], C.c_int),
+                "tma_batch_mpc": ([vp, i32, i32, st], C.c_int),
+                "tma_batch_results": ([vp, vp, P(d), P(i64), P(TmaState), P(u32), st], C.c_int),
+                "tma_batch_latency": ([vp, P(d), st], C.c_int),
+                "tma_batch_live_steps": ([vp, P(u64), st], C.c_int),
                 "tma_resample_noalloc": ([vp, i32, i64, u64, u32, u32, u32, vp, st], C.c_int),
                 "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
             }
@@ -318,6 +330,86 @@ def tma_profile_read(h, reset=True):
     prof = TmaProfile()
     _check(lib().tma_profile_read(h, C.byref(prof), int(bool(reset))), "tma_profile_read")
     return {name: (prof.ms[k], prof.launches[k]) for k, name in enumerate(STAGES)}
+
+
+# ------------------------------------------------------------- MPC plant
+
+def tma_plant_step(h, u, stream=None):
+    """Advance the solver's true state by one step with the segment-0 controls of
+    u (cuda float32 [N][S][3])."""
+    _check(lib().tma_plant_step(h, _dptr(u), _stream(stream)), "tma_plant_step")
+
+
+def tma_get_state(h, N, stream=None):
+    """(states [N][6] as numpy, MPC step) of the solver."""
+    arr = (TmaState * N)()
+    mpc = C.c_uint32()
+    _check(lib().tma_get_state(h, arr, C.byref(mpc), _stream(stream)), "tma_get_state")
+    return np.array([[a.x, a.y, a.z, a.v, a.chi, a.m] for a in arr]), mpc.value
+
+
+# ----------------------------------------------------------------- batches
+
+def tma_batch_create(problems):
+    """One batch handle for a list of problems sharing sizes and wind model."""
+    structs = [problem_struct(p) for p in problems]
+    n = len(structs)
+    parr = (TmaProblem * n)(*[s for s, _, _ in structs])
+    aptrs = (C.POINTER(TmaAircraft) * n)(*[C.cast(a, C.POINTER(TmaAircraft)) for _, a, _ in structs])
+    h = C.c_void_p()
+    _check(lib().tma_batch_create(parr, aptrs, n, C.byref(h)), "tma_batch_create")
+    return h
+
+
+def tma_batch_destroy(h):
+    if h:
+        lib().tma_batch_destroy(h)
+
+
+def tma_batch_set_state(h, x0=None, mpc=None, stream=None):
+    arr = states_struct(x0) if x0 is not None else None
+    m = (C.c_uint32 * len(mpc))(*[int(v) for v in mpc]) if mpc is not None else None
+    _check(lib().tma_batch_set_state(h, arr, m, _stream(stream)), "tma_batch_set_state")
+
+
+def tma_batch_solve(h, stream=None):
+    _check(lib().tma_batch_solve(h, _stream(stream)), "tma_batch_solve")
+
+
+def tma_batch_mpc(h, n_steps, use_graph=True, stream=None):
+    _check(lib().tma_batch_mpc(h, int(n_steps), int(bool(use_graph)), _stream(stream)), "tma_batch_mpc")
+
+
+def tma_batch_results(h, Ns, S, stream=None):
+    """dict with best_u (list of [N_s][S][3]), best_cost [n], best [n], states
+    (list of [N_s][6]) and mpc [n]."""
+    n, tot = len(Ns), int(sum(Ns))
+    bu = np.empty((tot, S, 3), np.float32)
+    bc = np.empty(n, np.float64)
+    bi = np.empty(n, np.int64)
+    xs = (TmaState * tot)()
+    mp = np.empty(n, np.uint32)
+    _check(lib().tma_batch_results(h, bu.ctypes.data_as(C.c_void_p), bc.ctypes.data_as(C.POINTER(C.c_double)),
+                                   bi.ctypes.data_as(C.POINTER(C.c_int64)), xs,
+                                   mp.ctypes.data_as(C.POINTER(C.c_uint32)), _stream(stream)),
+           "tma_batch_results")
+    st = np.array([[a.x, a.y, a.z, a.v, a.chi, a.m] for a in xs])
+    offs = np.r_[0, np.cumsum(Ns)]
+    return {"best_u": [bu[offs[k]:offs[k + 1]] for k in range(n)], "best_cost": bc, "best": bi,
+            "states": [st[offs[k]:offs[k + 1]] for k in range(n)], "mpc": mp}
+
+
+def tma_batch_latency(h, n, stream=None):
+    out = np.empty(n, np.float64)
+    _check(lib().tma_batch_latency(h, out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)),
+           "tma_batch_latency")
+    return out
+
+
+def tma_batch_live_steps(h, stream=None):
+    v = C.c_uint64()
+    _check(lib().tma_batch_live_steps(h, C.byref(v), _stream(stream)), "tma_batch_live_steps")
+    return v.value
 
 
 # --------------------------------------------------------- stateless stages

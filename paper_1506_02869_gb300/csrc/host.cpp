@@ -189,10 +189,10 @@ static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
     return TMA_OK;
 }
 
-static void derive(tma_solver *s)
+static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraft,
+                               const float *d_popdense)
 {
-    const tma_problem &p = s->prob;
-    ProblemC &P = s->P;
+    ProblemC P;
     std::memset(&P, 0, sizeof P);
     P.N = p.N;
     P.H = p.H;
@@ -210,6 +210,7 @@ static void derive(tma_solver *s)
     P.turb_sigma = (float)p.turb_sigma;
     P.sgmax = (float)std::sin(p.gamma_max);
     P.tpmax = (float)std::tan(p.phi_max);
+    P.climb_step = (float)(p.v_max * std::sin(p.gamma_max) * p.dt);
     P.Sh2 = (float)(p.sep_h * p.sep_h);
     P.Sh_inv = (float)(1.0 / p.sep_h);
     P.Sv = (float)p.sep_v;
@@ -226,7 +227,7 @@ static void derive(tma_solver *s)
     for (int j = 0; j < 3; ++j) P.a_arr[j] = (float)p.alpha_arr[j];
     P.w_noise = (float)p.w_noise;
     P.Ac_inv = (float)(p.A_c > 0 ? 1.0 / p.A_c : 0.0);
-    P.popdense = s->d_popdense;
+    P.popdense = d_popdense;
     for (int d = 0; d < 2; ++d) {
         P.pop_n[d] = p.pop_n[d];
         P.pop_lo[d] = (float)p.pop_lo[d];
@@ -241,9 +242,8 @@ static void derive(tma_solver *s)
     const uint64_t key = p.seed + (uint64_t)p.scenario_id * 0x9E3779B97F4A7C15ull;
     P.key0 = (uint32_t)key;
     P.key1 = (uint32_t)(key >> 32);
-    const double sgmax = std::sin(p.gamma_max);
     for (int i = 0; i < p.N; ++i) {
-        const tma_aircraft &a = s->aircraft[i];
+        const tma_aircraft &a = aircraft[i];
         AircraftC &c = P.ac[i];
         c.type = a.type;
         c.halfS = (float)(0.5 * a.S);
@@ -259,19 +259,14 @@ static void derive(tma_solver *s)
         c.vD = (float)a.v_D;
         const double Fmax = p.H * p.dt * a.Tmax * a.Cf1 * (1.0 + p.v_max / a.Cf2);
         c.invFmax = (float)(1.0 / Fmax);
-        // departure altitude term: per-step means of d0 +/- k dt vmax sin(gamma_max)
-        const double d0 = std::fabs(a.Z - a.x0.z), cl = p.v_max * sgmax * p.dt;
-        double sup = 0.0, inf = 0.0;
-        for (int k = 1; k <= p.H; ++k) {
-            sup += d0 + k * cl;
-            inf += std::max(d0 - k * cl, 0.0);
-        }
-        sup /= p.H;
-        inf /= p.H;
-        c.supB = (float)sup;
-        c.invSupInf = (float)(1.0 / (sup - inf));
         c.invCmax = (float)(1.0 / std::max(p.v_max - a.v_D, a.v_D - p.v_min));
     }
+    return P;
+}
+
+static void derive(tma_solver *s)
+{
+    s->P = derive_problem(s->prob, s->aircraft.data(), s->d_popdense);
 }
 
 static void upload_x0(tma_solver *s, DynState &d)
@@ -294,7 +289,7 @@ static void free_all(tma_solver *s)
     void *ptrs[] = {s->d_dyn, s->d_Lxy, s->d_Btmp, s->d_W, s->d_u[0], s->d_u[1], s->d_cost_ms,
                     s->d_cost_ms_soft, s->d_cbar, s->d_cbar_soft, s->d_wtilde, s->d_anc,
                     s->d_popdense, s->d_work, s->d_best, s->d_best_sum, s->d_ninf, s->d_flags,
-                    s->d_live, s->d_best_u};
+                    s->d_live, s->d_best_u, s->d_probs1, s->d_scen1, s->d_seg_scen1};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -592,11 +587,16 @@ tma_status tma_set_state(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step
         derive(s);   // departure altitude normalisation depends on the initial altitude
     }
     s->mpc_step = mpc_step;
-    // a pageable-memory copy would be unsafe to reuse before it runs; stage it
-    // through a per-call host buffer that the stream finishes before return
-    DynState d;
-    upload_x0(s, d);
-    TMA_CUDA(cudaMemcpyAsync(s->d_dyn, &d, sizeof d, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    if (h_x0) {
+        DynState d;
+        upload_x0(s, d);
+        TMA_CUDA(cudaMemcpyAsync(s->d_dyn, &d, sizeof d, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    } else {
+        // keep the device state (it may have been advanced by tma_plant_step)
+        TMA_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(s->d_dyn) + offsetof(DynState, mpc_step),
+                                 &mpc_step, sizeof mpc_step, cudaMemcpyHostToDevice,
+                                 (cudaStream_t)stream));
+    }
     TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     s->wind_ready = false;
     return TMA_OK;
@@ -936,6 +936,442 @@ tma_status tma_select(const float *d_cbar, int32_t N, int64_t L, int64_t *d_best
     if (N < 1 || L < 1 || !d_cbar || !d_best || !d_work || work_bytes < select_workspace(L))
         return TMA_ERR_INVALID_ARG;
     TMA_CUDA(launch_select(d_cbar, N, L, d_best, d_best_sum, d_ninf, d_work, (cudaStream_t)stream));
+    return TMA_OK;
+}
+
+
+// --------------------------------------------------------------- MPC plant
+
+tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream)
+{
+    if (!s || !d_u) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!s->d_probs1) {
+        cudaError_t e = alloc(&s->d_probs1, sizeof(ProblemC));
+        if (!e) e = alloc(&s->d_scen1, sizeof(BatchScen));
+        if (!e) e = alloc(&s->d_seg_scen1, sizeof(int) * TMA_MAX_AIRCRAFT);
+        if (!e) e = cudaMemset(s->d_seg_scen1, 0, sizeof(int) * TMA_MAX_AIRCRAFT);
+        if (e) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : cuda_fail(e);
+    }
+    if (!s->wind_ready) {
+        tma_status r = gen_wind(s, st);
+        if (r != TMA_OK) return r;
+    }
+    BatchScen sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.N = s->prob.N;
+    TMA_CUDA(cudaMemcpyAsync(s->d_probs1, &s->P, sizeof(ProblemC), cudaMemcpyHostToDevice, st));
+    TMA_CUDA(cudaMemcpyAsync(s->d_scen1, &sc, sizeof sc, cudaMemcpyHostToDevice, st));
+    TMA_CUDA(launch_plant_step(s->d_probs1, s->d_scen1, s->d_seg_scen1, s->prob.N, 1, s->d_dyn,
+                               s->d_W, d_u, s->prob.S, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    s->mpc_step += 1;
+    s->wind_ready = false;
+    return TMA_OK;
+}
+
+tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    DynState d;
+    TMA_CUDA(cudaMemcpyAsync(&d, s->d_dyn, sizeof d, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int i = 0; h_x && i < s->prob.N; ++i) {
+        h_x[i].x = d.x0[i][0];
+        h_x[i].y = d.x0[i][1];
+        h_x[i].z = d.x0[i][2];
+        h_x[i].v = d.x0[i][3];
+        h_x[i].chi = d.x0[i][4];
+        h_x[i].m = d.x0[i][5];
+    }
+    if (h_mpc) *h_mpc = d.mpc_step;
+    return TMA_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+static void batch_free(tma_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    void *ptrs[] = {b->d_probs, b->d_scen, b->d_seg_scen, b->d_segkeys, b->d_dyns, b->d_Lxy,
+                    b->d_Btmp, b->d_W, b->d_u[0], b->d_u[1], b->d_cost_ms, b->d_cost_ms_soft,
+                    b->d_cbar, b->d_cbar_soft, b->d_wtilde, b->d_anc, b->d_work, b->d_best,
+                    b->d_best_sum, b->d_ninf, b->d_best_u, b->d_t_start, b->d_t_end, b->d_live,
+                    b->d_queue, b->d_flags};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (float *p : b->d_pops)
+        if (p) cudaFree(p);
+}
+
+static bool same_shape(const tma_problem &a, const tma_problem &b)
+{
+    bool ok = a.L == b.L && a.M == b.M && a.H == b.H && a.S == b.S && a.J_max == b.J_max &&
+              a.dt == b.dt && a.beta_xy == b.beta_xy && a.gam_z == b.gam_z && a.lam_t == b.lam_t &&
+              a.wind_sigma == b.wind_sigma && a.sep_mode == b.sep_mode;
+    for (int d = 0; d < 3; ++d)
+        ok = ok && a.grid[d] == b.grid[d] && a.box_lo[d] == b.box_lo[d] && a.box_hi[d] == b.box_hi[d];
+    return ok;
+}
+
+static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
+{
+    const long long L = b->L;
+    const size_t P = (size_t)b->probs[0].grid[0] * b->probs[0].grid[1] * b->probs[0].grid[2];
+    TMA_CUDA(launch_stamp_start(b->d_t_start, st));
+    for (size_t g = 0; g < b->wind_groups.size(); ++g) {
+        const WindC &w = b->wind_groups[g];
+        const int s0 = b->group_start[g];
+        TMA_CUDA(launch_batch_wind_normals(w, s0, b->M, b->d_scen, b->d_dyns, b->d_Btmp, st));
+        TMA_CUDA(launch_wind_gemm(w, b->d_Lxy, b->lda, b->d_Btmp,
+                                  b->d_W + (size_t)s0 * b->M * b->H * P * 4, st));
+    }
+    TMA_CUDA(launch_batch_init(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, L, b->S, b->d_u[0], st));
+    TMA_CUDA(cudaMemsetAsync(b->d_flags, 0, 4, st));
+    TMA_CUDA(cudaMemsetAsync(b->d_live, 0, 8, st));
+    int cur = 0;
+    const bool soft = b->sep_mode != 0;
+    float *cb = b->sep_mode == 1 ? b->d_cbar_soft : b->d_cbar;
+    for (int J = 0; J < b->J_max; ++J) {
+        TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->n_items, b->d_dyns,
+                                      b->d_u[cur], b->d_W, L, J, b->d_cost_ms,
+                                      soft ? b->d_cost_ms_soft : nullptr, b->d_live, b->d_queue,
+                                      b->grid, st));
+        TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms, b->d_scen, b->d_seg_scen, b->nseg, L, b->M,
+                                          b->d_cbar, st));
+        if (soft)
+            TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms_soft, b->d_scen, b->d_seg_scen, b->nseg, L,
+                                              b->M, b->d_cbar_soft, st));
+        if (J < b->J_max - 1) {
+            TMA_CUDA(launch_lse(cb, (int)b->nseg, L, (double)kappa_of(J), b->d_wtilde, nullptr,
+                                nullptr, b->d_work, st));
+            TMA_CUDA(launch_resample(b->d_wtilde, (int)b->nseg, L, 0u, 0u, (uint32_t)J, nullptr, 0u,
+                                     b->d_anc, b->d_work, b->d_flags, st, b->d_segkeys, b->d_dyns));
+            TMA_CUDA(launch_batch_move(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, L, b->S,
+                                       b->d_u[cur], b->d_anc, J, b->d_u[cur ^ 1], st));
+            cur ^= 1;
+        }
+    }
+    TMA_CUDA(launch_batch_select(b->d_scen, b->n_scen, cb, L, b->S, b->d_u[cur], b->d_best,
+                                 b->d_best_sum, b->d_ninf, b->d_best_u, b->d_t_end, st));
+    b->final_u = cur;
+    return TMA_OK;
+}
+
+static tma_status batch_mpc_steps(tma_batch *b, int n_steps, cudaStream_t st)
+{
+    for (int n = 0; n < n_steps; ++n) {
+        tma_status r = batch_solve_device(b, st);
+        if (r != TMA_OK) return r;
+        TMA_CUDA(launch_plant_step(b->d_probs, b->d_scen, b->d_seg_scen, b->nseg, b->n_scen,
+                                   b->d_dyns, b->d_W, b->d_best_u, b->S, st));
+    }
+    return TMA_OK;
+}
+
+tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const *aircraft,
+                            int32_t n_scen, tma_batch **out)
+{
+    if (!out || !probs || !aircraft || n_scen < 1 || n_scen > (1 << 20)) return TMA_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int s = 0; s < n_scen; ++s) {
+        tma_status v = validate(&probs[s], aircraft[s]);
+        if (v != TMA_OK) return v;
+        if (!same_shape(probs[0], probs[s])) return TMA_ERR_INVALID_ARG;
+    }
+    tma_batch *b = nullptr;
+    try {
+        b = new tma_batch();
+        cudaGetDevice(&b->device);
+        const tma_problem &p0 = probs[0];
+        b->n_scen = n_scen;
+        b->L = p0.L;
+        b->M = p0.M;
+        b->H = p0.H;
+        b->S = p0.S;
+        b->J_max = p0.J_max;
+        b->sep_mode = p0.sep_mode;
+        const int nx = p0.grid[0], ny = p0.grid[1], nz = p0.grid[2], nxy = nx * ny;
+        const size_t P = (size_t)nxy * nz;
+        const long long nLb = ((long long)p0.L + kTileParticles - 1) / kTileParticles;
+        auto fail = [&](cudaError_t e) {
+            batch_free(b);
+            delete b;
+            return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : cuda_fail(e);
+        };
+        cudaError_t e;
+        std::vector<ProblemC> pc(n_scen);
+        std::vector<SegKey> segkeys;
+        long long u_off = 0, items = 0;
+        for (int s = 0; s < n_scen; ++s) {
+            const tma_problem &p = probs[s];
+            b->probs.push_back(p);
+            b->aircraft.emplace_back(aircraft[s], aircraft[s] + p.N);
+            float *dpop = nullptr;
+            if (p.pop_n[0] >= 2) {
+                std::vector<float> pf(p.popdense, p.popdense + (size_t)p.pop_n[0] * p.pop_n[1]);
+                if ((e = alloc(&dpop, pf.size() * 4))) return fail(e);
+                b->d_pops.push_back(dpop);
+                if ((e = cudaMemcpy(dpop, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice))) return fail(e);
+            }
+            b->probs.back().popdense = nullptr;
+            pc[s] = derive_problem(p, aircraft[s], dpop);
+            BatchScen sc;
+            std::memset(&sc, 0, sizeof sc);
+            sc.u_off = u_off;
+            sc.seg_off = b->nseg;
+            sc.w_off = (long long)s * p.M * p.H * (long long)P;
+            sc.N = p.N;
+            sc.T = 32 / p.N;
+            sc.items = (long long)p.M * ((nLb + sc.T - 1) / sc.T);
+            sc.item_off = items;
+            for (int c = 0; c < 3; ++c) {
+                sc.ctrl_lo[c] = (float)p.ctrl_lo[c];
+                sc.ctrl_hi[c] = (float)p.ctrl_hi[c];
+                sc.move_sigma[c] = (float)p.move_sigma[c];
+            }
+            sc.key0 = pc[s].key0;
+            sc.key1 = pc[s].key1;
+            b->scen.push_back(sc);
+            for (int i = 0; i < p.N; ++i) {
+                b->seg_scen.push_back(s);
+                segkeys.push_back(SegKey{sc.key0, sc.key1, (uint32_t)i, s});
+            }
+            DynState d;
+            std::memset(&d, 0, sizeof d);
+            for (int i = 0; i < p.N; ++i) {
+                const tma_state &x = aircraft[s][i].x0;
+                d.x0[i][0] = (float)x.x;
+                d.x0[i][1] = (float)x.y;
+                d.x0[i][2] = (float)x.z;
+                d.x0[i][3] = (float)x.v;
+                d.x0[i][4] = (float)x.chi;
+                d.x0[i][5] = (float)x.m;
+            }
+            d.mpc_step = p.mpc_step;
+            b->dyn_h.push_back(d);
+            u_off += (long long)p.L * p.N * p.S * 3;
+            items += sc.items;
+            b->nseg += p.N;
+        }
+        b->n_items = items;
+        if (b->nseg > 65535) {
+            batch_free(b);
+            delete b;
+            return TMA_ERR_INVALID_ARG;   // one resampling block row per segment
+        }
+        // wind factors shared by all scenarios (same grid and rates)
+        auto lxy = horizontal_factor(p0);
+        std::vector<double> Rz((size_t)nz * nz);
+        for (int a = 0; a < nz; ++a)
+            for (int c = 0; c <= a; ++c) {
+                const double za = p0.box_lo[2] + (p0.box_hi[2] - p0.box_lo[2]) * a / (nz - 1);
+                const double zc = p0.box_lo[2] + (p0.box_hi[2] - p0.box_lo[2]) * c / (nz - 1);
+                Rz[(size_t)a * nz + c] = std::exp(-p0.gam_z * std::fabs(za - zc));
+            }
+        if (!lxy || !cholesky_lower(Rz, nz)) {
+            batch_free(b);
+            delete b;
+            return TMA_ERR_INVALID_ARG;
+        }
+        b->lda = lxy->lda;
+        const long long per_scen = (long long)p0.M * p0.H * 2 * nz;
+        int gsz = (int)std::max(1LL, std::min(64LL, (1LL << 28) / ((long long)b->lda * per_scen)));
+        gsz = std::min(gsz, n_scen);
+        const int max_ldb = (int)(((gsz * per_scen) + 127) / 128 * 128);
+        const double a = std::exp(-p0.dt * p0.lam_t);
+        for (int s0 = 0; s0 < n_scen; s0 += gsz) {
+            const int nsc = std::min(gsz, n_scen - s0);
+            WindC w;
+            std::memset(&w, 0, sizeof w);
+            w.M = nsc * p0.M;
+            w.H = p0.H;
+            w.nxy = nxy;
+            w.nz = nz;
+            w.ncol = (int)(nsc * per_scen);
+            w.ldb = max_ldb;
+            w.a = (float)a;
+            w.b = (float)std::sqrt(std::max(0.0, 1.0 - a * a));
+            w.sigma = (float)p0.wind_sigma;
+            for (int r = 0; r < nz; ++r)
+                for (int c = 0; c <= r; ++c) w.Lz[r * TMA_MAX_GRID_Z + c] = (float)Rz[(size_t)r * nz + c];
+            b->wind_groups.push_back(w);
+            b->group_start.push_back(s0);
+        }
+        const size_t L = (size_t)p0.L, M = (size_t)p0.M, nseg = (size_t)b->nseg;
+        if ((e = alloc(&b->d_probs, sizeof(ProblemC) * n_scen))) return fail(e);
+        if ((e = alloc(&b->d_scen, sizeof(BatchScen) * n_scen))) return fail(e);
+        if ((e = alloc(&b->d_seg_scen, sizeof(int) * nseg))) return fail(e);
+        if ((e = alloc(&b->d_segkeys, sizeof(SegKey) * nseg))) return fail(e);
+        if ((e = alloc(&b->d_dyns, sizeof(DynState) * n_scen))) return fail(e);
+        if ((e = alloc(&b->d_Lxy, lxy->L.size() * 4))) return fail(e);
+        if ((e = alloc(&b->d_Btmp, (size_t)b->lda * max_ldb * 4))) return fail(e);
+        if ((e = cudaMemset(b->d_Btmp, 0, (size_t)b->lda * max_ldb * 4))) return fail(e);
+        if ((e = alloc(&b->d_W, (size_t)n_scen * M * p0.H * P * 16))) return fail(e);
+        if ((e = alloc(&b->d_u[0], (size_t)u_off * 4))) return fail(e);
+        if ((e = alloc(&b->d_u[1], (size_t)u_off * 4))) return fail(e);
+        if ((e = alloc(&b->d_cost_ms, M * nseg * L * 4))) return fail(e);
+        if (b->sep_mode && (e = alloc(&b->d_cost_ms_soft, M * nseg * L * 4))) return fail(e);
+        if ((e = alloc(&b->d_cbar, nseg * L * 4))) return fail(e);
+        if (b->sep_mode && (e = alloc(&b->d_cbar_soft, nseg * L * 4))) return fail(e);
+        if ((e = alloc(&b->d_wtilde, nseg * L * 8))) return fail(e);
+        if ((e = alloc(&b->d_anc, nseg * L * 4))) return fail(e);
+        if ((e = alloc(&b->d_work, std::max(lse_workspace((int)nseg, L), resample_workspace((int)nseg, L)))))
+            return fail(e);
+        if ((e = alloc(&b->d_best, 8 * (size_t)n_scen))) return fail(e);
+        if ((e = alloc(&b->d_best_sum, 8 * (size_t)n_scen))) return fail(e);
+        if ((e = alloc(&b->d_ninf, 4 * (size_t)n_scen))) return fail(e);
+        if ((e = alloc(&b->d_best_u, nseg * p0.S * 3 * 4))) return fail(e);
+        if ((e = alloc(&b->d_t_start, 8))) return fail(e);
+        if ((e = alloc(&b->d_t_end, 8 * (size_t)n_scen))) return fail(e);
+        if ((e = alloc(&b->d_live, 8))) return fail(e);
+        if ((e = alloc(&b->d_queue, 8))) return fail(e);
+        if ((e = alloc(&b->d_flags, 4))) return fail(e);
+        if ((e = cudaMemcpy(b->d_probs, pc.data(), sizeof(ProblemC) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaMemcpy(b->d_scen, b->scen.data(), sizeof(BatchScen) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaMemcpy(b->d_seg_scen, b->seg_scen.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaMemcpy(b->d_segkeys, segkeys.data(), sizeof(SegKey) * nseg, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaMemcpy(b->d_dyns, b->dyn_h.data(), sizeof(DynState) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaMemcpy(b->d_Lxy, lxy->L.data(), lxy->L.size() * 4, cudaMemcpyHostToDevice))) return fail(e);
+        if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking))) return fail(e);
+        b->grid = batch_rollout_grid();
+    } catch (const std::bad_alloc &) {
+        if (b) {
+            batch_free(b);
+            delete b;
+        }
+        return TMA_ERR_OOM;
+    }
+    *out = b;
+    return TMA_OK;
+}
+
+void tma_batch_destroy(tma_batch *b)
+{
+    if (!b) return;
+    batch_free(b);
+    delete b;
+}
+
+tma_status tma_batch_set_state(tma_batch *b, const tma_state *h_x0, const uint32_t *h_mpc,
+                               tma_stream_t stream)
+{
+    if (!b) return TMA_ERR_INVALID_ARG;
+    // start from the device state so that plant-advanced states are kept
+    TMA_CUDA(cudaMemcpyAsync(b->dyn_h.data(), b->d_dyns, sizeof(DynState) * b->n_scen,
+                             cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    long long k = 0;
+    for (int s = 0; s < b->n_scen; ++s) {
+        for (int i = 0; i < b->probs[s].N; ++i, ++k) {
+            if (!h_x0) continue;
+            const tma_state &x = h_x0[k];
+            if (!(x.v > 0) || !(x.m > 0)) return TMA_ERR_INVALID_ARG;
+            float *d = b->dyn_h[s].x0[i];
+            d[0] = (float)x.x;
+            d[1] = (float)x.y;
+            d[2] = (float)x.z;
+            d[3] = (float)x.v;
+            d[4] = (float)x.chi;
+            d[5] = (float)x.m;
+        }
+        if (h_mpc) {
+            if (h_mpc[s] > 0xFFFF) return TMA_ERR_INVALID_ARG;
+            b->dyn_h[s].mpc_step = h_mpc[s];
+        }
+    }
+    TMA_CUDA(cudaMemcpyAsync(b->d_dyns, b->dyn_h.data(), sizeof(DynState) * b->n_scen,
+                             cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return TMA_OK;
+}
+
+tma_status tma_batch_solve(tma_batch *b, tma_stream_t stream)
+{
+    if (!b) return TMA_ERR_INVALID_ARG;
+    return batch_solve_device(b, (cudaStream_t)stream);
+}
+
+tma_status tma_batch_mpc(tma_batch *b, int32_t n_steps, int32_t use_graph, tma_stream_t stream)
+{
+    if (!b || n_steps < 0) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_steps == 0) return TMA_OK;
+    if (!use_graph) return batch_mpc_steps(b, n_steps, st);
+    if (!b->graph || b->graph_steps != n_steps) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        TMA_CUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+        tma_status r = batch_mpc_steps(b, n_steps, b->capture_stream);
+        const cudaError_t ec = cudaStreamEndCapture(b->capture_stream, &g);
+        if (r != TMA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (ec != cudaSuccess) return cuda_fail(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            b->graph = nullptr;
+            return cuda_fail(ei);
+        }
+        b->graph_steps = n_steps;
+    }
+    TMA_CUDA(cudaGraphLaunch(b->graph, st));
+    return TMA_OK;
+}
+
+tma_status tma_batch_results(tma_batch *b, float *h_best_u, double *h_best_cost, int64_t *h_best,
+                             tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream)
+{
+    if (!b) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h_best_u)
+        TMA_CUDA(cudaMemcpyAsync(h_best_u, b->d_best_u, (size_t)b->nseg * b->S * 3 * 4,
+                                 cudaMemcpyDeviceToHost, st));
+    if (h_best_cost)
+        TMA_CUDA(cudaMemcpyAsync(h_best_cost, b->d_best_sum, 8 * (size_t)b->n_scen, cudaMemcpyDeviceToHost, st));
+    if (h_best)
+        TMA_CUDA(cudaMemcpyAsync(h_best, b->d_best, 8 * (size_t)b->n_scen, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaMemcpyAsync(b->dyn_h.data(), b->d_dyns, sizeof(DynState) * b->n_scen,
+                             cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    long long k = 0;
+    for (int s = 0; s < b->n_scen; ++s) {
+        if (h_mpc) h_mpc[s] = b->dyn_h[s].mpc_step;
+        for (int i = 0; i < b->probs[s].N; ++i, ++k) {
+            if (!h_x) continue;
+            const float *d = b->dyn_h[s].x0[i];
+            h_x[k] = tma_state{d[0], d[1], d[2], d[3], d[4], d[5]};
+        }
+    }
+    return TMA_OK;
+}
+
+tma_status tma_batch_latency(tma_batch *b, double *h_ms, tma_stream_t stream)
+{
+    if (!b || !h_ms) return TMA_ERR_INVALID_ARG;
+    std::vector<unsigned long long> t(b->n_scen);
+    unsigned long long t0 = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    TMA_CUDA(cudaMemcpyAsync(&t0, b->d_t_start, 8, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaMemcpyAsync(t.data(), b->d_t_end, 8 * t.size(), cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    for (int s = 0; s < b->n_scen; ++s) h_ms[s] = (double)(long long)(t[s] - t0) * 1e-6;
+    return TMA_OK;
+}
+
+tma_status tma_batch_live_steps(tma_batch *b, uint64_t *h_live, tma_stream_t stream)
+{
+    if (!b || !h_live) return TMA_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    TMA_CUDA(cudaMemcpyAsync(&v, b->d_live, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    *h_live = v;
     return TMA_OK;
 }
 

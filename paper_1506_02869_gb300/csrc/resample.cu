@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
                                                        uint32_t key0, uint32_t key1, uint32_t J,
                                                        const uint32_t *__restrict__ d_mpc,
                                                        uint32_t mpc_host, int32_t *__restrict__ anc,
-                                                       unsigned int *__restrict__ flags)
+                                                       unsigned int *__restrict__ flags,
+                                                       const SegKey *__restrict__ seg_keys,
+                                                       const DynState *__restrict__ dyns)
 {
     __shared__ unsigned long long Ssm[kChunk];
     __shared__ unsigned long long wtot[kThreads / 32];
@@ -241,8 +243,15 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
     for (int j = 0; j < kPer; ++j) Ssm[threadIdx.x * kPer + j] += add;
     __syncthreads();
 
-    const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
-    const uint32_t r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
+    uint32_t r;
+    if (seg_keys) {
+        // batched: the segment's scenario key and aircraft index, its scenario's MPC step
+        const SegKey sk = seg_keys[s];
+        r = draw(sk.key0, sk.key1, 0u, sk.c1, 0u, 2u, J, dyns[sk.scen].mpc_step).x;
+    } else {
+        const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
+        r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
+    }
     const unsigned long long D = (unsigned long long)L << 32;
     if (threadIdx.x == 0) range[0] = count_below(before, total, D, r, L);
     if (threadIdx.x == 32) range[1] = count_below(Ssm[len - 1], total, D, r, L);
@@ -333,7 +342,8 @@ cudaError_t scratch_address(void **out)
 
 cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
-                            int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st)
+                            int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st,
+                            const SegKey *seg_keys, const DynState *dyns)
 {
     if (nseg <= 0 || L <= 0) return cudaSuccess;
     const int nc = n_chunks(L);
@@ -342,7 +352,7 @@ cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t 
     dim3 grid(nc, nseg);
     res_chunk_sum<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq);
     res_expand<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq, key0, key1, J, d_mpc, mpc_host, anc,
-                                          d_flags);
+                                          d_flags, seg_keys, dyns);
     count_launch(2);
     return cudaGetLastError();
 }

@@ -13,6 +13,7 @@
 namespace tma {
 
 constexpr int kMaxN = TMA_MAX_AIRCRAFT;
+constexpr int kTileParticles = 32;   // particles per rollout tile (one warp per aircraft)
 
 // Per-aircraft constants in FP32 (derived on the host in FP64).
 struct AircraftC {
@@ -21,7 +22,6 @@ struct AircraftC {
     float Cf1, invCf2, Tmin, Tmax, m_empty;
     float thF, Z, vD;
     float invFmax;         // 1 / (H dt Tmax eta(vmax))
-    float supB, invSupInf; // departure altitude-term normalisation
     float invCmax;         // departure speed-term normalisation
 };
 
@@ -34,6 +34,7 @@ struct ProblemC {
     float box_lo[3], box_hi[3], inv_h[3];
     float turb_sigma;
     float sgmax, tpmax;    // sin(gamma_max), tan(phi_max)
+    float climb_step;      // vmax sin(gamma_max) dt: largest altitude change per step
     float Sh2, Sh_inv, Sv, Sv_inv;
     int sep_mode;
     float sp_beta, sp_inv_beta, mu_sep;
@@ -62,6 +63,24 @@ struct WindC {
     uint32_t key0, key1;
 };
 
+// One scenario of a batch: offsets into the packed batch buffers.
+struct BatchScen {
+    long long u_off;      // floats: controls u_s[L][N][S][3]
+    long long seg_off;    // first segment (aircraft) of the scenario
+    long long w_off;      // float4s: packed wind field [M][H][P]
+    long long item_off;   // first work item of the scenario in the persistent queue
+    long long items;      // its work items: M * ceil(nLb / T)
+    int N, T;             // aircraft; particle tiles per CTA
+    float ctrl_lo[3], ctrl_hi[3], move_sigma[3];
+    uint32_t key0, key1;
+};
+
+// Per-segment key of the resampling uniform (batched form).
+struct SegKey {
+    uint32_t key0, key1, c1;
+    int scen;
+};
+
 // ------------------------------------------------------------------ launchers
 // Each returns cudaSuccess or the launch error.
 
@@ -84,7 +103,8 @@ cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, dou
 size_t lse_workspace(int nseg, int64_t L);
 cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
-                            int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st);
+                            int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st,
+                            const SegKey *seg_keys = nullptr, const DynState *dyns = nullptr);
 size_t resample_workspace(int nseg, int64_t L);
 
 cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
@@ -98,6 +118,32 @@ cudaError_t launch_select(const float *cbar, int N, int64_t L, int64_t *best, do
 size_t select_workspace(int64_t L);
 cudaError_t launch_gather_best(const float *u, const int64_t *best, int nctl_per_particle,
                                float *best_u, cudaStream_t st);
+
+// batched MPC (batch.cu)
+size_t batch_rollout_smem();
+int batch_rollout_grid();
+cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
+                                 long long n_items, const DynState *dyns, const float *u,
+                                 const float *W, long long L, int J, float *cost_ms,
+                                 float *cost_ms_soft, unsigned long long *live,
+                                 unsigned long long *queue, int grid, cudaStream_t st);
+cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen,
+                                     const int *seg_scen, long long nseg, long long L, int M,
+                                     float *cbar, cudaStream_t st);
+cudaError_t launch_batch_move(const BatchScen *scen, const int *seg_scen, const DynState *dyns,
+                              long long nseg, long long L, int S, const float *u,
+                              const int32_t *anc, int J, float *u_out, cudaStream_t st);
+cudaError_t launch_batch_init(const BatchScen *scen, const int *seg_scen, const DynState *dyns,
+                              long long nseg, long long L, int S, float *u, cudaStream_t st);
+cudaError_t launch_batch_wind_normals(const WindC &w, int s0, int M_scen, const BatchScen *scen,
+                                      const DynState *dyns, float *Btmp, cudaStream_t st);
+cudaError_t launch_batch_select(const BatchScen *scen, int n_scen, const float *cbar, long long L,
+                                int S, const float *u, long long *best, double *best_sum, int *ninf,
+                                float *best_u, unsigned long long *t_end, cudaStream_t st);
+cudaError_t launch_stamp_start(unsigned long long *t0, cudaStream_t st);
+cudaError_t launch_plant_step(const ProblemC *probs, const BatchScen *scen, const int *seg_scen,
+                              long long nseg, int n_scen, DynState *dyns, const float *W,
+                              const float *best_u, int S, cudaStream_t st);
 
 void count_launch(int n = 1);
 
@@ -151,9 +197,54 @@ struct tma_solver {
     std::vector<cudaEvent_t> event_pool;
     double prof_ms[8] = {0};
     uint64_t prof_n[8] = {0};
+    // one-scenario tables for the plant step (the batched plant kernel)
+    tma::ProblemC *d_probs1 = nullptr;
+    tma::BatchScen *d_scen1 = nullptr;
+    int *d_seg_scen1 = nullptr;
     // autotuned launch variant of the rollout kernel and the timings behind it
     int rollout_variant = -1;
     int n_tuned = 0;
     int tuned_variant[8] = {0};
     float tuned_ms[8] = {0};
+};
+
+struct tma_batch {
+    int n_scen = 0;
+    int device = 0;
+    int L = 0, M = 0, H = 0, S = 0, J_max = 0, sep_mode = 0;
+    long long nseg = 0, n_items = 0;
+    int grid = 0;
+    std::vector<tma_problem> probs;
+    std::vector<std::vector<tma_aircraft>> aircraft;
+    std::vector<std::vector<double>> pop;
+    std::vector<tma::BatchScen> scen;
+    std::vector<int> seg_scen;
+    std::vector<tma::DynState> dyn_h;
+    std::vector<tma::WindC> wind_groups;   // one GEMM per group of scenarios
+    std::vector<int> group_start;
+    int lda = 0;
+    // device buffers (owned)
+    tma::ProblemC *d_probs = nullptr;
+    tma::BatchScen *d_scen = nullptr;
+    int *d_seg_scen = nullptr;
+    tma::SegKey *d_segkeys = nullptr;
+    tma::DynState *d_dyns = nullptr;
+    float *d_Lxy = nullptr, *d_Btmp = nullptr, *d_W = nullptr;
+    float *d_u[2] = {nullptr, nullptr};
+    float *d_cost_ms = nullptr, *d_cost_ms_soft = nullptr, *d_cbar = nullptr, *d_cbar_soft = nullptr;
+    double *d_wtilde = nullptr;
+    int32_t *d_anc = nullptr;
+    void *d_work = nullptr;
+    long long *d_best = nullptr;
+    double *d_best_sum = nullptr;
+    int *d_ninf = nullptr;
+    float *d_best_u = nullptr;
+    unsigned long long *d_t_start = nullptr, *d_t_end = nullptr, *d_live = nullptr, *d_queue = nullptr;
+    unsigned int *d_flags = nullptr;
+    std::vector<float *> d_pops;
+    int final_u = 0;
+    // captured MPC loop
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
 };

@@ -122,3 +122,26 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pkg, "LIBPATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         pkg.lib()
+
+
+def test_batch_create_rejects_invalid_batches(lib):
+    import scenarios as S
+    ps = [S.shrink(p, L=64, M=2, H=10, J_max=2) for p in S.config5(n_scen=3)]
+    structs = [pkg.problem_struct(p) for p in ps]
+
+    def create(plist):
+        n = len(plist)
+        parr = (pkg.TmaProblem * max(n, 1))(*[s for s, _, _ in plist])
+        aptrs = (C.POINTER(pkg.TmaAircraft) * max(n, 1))(
+            *[C.cast(a, C.POINTER(pkg.TmaAircraft)) for _, a, _ in plist])
+        h = C.c_void_p()
+        return lib.tma_batch_create(parr, aptrs, n, C.byref(h)), h
+
+    assert create([])[0] == pkg.TMA_ERR_INVALID_ARG
+    bad = pkg.problem_struct(ps[1].copy(M=3))
+    st, h = create([structs[0], bad])
+    assert st == pkg.TMA_ERR_INVALID_ARG and not h.value
+    bad_grid = pkg.problem_struct(ps[1].copy(grid=(8, 8, 4)))
+    assert create([structs[0], bad_grid])[0] == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_batch_mpc(None, 1, 1, None) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_plant_step(None, None, None) == pkg.TMA_ERR_INVALID_ARG

@@ -1,0 +1,133 @@
+"""Batched MPC on the GPU: many scenarios with uneven aircraft counts in one
+persistent launch per stage, the receding-horizon loop (plant step) and its
+CUDA-graph capture.  The batched solve shares the single-scenario arithmetic,
+so it must reproduce single-scenario solves bit for bit; the plant step is
+checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenarios as S
+from gpu_helpers import cuda, oracle_wind
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda()
+
+
+@pytest.fixture(scope="module")
+def pkg(torch):
+    import paper_1506_02869_gb300 as pkg
+    return pkg
+
+
+def mixed_batch(n, L=1024, M=4, H=24, J=4):
+    """Scenarios of the batched workload spanning the aircraft counts: 2 (16
+    tiles per CTA), around 10 (3 tiles), above 16 (1 tile) and the largest."""
+    ps = S.config5(n_scen=48)
+    order = sorted(range(len(ps)), key=lambda s: ps[s].N)
+    pick = [order[0], order[len(order) // 3], order[len(order) // 2], order[-1],
+            order[len(order) // 4], order[-2], order[1], order[-3]][:n]
+    return [S.shrink(ps[k], L=L, M=M, H=H, J_max=J) for k in pick]
+
+
+def _states(p):
+    return np.array([[a[k] for k in ("x", "y", "z", "v", "chi", "m")] for a in p.aircraft])
+
+
+def test_batch_solve_equals_single_solves(torch, pkg):
+    ps = mixed_batch(6)
+    Ns = [p.N for p in ps]
+    assert min(Ns) <= 3 and max(Ns) > 16
+    b = pkg.tma_batch_create(ps)
+    pkg.tma_batch_solve(b)
+    res = pkg.tma_batch_results(b, Ns, ps[0].S)
+    live = pkg.tma_batch_live_steps(b)
+    lat = pkg.tma_batch_latency(b, len(ps))
+    pkg.tma_batch_destroy(b)
+    live_single = 0
+    for k, p in enumerate(ps):
+        sol = pkg.Solver(p)
+        bu, c, _ = sol.solve()
+        best = sol.best_index()
+        live_single += sol.live_steps()
+        sol.close()
+        assert np.array_equal(res["best_u"][k], bu.cpu().numpy()), k
+        assert res["best_cost"][k] == c or (np.isinf(c) and np.isinf(res["best_cost"][k]))
+        assert res["best"][k] == best
+    assert live == live_single
+    assert (lat > 0).all() and np.isfinite(lat).all()
+
+
+def test_batch_mpc_graph_equals_eager_and_single_loop(torch, pkg):
+    ps = mixed_batch(4, L=512, M=3, H=20, J=3)
+    Ns = [p.N for p in ps]
+    bg = pkg.tma_batch_create(ps)
+    be = pkg.tma_batch_create(ps)
+    pkg.tma_batch_mpc(bg, 2, use_graph=True)
+    pkg.tma_batch_mpc(be, 2, use_graph=False)
+    rg = pkg.tma_batch_results(bg, Ns, ps[0].S)
+    re = pkg.tma_batch_results(be, Ns, ps[0].S)
+    for k in range(len(ps)):
+        assert np.array_equal(rg["states"][k], re["states"][k])
+        assert np.array_equal(rg["best_u"][k], re["best_u"][k])
+    assert (rg["mpc"] == np.array([p.mpc_step + 2 for p in ps])).all()
+    # replaying the captured graph continues from the advanced state
+    pkg.tma_batch_mpc(bg, 2, use_graph=True)
+    pkg.tma_batch_mpc(be, 2, use_graph=False)
+    rg = pkg.tma_batch_results(bg, Ns, ps[0].S)
+    re = pkg.tma_batch_results(be, Ns, ps[0].S)
+    for k in range(len(ps)):
+        assert np.array_equal(rg["states"][k], re["states"][k])
+    pkg.tma_batch_destroy(bg)
+    pkg.tma_batch_destroy(be)
+    # the same loop through single-scenario solvers: solve, then the plant step
+    for k, p in enumerate(ps):
+        sol = pkg.Solver(p)
+        for _ in range(4):
+            bu, _, _ = sol.solve()
+            pkg.tma_plant_step(sol.h, bu)
+        x, mpc = pkg.tma_get_state(sol.h, p.N)
+        sol.close()
+        assert mpc == p.mpc_step + 4
+        assert np.array_equal(x.astype(np.float32), re["states"][k].astype(np.float32)), k
+
+
+def test_plant_step_matches_oracle(torch, pkg):
+    p = S.config1().copy(mpc_step=2)
+    sol = pkg.Solver(p)
+    sol.set_state(mpc_step=2)
+    rng = np.random.default_rng(31)
+    u = S.mild_controls(p, 1, rng)[0]
+    pkg.tma_plant_step(sol.h, torch.from_numpy(u).cuda())
+    x, mpc = pkg.tma_get_state(sol.h, p.N)
+    sol.close()
+    ref = O.plant_step(p, _states(p), oracle_wind(p)[0, 0], u[:, 0, :])
+    assert mpc == 3
+    scale = np.array([1e4, 1e4, 1e3, 1e2, 1.0, 1e4])
+    assert np.all(np.abs(x - ref) <= 2e-6 * np.maximum(np.abs(ref), scale)), (x, ref)
+
+
+def test_plant_step_limits_thrust_like_the_oracle(torch, pkg):
+    # a steep descent needs negative thrust: the plant applies Tmin and slows down
+    p = S.config1()
+    sol = pkg.Solver(p)
+    u = np.zeros((p.N, p.S, 3), np.float32)
+    u[:, :, 1] = -15.0
+    u[:, :, 2] = -1.0
+    pkg.tma_plant_step(sol.h, torch.from_numpy(u).cuda())
+    x, _ = pkg.tma_get_state(sol.h, p.N)
+    sol.close()
+    ref = O.plant_step(p, _states(p), oracle_wind(p)[0, 0], u[:, 0, :])
+    assert np.allclose(x, ref, rtol=2e-6, atol=1e-3)
+    assert (ref[:, 5] == _states(p)[:, 5]).all()          # idle thrust burns no fuel
+
+
+def test_batch_rejects_mismatched_shapes(torch, pkg):
+    ps = mixed_batch(2)
+    ps[1] = ps[1].copy(M=ps[0].M + 1)
+    with pytest.raises(pkg.TmaError):
+        pkg.tma_batch_create(ps)
