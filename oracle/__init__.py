@@ -87,6 +87,8 @@ def lib():
                                          P(i64), i32, i32, i32, P(d), P(d), P(d), P(d), P(i64)]
             _lib.orc_trajectory.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), i32, P(d), i64,
                                             i32, P(d), P(d), P(d)]
+            _lib.orc_rollout_grad.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), i64, i32, P(d)]
+            _lib.orc_rollout_grad.restype = d
             _lib.orc_plant_step.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), P(d), P(d)]
             _lib.orc_kappa.argtypes = [i32]
             _lib.orc_kappa.restype = i32
@@ -340,6 +342,18 @@ def trajectory(p, u_l, W_m, l=0, m=0, J=0):
     lib().orc_trajectory(mm.ps, mm.ac, _ptr(Wm, C.c_double), m, _ptr(u, C.c_double), l, J,
                          _ptr(traj, C.c_double), _ptr(ch, C.c_double), _ptr(cs, C.c_double))
     return traj, ch, cs
+
+
+def rollout_grad(p, u_l, W, l=0, J=0):
+    """(C, dC/du) of one particle: C = sum_i mean_m c_soft (softplus separation),
+    gradient by reverse mode; (inf, 0) if the particle is infeasible."""
+    u = np.ascontiguousarray(u_l, np.float64).reshape(p.N, p.S, 3)
+    Wc = np.ascontiguousarray(W, np.float64)
+    g = np.empty((p.N, p.S, 3))
+    mm = _Marshalled(p)
+    c = lib().orc_rollout_grad(mm.ps, mm.ac, _ptr(Wc, C.c_double), _ptr(u, C.c_double), l, J,
+                               _ptr(g, C.c_double))
+    return c, g
 
 
 def plant_step(p, x, W0, u0):

@@ -509,6 +509,391 @@ void orc_trajectory(const orc_problem *P, const orc_aircraft *A, const double *W
 }
 
 /* ------------------------------------------------------------------ */
+/* reverse-mode derivative of the soft cost (gradient for the MALA move)   */
+/* ------------------------------------------------------------------ */
+
+/* wind interpolation with its gradient with respect to position (zero along
+ * an axis where the position is clamped to the box) */
+static void trilinear_grad(const orc_problem *P, const double *Wk, double x, double y, double z,
+                           double w[2], double dw[2][3])
+{
+    double pos[3] = {x, y, z};
+    int idx[3], inside[3];
+    double t[3], ih[3];
+    for (int d = 0; d < 3; d++) {
+        double lo = P->box_lo[d], hi = P->box_hi[d];
+        int n = P->grid[d];
+        double h = (hi - lo) / (n - 1);
+        inside[d] = pos[d] > lo && pos[d] < hi;
+        double c = pos[d] < lo ? lo : (pos[d] > hi ? hi : pos[d]);
+        double f = (c - lo) / h;
+        int i = (int)floor(f);
+        if (i > n - 2) i = n - 2;
+        if (i < 0) i = 0;
+        idx[d] = i;
+        t[d] = f - i;
+        ih[d] = 1.0 / h;
+    }
+    const int ny = P->grid[1], nz = P->grid[2];
+    for (int c = 0; c < 2; c++) {
+        w[c] = 0.0;
+        dw[c][0] = dw[c][1] = dw[c][2] = 0.0;
+    }
+    for (int dx = 0; dx < 2; dx++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dz = 0; dz < 2; dz++) {
+                double fx = dx ? t[0] : 1.0 - t[0], fy = dy ? t[1] : 1.0 - t[1], fz = dz ? t[2] : 1.0 - t[2];
+                double gx = (dx ? 1.0 : -1.0) * ih[0], gy = (dy ? 1.0 : -1.0) * ih[1], gz = (dz ? 1.0 : -1.0) * ih[2];
+                int64_t p = ((int64_t)(idx[0] + dx) * ny + (idx[1] + dy)) * nz + (idx[2] + dz);
+                for (int c = 0; c < 2; c++) {
+                    double v = Wk[2 * p + c];
+                    w[c] += fx * fy * fz * v;
+                    dw[c][0] += gx * fy * fz * v;
+                    dw[c][1] += fx * gy * fz * v;
+                    dw[c][2] += fx * fy * gz * v;
+                }
+            }
+    for (int c = 0; c < 2; c++)
+        for (int d = 0; d < 3; d++)
+            if (!inside[d]) dw[c][d] = 0.0;
+}
+
+/* population density and its gradient (0 outside the grid) */
+static double popdense_grad(const orc_problem *P, double x, double y, double *gx, double *gy)
+{
+    *gx = *gy = 0.0;
+    if (!P->popdense || P->pop_n[0] < 2 || P->pop_n[1] < 2) return 0.0;
+    if (x < P->pop_lo[0] || x > P->pop_hi[0] || y < P->pop_lo[1] || y > P->pop_hi[1]) return 0.0;
+    const int n0 = P->pop_n[0], n1 = P->pop_n[1];
+    double h0 = (P->pop_hi[0] - P->pop_lo[0]) / (n0 - 1), h1 = (P->pop_hi[1] - P->pop_lo[1]) / (n1 - 1);
+    double f0 = (x - P->pop_lo[0]) / h0, f1 = (y - P->pop_lo[1]) / h1;
+    int i0 = (int)floor(f0), i1 = (int)floor(f1);
+    if (i0 > n0 - 2) i0 = n0 - 2;
+    if (i1 > n1 - 2) i1 = n1 - 2;
+    if (i0 < 0) i0 = 0;
+    if (i1 < 0) i1 = 0;
+    double t0 = f0 - i0, t1 = f1 - i1;
+    const double *g = P->popdense;
+    double g00 = g[(int64_t)i0 * n1 + i1], g01 = g[(int64_t)i0 * n1 + i1 + 1];
+    double g10 = g[(int64_t)(i0 + 1) * n1 + i1], g11 = g[(int64_t)(i0 + 1) * n1 + i1 + 1];
+    *gx = ((1 - t1) * (g10 - g00) + t1 * (g11 - g01)) / h0;
+    *gy = ((1 - t0) * (g01 - g00) + t0 * (g11 - g10)) / h1;
+    return (1 - t0) * (1 - t1) * g00 + (1 - t0) * t1 * g01 + t0 * (1 - t1) * g10 + t0 * t1 * g11;
+}
+
+static double wrap_pi(double a)  /* to (-pi, pi] */
+{
+    double r = fmod(a, 2.0 * M_PI);
+    if (r > M_PI) r -= 2.0 * M_PI;
+    if (r <= -M_PI) r += 2.0 * M_PI;
+    return r;
+}
+
+static double sgn(double a) { return a > 0 ? 1.0 : (a < 0 ? -1.0 : 0.0); }
+
+typedef struct {
+    double x, y, z, v, chi, F;
+    int upd;       /* the aircraft was advanced at this step */
+    int active;    /* flying (not violated, not landed) after the step */
+} gstep;
+
+/* The soft objective of one particle, C = sum_i (1/M) sum_m c_soft[i][m]
+ * (softplus separation of reading R5, unary and control constraints hard), and
+ * its gradient with respect to the controls u[N][S][3], by the reverse mode of
+ * the rollout (Sec. 3.3-3.5, Sec. 7.1).  The forward pass is the rollout of
+ * orc_rollout written with the identities of reading R1 (z' = z + dt hdot,
+ * v' = v + dt a, chi' = chi + dt w) and the drag of reading R2 in closed form,
+ * D = q CD0 + CD2 m^2 (g^2 (1 - hdot^2/v^2) + w^2 v^2) / q, q = rho v^2 S / 2.
+ * Decisions (limits, landing, kinks of |.| and of the interpolation) are held
+ * at their forward values.  Returns +inf (gradient 0) when any aircraft
+ * violates a hard constraint in any sample. */
+double orc_rollout_grad(const orc_problem *P, const orc_aircraft *A, const double *W,
+                        const double *ul, int64_t l, int J, double *grad)
+{
+    const int N = P->N, H = P->H, S = P->S, M = P->M;
+    const int64_t Pn = (int64_t)P->grid[0] * P->grid[1] * P->grid[2];
+    const double dt = P->dt, sgmax = sin(P->gamma_max), tpmax = tan(P->phi_max);
+    const double Sh = P->sep_h, Sv = P->sep_v, bet = P->sp_beta, mu = P->mu_sep;
+    gstep *tr = (gstep *)malloc(sizeof(gstep) * (size_t)(H + 1) * N);
+    double *gs = (double *)calloc((size_t)N * S * 3, sizeof(double));
+    double total = 0.0;
+    int infeasible = 0;
+    for (int n = 0; n < N * S * 3; n++) grad[n] = 0.0;
+
+    for (int m = 0; m < M && !infeasible; m++) {
+        const double *Wm = W + (int64_t)m * H * Pn * 2;
+        double sA[64], sB[64], sC[64], sN[64], soft[64], nz[64][2];
+        int dead[64], landed[64];
+        /* turbulence normals of the sample (as the forward rollout draws them) */
+        double *turb = (double *)malloc(sizeof(double) * (size_t)H * N * 2);
+        for (int i = 0; i < N; i++) {
+            gstep *g = &tr[i];
+            g->x = A[i].x; g->y = A[i].y; g->z = A[i].z; g->v = A[i].v; g->chi = A[i].chi; g->F = 0.0;
+            g->upd = 0; g->active = 1;
+            sA[i] = sB[i] = sC[i] = sN[i] = soft[i] = 0.0;
+            dead[i] = landed[i] = 0;
+            for (int k = 0; k < H; k += 2) {
+                uint32_t tb[4];
+                orc_draw(P, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, tb);
+                double a0, a1, b0, b1;
+                orc_box_muller(tb[0], tb[1], &a0, &a1);
+                orc_box_muller(tb[2], tb[3], &b0, &b1);
+                turb[((int64_t)k * N + i) * 2] = a0;
+                turb[((int64_t)k * N + i) * 2 + 1] = a1;
+                if (k + 1 < H) {
+                    turb[((int64_t)(k + 1) * N + i) * 2] = b0;
+                    turb[((int64_t)(k + 1) * N + i) * 2 + 1] = b1;
+                }
+            }
+            (void)nz;
+        }
+        /* ---------------- forward */
+        for (int k = 0; k < H; k++) {
+            for (int i = 0; i < N; i++) {
+                const orc_aircraft *a = &A[i];
+                gstep *c = &tr[(int64_t)k * N + i], *n1 = &tr[(int64_t)(k + 1) * N + i];
+                *n1 = *c;
+                n1->upd = 0;
+                c->upd = 0;
+                if (dead[i] || landed[i]) { n1->active = 0; continue; }
+                const int seg = (int)(((int64_t)k * S) / H);
+                const double *uu = ul + ((int64_t)i * S + seg) * 3;
+                const double w = uu[0], hd = uu[1], acc = uu[2];
+                const double mass = a->m - c->F;
+                double sg = hd / c->v;
+                int ok = fabs(sg) <= sgmax && fabs(sg) < 1.0;
+                double cg = ok ? sqrt(1.0 - sg * sg) : 1.0;
+                double tp = w * c->v / (G0 * cg);
+                ok = ok && fabs(tp) < tpmax;
+                double rho = 1.225 * pow(fmax(1.0 - 2.2558e-5 * c->z, 0.0), 4.2559);
+                double q = 0.5 * rho * c->v * c->v * a->S;
+                double A2 = G0 * G0 * (1.0 - sg * sg) + w * w * c->v * c->v;
+                double D = q * a->CD0 + a->CD2 * mass * mass * A2 / q;
+                double T = mass * (acc + G0 * sg) + D;
+                ok = ok && T >= a->Tmin && T <= a->Tmax;
+                if (!ok) { dead[i] = 1; n1->active = 0; continue; }
+                c->upd = 1;
+                double wv[2], dw[2][3];
+                trilinear_grad(P, Wm + (int64_t)k * Pn * 2, c->x, c->y, c->z, wv, dw);
+                const double *tn = &turb[((int64_t)k * N + i) * 2];
+                n1->x = c->x + dt * (c->v * cg * cos(c->chi) + wv[0] + P->turb_sigma * tn[0]);
+                n1->y = c->y + dt * (c->v * cg * sin(c->chi) + wv[1] + P->turb_sigma * tn[1]);
+                n1->z = c->z + dt * hd;
+                n1->v = c->v + dt * acc;
+                n1->chi = c->chi + dt * w;
+                n1->F = c->F + dt * a->Cf1 * (1.0 + c->v / a->Cf2) * T;
+                if (!(n1->z >= P->z_min && n1->z <= P->z_max && n1->v >= P->v_min && n1->v <= P->v_max &&
+                      a->m - n1->F >= a->m_empty)) { dead[i] = 1; n1->active = 0; continue; }
+                double th = atan2(n1->y, n1->x);
+                if (a->type == 0) {
+                    double r = sqrt(n1->x * n1->x + n1->y * n1->y), ath = fabs(th);
+                    double ratio = ath < 1e-3 ? 1.0 + th * th / 6.0 : ath / fmax(sin(ath), 0.25 * ath);
+                    double beta = atan2(n1->z, r * ratio);
+                    if (r <= P->P_runway && beta <= P->P_beta && n1->x > 0.0 && ath <= P->P_chi &&
+                        angdist(n1->chi - M_PI) <= P->P_chi && n1->v <= P->P_vs) {
+                        landed[i] = 1; n1->active = 0; continue;
+                    }
+                    sA[i] += angdist(n1->chi - M_PI - 2.0 * th);
+                    sB[i] += fabs(beta - P->beta_f);
+                } else {
+                    sA[i] += angdist(th - a->theta_F);
+                    sB[i] += fabs(a->Z - n1->z);
+                    sC[i] += fabs(n1->v - a->v_D);
+                }
+                if (P->w_noise != 0.0) {
+                    double za = n1->z / P->A_c, h = fmax(1.0 - za * za, 0.0);
+                    sN[i] += h * popdense_at(P, n1->x, n1->y);
+                }
+                n1->active = 1;
+            }
+            for (int i = 0; i < N; i++) {
+                const gstep *pi_ = &tr[(int64_t)(k + 1) * N + i];
+                if (!pi_->active) continue;
+                for (int j = i + 1; j < N; j++) {
+                    const gstep *pj = &tr[(int64_t)(k + 1) * N + j];
+                    if (!pj->active) continue;
+                    double dx = pi_->x - pj->x, dy = pi_->y - pj->y, dz = pi_->z - pj->z;
+                    double g = fmin(1.0 - sqrt(dx * dx + dy * dy) / Sh, 1.0 - fabs(dz) / Sv);
+                    double pen = softplus(g, bet);
+                    soft[i] += pen;
+                    soft[j] += pen;
+                }
+            }
+        }
+        for (int i = 0; i < N; i++)
+            if (dead[i]) infeasible = 1;
+        if (infeasible) { free(turb); break; }
+        /* objective and its sensitivity to the accumulated sums */
+        double gA[64], gB[64], gC[64], gN[64], gF[64];
+        for (int i = 0; i < N; i++) {
+            const orc_aircraft *a = &A[i];
+            const double Fmax = H * dt * a->Tmax * a->Cf1 * (1.0 + P->v_max / a->Cf2);
+            const double FH = tr[(int64_t)H * N + i].F;
+            double Jsum, dA, dB, dC = 0.0, dF;
+            if (a->type == 1) {
+                double d0 = fabs(a->Z - a->z), cl = P->v_max * sgmax * dt, sup = 0.0, inf = 0.0;
+                for (int k = 1; k <= H; k++) {
+                    sup += d0 + k * cl;
+                    inf += (d0 - k * cl) > 0.0 ? d0 - k * cl : 0.0;
+                }
+                sup /= H;
+                inf /= H;
+                double Cmax = fmax(P->v_max - a->v_D, a->v_D - P->v_min);
+                Jsum = P->alpha_dep[0] * (1.0 - sA[i] / H / M_PI) + P->alpha_dep[1] * (1.0 - FH / Fmax) +
+                       P->alpha_dep[2] * (sup - sB[i] / H) / (sup - inf) +
+                       P->alpha_dep[3] * (1.0 - sC[i] / H / Cmax);
+                dA = -P->alpha_dep[0] / (H * M_PI);
+                dB = -P->alpha_dep[2] / (H * (sup - inf));
+                dC = -P->alpha_dep[3] / (H * Cmax);
+                dF = -P->alpha_dep[1] / Fmax;
+            } else {
+                Jsum = P->alpha_arr[0] * (1.0 - sA[i] / H / M_PI) + P->alpha_arr[1] * (1.0 - sB[i] / H / (0.5 * M_PI)) +
+                       P->alpha_arr[2] * (1.0 - FH / Fmax);
+                dA = -P->alpha_arr[0] / (H * M_PI);
+                dB = -P->alpha_arr[1] / (H * 0.5 * M_PI);
+                dF = -P->alpha_arr[2] / Fmax;
+            }
+            double JT = (1.0 - P->w_noise) * Jsum + P->w_noise * (1.0 - sN[i] / H);
+            double gJ = JT > 1e-30 ? -1.0 / JT : 0.0;
+            total += (-log(JT > 1e-30 ? JT : 1e-30) + mu * soft[i]) / M;
+            gA[i] = gJ * (1.0 - P->w_noise) * dA / M;
+            gB[i] = gJ * (1.0 - P->w_noise) * dB / M;
+            gC[i] = gJ * (1.0 - P->w_noise) * dC / M;
+            gN[i] = gJ * (-P->w_noise / H) / M;
+            gF[i] = gJ * (1.0 - P->w_noise) * dF / M;
+        }
+        /* ---------------- reverse */
+        double bx[64], by[64], bz[64], bv[64], bc[64], bF[64];
+        for (int i = 0; i < N; i++) {
+            bx[i] = by[i] = bz[i] = bv[i] = bc[i] = 0.0;
+            bF[i] = gF[i];
+        }
+        for (int k = H - 1; k >= 0; k--) {
+            /* separation terms at step k+1: dC/dp_ij = 2 mu / M */
+            for (int i = 0; i < N; i++) {
+                const gstep *pi_ = &tr[(int64_t)(k + 1) * N + i];
+                if (!pi_->active) continue;
+                for (int j = i + 1; j < N; j++) {
+                    const gstep *pj = &tr[(int64_t)(k + 1) * N + j];
+                    if (!pj->active) continue;
+                    double dx = pi_->x - pj->x, dy = pi_->y - pj->y, dz = pi_->z - pj->z;
+                    double dh = sqrt(dx * dx + dy * dy);
+                    double gh = 1.0 - dh / Sh, gv = 1.0 - fabs(dz) / Sv, g = fmin(gh, gv);
+                    double sig = 1.0 / (1.0 + exp(-bet * g));
+                    double s = 2.0 * mu / M * sig;
+                    if (gh <= gv) {
+                        if (dh > 0.0) {
+                            double ex = dx / dh / Sh, ey = dy / dh / Sh;
+                            bx[i] -= s * ex; by[i] -= s * ey;
+                            bx[j] += s * ex; by[j] += s * ey;
+                        }
+                    } else {
+                        double ez = sgn(dz) / Sv;
+                        bz[i] -= s * ez;
+                        bz[j] += s * ez;
+                    }
+                }
+            }
+            for (int i = 0; i < N; i++) {
+                const orc_aircraft *a = &A[i];
+                const gstep *c = &tr[(int64_t)k * N + i], *n1 = &tr[(int64_t)(k + 1) * N + i];
+                if (!c->upd) continue;
+                /* per-step terms on the step-(k+1) state (only while flying) */
+                if (n1->active) {
+                    double x = n1->x, y = n1->y, z = n1->z, r2 = x * x + y * y;
+                    double th = atan2(y, x), dthx = -y / r2, dthy = x / r2;
+                    if (a->type == 1) {
+                        double s = sgn(wrap_pi(th - a->theta_F)) * gA[i];
+                        bx[i] += s * dthx; by[i] += s * dthy;
+                        bz[i] += gB[i] * sgn(z - a->Z);
+                        bv[i] += gC[i] * sgn(n1->v - a->v_D);
+                    } else {
+                        double se = sgn(wrap_pi(n1->chi - M_PI - 2.0 * th)) * gA[i];
+                        bc[i] += se;
+                        bx[i] += -2.0 * se * dthx; by[i] += -2.0 * se * dthy;
+                        double r = sqrt(r2), ath = fabs(th), ratio, dratio;
+                        if (ath < 1e-3) { ratio = 1.0 + th * th / 6.0; dratio = th / 3.0; }
+                        else if (sin(ath) >= 0.25 * ath) {
+                            ratio = ath / sin(ath);
+                            dratio = sgn(th) * (sin(ath) - ath * cos(ath)) / (sin(ath) * sin(ath));
+                        } else { ratio = 4.0; dratio = 0.0; }
+                        double sa = r * ratio, beta = atan2(z, sa), den = z * z + sa * sa;
+                        double bb = gB[i] * sgn(beta - P->beta_f);
+                        bz[i] += bb * sa / den;
+                        double bsa = -bb * z / den;
+                        bx[i] += bsa * ratio * x / r + bsa * r * dratio * dthx;
+                        by[i] += bsa * ratio * y / r + bsa * r * dratio * dthy;
+                    }
+                    if (P->w_noise != 0.0) {
+                        double gx, gy, pd = popdense_grad(P, x, y, &gx, &gy);
+                        double za = z / P->A_c, h = 1.0 - za * za;
+                        if (h > 0.0) {
+                            bx[i] += gN[i] * h * gx;
+                            by[i] += gN[i] * h * gy;
+                            bz[i] += gN[i] * pd * (-2.0 * z / (P->A_c * P->A_c));
+                        }
+                    }
+                }
+                /* the step map k -> k+1 */
+                const int seg = (int)(((int64_t)k * S) / H);
+                const double *uu = ul + ((int64_t)i * S + seg) * 3;
+                const double w = uu[0], hd = uu[1], acc = uu[2];
+                const double v = c->v, mass = a->m - c->F, chi = c->chi;
+                const double sg = hd / v, cg = sqrt(1.0 - sg * sg);
+                const double dcg_dv = (hd * hd / (v * v * v)) / cg, dcg_dh = -(hd / (v * v)) / cg;
+                const double base = 1.0 - 2.2558e-5 * c->z;
+                const double rho = 1.225 * pow(base, 4.2559);
+                const double q = 0.5 * rho * v * v * a->S;
+                const double dq_dz = q * (4.2559 * -2.2558e-5 / base), dq_dv = 2.0 * q / v;
+                const double A2 = G0 * G0 * (1.0 - sg * sg) + w * w * v * v;
+                const double dA2_dv = 2.0 * G0 * G0 * hd * hd / (v * v * v) + 2.0 * w * w * v;
+                const double dA2_dh = -2.0 * G0 * G0 * hd / (v * v), dA2_dw = 2.0 * w * v * v;
+                const double K2 = a->CD2 * mass * mass;
+                const double D = q * a->CD0 + K2 * A2 / q;
+                const double T = mass * (acc + G0 * sg) + D;
+                const double dD_dv = a->CD0 * dq_dv + K2 * (dA2_dv / q - A2 * dq_dv / (q * q));
+                const double dD_dz = a->CD0 * dq_dz - K2 * A2 * dq_dz / (q * q);
+                const double dD_dm = 2.0 * a->CD2 * mass * A2 / q;
+                const double dT_dv = -mass * G0 * hd / (v * v) + dD_dv;
+                const double dT_dz = dD_dz;
+                const double dT_dm = acc + G0 * sg + dD_dm;
+                const double dT_dh = mass * G0 / v + K2 * dA2_dh / q;
+                const double dT_dw = K2 * dA2_dw / q;
+                const double dT_da = mass;
+                const double eta = a->Cf1 * (1.0 + v / a->Cf2), deta_dv = a->Cf1 / a->Cf2;
+                double wv[2], dw[2][3];
+                trilinear_grad(P, Wm + (int64_t)k * Pn * 2, c->x, c->y, c->z, wv, dw);
+                const double X = bx[i], Y = by[i], Z = bz[i], V = bv[i], CH = bc[i], FF = bF[i];
+                double nbx = X + dt * (X * dw[0][0] + Y * dw[1][0]);
+                double nby = Y + dt * (X * dw[0][1] + Y * dw[1][1]);
+                double nbz = Z + dt * (X * dw[0][2] + Y * dw[1][2]) + FF * dt * eta * dT_dz;
+                double nbv = V + dt * cos(chi) * (cg + v * dcg_dv) * X + dt * sin(chi) * (cg + v * dcg_dv) * Y +
+                             FF * dt * (deta_dv * T + eta * dT_dv);
+                double nbc = CH + dt * (-v * cg * sin(chi)) * X + dt * (v * cg * cos(chi)) * Y;
+                double nbF = FF * (1.0 - dt * eta * dT_dm);
+                double *gu = gs + ((int64_t)i * S + seg) * 3;
+                gu[0] += dt * CH + FF * dt * eta * dT_dw;
+                gu[1] += dt * Z + dt * v * dcg_dh * (cos(chi) * X + sin(chi) * Y) + FF * dt * eta * dT_dh;
+                gu[2] += dt * V + FF * dt * eta * dT_da;
+                bx[i] = nbx; by[i] = nby; bz[i] = nbz; bv[i] = nbv; bc[i] = nbc; bF[i] = nbF;
+            }
+        }
+        for (int n = 0; n < N * S * 3; n++) {
+            grad[n] += gs[n];
+            gs[n] = 0.0;
+        }
+        free(turb);
+    }
+    free(tr);
+    free(gs);
+    if (infeasible) {
+        for (int n = 0; n < N * S * 3; n++) grad[n] = 0.0;
+        return INFINITY;
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------ */
 /* the plant of the MPC loop (Sec. 2, Fig. 1)                            */
 /* ------------------------------------------------------------------ */
 

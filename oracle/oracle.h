@@ -90,6 +90,13 @@ void orc_trajectory(const orc_problem *P, const orc_aircraft *A, const double *W
                     const double *ul, int64_t l, int J, double *traj, double *cost_hard,
                     double *cost_soft);
 
+/* Soft objective C = sum_i mean_m c_soft[i][m] of particle l (controls
+ * ul[N][S][3], all M wind samples W[M][H][P][2], iteration J) and its
+ * gradient grad[N][S][3] by reverse mode; +inf (gradient 0) if infeasible.
+ * N <= 64. */
+double orc_rollout_grad(const orc_problem *P, const orc_aircraft *A, const double *W,
+                        const double *ul, int64_t l, int J, double *grad);
+
 /* One step of the true system (plant of the MPC loop): x_in/x_out[N][6]
  * (x, y, z, v, chi, m), W0 = wind field of sample 0 at step 0, u0[N][3]. */
 void orc_plant_step(const orc_problem *P, const orc_aircraft *A, const double *x_in,
