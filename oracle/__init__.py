@@ -89,6 +89,13 @@ def lib():
                                             i32, P(d), P(d), P(d)]
             _lib.orc_rollout_grad.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), i64, i32, P(d)]
             _lib.orc_rollout_grad.restype = d
+            _lib.orc_mh_propose.argtypes = [P(OrcProblem), P(d), P(d), i64, i32, d, d, i32, P(d),
+                                            P(C.c_uint8)]
+            _lib.orc_mh_propose.restype = None
+            _lib.orc_mh_accept.argtypes = [P(OrcProblem), P(d), P(d), P(d), P(d), P(d), P(d),
+                                           P(C.c_uint8), i64, i32, d, d, i32, P(d), P(C.c_uint8),
+                                           P(d)]
+            _lib.orc_mh_accept.restype = None
             _lib.orc_plant_step.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), P(d), P(d)]
             _lib.orc_kappa.argtypes = [i32]
             _lib.orc_kappa.restype = i32
@@ -354,6 +361,42 @@ def rollout_grad(p, u_l, W, l=0, J=0):
     c = lib().orc_rollout_grad(mm.ps, mm.ac, _ptr(Wc, C.c_double), _ptr(u, C.c_double), l, J,
                                _ptr(g, C.c_double))
     return c, g
+
+
+def mh_propose(p, u, grad, J, kappa, eps, kind):
+    """Proposal of the Metropolis-Hastings move (kind 1 random walk, 2 Langevin):
+    (u_prop [L][N][S][3], inbox [L])."""
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, p.N, p.S, 3)
+    L = u.shape[0]
+    g = np.ascontiguousarray(grad if grad is not None else np.zeros_like(u), np.float64)
+    up = np.empty_like(u)
+    inbox = np.empty(L, np.uint8)
+    mm = _Marshalled(p)
+    lib().orc_mh_propose(mm.ps, _ptr(u, C.c_double), _ptr(g, C.c_double), L, J, kappa, eps, kind,
+                         _ptr(up, C.c_double), _ptr(inbox, C.c_uint8))
+    return up, inbox
+
+
+def mh_accept(p, u, up, cbar, cbarp, g, gp, inbox, J, kappa, eps, kind):
+    """Accept step: (u_out, accepted [L], log_alpha [L])."""
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, p.N, p.S, 3)
+    L = u.shape[0]
+    up = np.ascontiguousarray(up, np.float64).reshape(u.shape)
+    z = np.zeros_like(u)
+    g = np.ascontiguousarray(g if g is not None else z, np.float64).reshape(u.shape)
+    gp = np.ascontiguousarray(gp if gp is not None else z, np.float64).reshape(u.shape)
+    cb = np.ascontiguousarray(cbar, np.float64).reshape(p.N, L)
+    cbp = np.ascontiguousarray(cbarp, np.float64).reshape(p.N, L)
+    ib = np.ascontiguousarray(inbox, np.uint8)
+    out = np.empty_like(u)
+    acc = np.empty(L, np.uint8)
+    la = np.empty(L)
+    mm = _Marshalled(p)
+    lib().orc_mh_accept(mm.ps, _ptr(u, C.c_double), _ptr(up, C.c_double), _ptr(cb, C.c_double),
+                        _ptr(cbp, C.c_double), _ptr(g, C.c_double), _ptr(gp, C.c_double),
+                        _ptr(ib, C.c_uint8), L, J, kappa, eps, kind, _ptr(out, C.c_double),
+                        _ptr(acc, C.c_uint8), _ptr(la, C.c_double))
+    return out, acc.astype(bool), la
 
 
 def plant_step(p, x, W0, u0):

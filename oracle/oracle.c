@@ -894,6 +894,92 @@ double orc_rollout_grad(const orc_problem *P, const orc_aircraft *A, const doubl
 }
 
 /* ------------------------------------------------------------------ */
+/* Metropolis-Hastings moves of whole particles (extension of the        */
+/* perturbation of Algorithm 1).  Target pi(u) ~ exp(-kappa C(u)),       */
+/* C = sum_i cbar_soft[i]; controls scaled by the move step sigma of     */
+/* their kind (z = u / sigma).                                           */
+/* ------------------------------------------------------------------ */
+
+/* standard normal number e of aircraft i of particle l for the proposal:
+ * random stream 5, draw e/4, words (0,1) -> first pair, (2,3) -> second */
+static double mh_normal(const orc_problem *P, int64_t l, int i, int e, int J)
+{
+    uint32_t r[4];
+    orc_draw(P, (uint32_t)l, (uint32_t)i, (uint32_t)(e / 4), 5u, (uint32_t)J, r);
+    double a, b;
+    if (e % 4 < 2) orc_box_muller(r[0], r[1], &a, &b);
+    else orc_box_muller(r[2], r[3], &a, &b);
+    return (e % 2 == 0) ? a : b;
+}
+
+void orc_mh_propose(const orc_problem *P, const double *u, const double *grad, int64_t L, int J,
+                    double kappa, double eps, int kind, double *u_prop, uint8_t *inbox)
+{
+    const int N = P->N, S = P->S;
+    for (int64_t l = 0; l < L; l++) {
+        int ok = 1;
+        for (int i = 0; i < N; i++)
+            for (int e = 0; e < 3 * S; e++) {
+                const int c = e % 3;
+                const int64_t o = (l * N + i) * 3 * S + e;
+                const double sg = P->move_sigma[c];
+                /* Langevin: z' = z - (eps^2/2) kappa grad_z C + eps xi, grad_z = sigma grad_u */
+                double z = u[o] / sg;
+                if (kind == 2) z -= 0.5 * eps * eps * kappa * sg * grad[o];
+                z += eps * mh_normal(P, l, i, e, J);
+                u_prop[o] = sg * z;
+                if (!(u_prop[o] >= P->ctrl_lo[c] && u_prop[o] <= P->ctrl_hi[c])) ok = 0;
+            }
+        inbox[l] = (uint8_t)ok;
+    }
+}
+
+void orc_mh_accept(const orc_problem *P, const double *u, const double *up, const double *cbar,
+                   const double *cbarp, const double *g, const double *gp, const uint8_t *inbox,
+                   int64_t L, int J, double kappa, double eps, int kind, double *u_out,
+                   uint8_t *accepted, double *log_alpha)
+{
+    const int N = P->N, S = P->S, nel = N * 3 * S;
+    for (int64_t l = 0; l < L; l++) {
+        double C = 0.0, Cp = 0.0;
+        int inf = 0, infp = 0;
+        for (int i = 0; i < N; i++) {
+            if (isinf(cbar[(int64_t)i * L + l])) inf = 1; else C += cbar[(int64_t)i * L + l];
+            if (isinf(cbarp[(int64_t)i * L + l])) infp = 1; else Cp += cbarp[(int64_t)i * L + l];
+        }
+        /* log of the Metropolis-Hastings ratio pi(u') q(u|u') / (pi(u) q(u'|u)) */
+        double la = -kappa * (Cp - C);
+        if (kind == 2) {
+            /* Gaussian proposal densities in z: q(z'|z) ~ exp(-|z' - m(z)|^2 / (2 eps^2)),
+             * m(z) = z - (eps^2/2) kappa grad_z C(z) */
+            const double d = 0.5 * eps * eps * kappa;
+            double fw = 0.0, bw = 0.0;
+            for (int n = 0; n < nel; n++) {
+                const int64_t o = l * nel + n;
+                const double sg = P->move_sigma[n % 3];
+                const double z = u[o] / sg, zp = up[o] / sg;
+                const double f = zp - (z - d * sg * g[o]);      /* z' - m(z)  */
+                const double b = z - (zp - d * sg * gp[o]);     /* z  - m(z') */
+                fw += f * f;
+                bw += b * b;
+            }
+            la += -(bw - fw) / (2.0 * eps * eps);
+        }
+        int acc;
+        if (!inbox[l] || infp) acc = 0;
+        else if (inf) acc = 1;
+        else {
+            uint32_t r[4];
+            orc_draw(P, (uint32_t)l, 0u, 0u, 6u, (uint32_t)J, r);
+            acc = log(orc_uniform23(r[0])) < la;
+        }
+        if (log_alpha) log_alpha[l] = (!inbox[l] || infp) ? -INFINITY : (inf ? INFINITY : la);
+        if (accepted) accepted[l] = (uint8_t)acc;
+        for (int n = 0; n < nel; n++) u_out[l * nel + n] = acc ? up[l * nel + n] : u[l * nel + n];
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* the plant of the MPC loop (Sec. 2, Fig. 1)                            */
 /* ------------------------------------------------------------------ */
 

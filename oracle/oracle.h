@@ -97,6 +97,19 @@ void orc_trajectory(const orc_problem *P, const orc_aircraft *A, const double *W
 double orc_rollout_grad(const orc_problem *P, const orc_aircraft *A, const double *W,
                         const double *ul, int64_t l, int J, double *grad);
 
+/* Metropolis-Hastings move of whole particles u[L][N][S][3] (kind 1 random
+ * walk, 2 Langevin): proposal from random stream 5 of iteration J, in-box
+ * flag per particle; accept with the 23-bit uniform of stream 6.  cbar and
+ * cbarp are per-aircraft soft means [N][L]; g, gp gradients [L][N][S][3]
+ * (kind 2 only).  log_alpha (may be NULL) receives the log acceptance ratio
+ * (-inf for a rejected-by-rule proposal, +inf for a forced accept). */
+void orc_mh_propose(const orc_problem *P, const double *u, const double *grad, int64_t L, int J,
+                    double kappa, double eps, int kind, double *u_prop, uint8_t *inbox);
+void orc_mh_accept(const orc_problem *P, const double *u, const double *up, const double *cbar,
+                   const double *cbarp, const double *g, const double *gp, const uint8_t *inbox,
+                   int64_t L, int J, double kappa, double eps, int kind, double *u_out,
+                   uint8_t *accepted, double *log_alpha);
+
 /* One step of the true system (plant of the MPC loop): x_in/x_out[N][6]
  * (x, y, z, v, chi, m), W0 = wind field of sample 0 at step 0, u0[N][3]. */
 void orc_plant_step(const orc_problem *P, const orc_aircraft *A, const double *x_in,
