@@ -417,6 +417,117 @@ def run_batched(args, local):
     return 0
 
 
+def run_moves(args, local):
+    """Moves between the SMC iterations on the softplus-separation workload
+    (12 aircraft, L 16384, M 16, H 60, 16x16x4 wind grid): the paper's clipped
+    random walk, a random walk with a Metropolis-Hastings accept step, and the
+    Langevin proposal with accept step.  For every seed (a new traffic scenario
+    and random streams) each kind solves with J_max on a ladder; the chosen
+    controls are scored on 256 held-out wind samples (random stream 8) as
+    sum_i cbar_soft[i].  Target: the paper move's held-out cost at the full
+    J_max.  Time to target = device time of the first ladder solve whose
+    held-out cost is at most the target."""
+    import numpy as np
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+    import scenarios as S
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    base = S.config4()
+    ladder = [j for j in (2, 4, 6, 8, 12, 16, 20, 25, 30) if j <= base.J_max]
+    kinds = {0: ("paper", None), 1: ("rw_mh", args.eps_rw), 2: ("mala", args.eps_mala)}
+    n_seeds = args.seeds
+    stream = torch.cuda.current_stream()
+
+    def timed_solve(p, kind):
+        sol = pkg.Solver(p)
+        if kind:
+            sol.set_move(kind, kinds[kind][1])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bu, _, _ = sol.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        acc = sol.mh_stats()[0] / p.L if kind else None
+        sol.close()
+        return bu, ms, acc
+
+    # warm-up (module load, autotuning, allocation paths)
+    for k in kinds:
+        timed_solve(base.copy(J_max=2), k)
+
+    res = {kinds[k][0]: {"heldout": [], "ms": []} for k in kinds}
+    acc_example = {}
+    for s in range(n_seeds):
+        p = S.config4(seed=base.seed + 1000 * s)
+        ev = pkg.Solver(p.copy(M=256, L=32))
+        ev.set_wind_stream(8)
+        ev.wind_field()
+        for k, (name, _) in kinds.items():
+            hs, ts = [], []
+            for J in ladder:
+                bu, ms, acc = timed_solve(p.copy(J_max=J), k)
+                _, cs = ev.rollout_cost(bu[None].contiguous(), 0, soft=True)
+                hs.append(float(cs[:, 0].double().sum().item()))
+                ts.append(ms)
+                if s == 0 and J == ladder[-1] and acc is not None:
+                    acc_example[name] = [round(float(a), 3) for a in acc]
+            res[name]["heldout"].append(hs)
+            res[name]["ms"].append(ts)
+        ev.close()
+    out = {"mode": "moves", "workload": "tma-12ac-L16384-M16-H60-grid16x16x4-softplus",
+           "seeds": n_seeds, "ladder_J_max": ladder, "heldout_samples": 256,
+           "eps0": {"rw_mh": args.eps_rw, "mala": args.eps_mala},
+           "acceptance_per_iteration_seed0": acc_example}
+    # one rollout and one gradient pass on the full workload (J = 3)
+    sol = pkg.Solver(base)
+    u = sol.init_controls()
+    sol.rollout_grad(u, 3)
+    cb = torch.empty((base.N, base.L), device="cuda")
+
+    def med_ms(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    ms_roll = med_ms(lambda: pkg.tma_rollout_cost(sol.h, u, 3, cb, torch.empty_like(cb)))
+    ms_grad = med_ms(lambda: sol.rollout_grad(u, 3))
+    gv, gt = pkg.tma_get_grad_tuning(sol.h)
+    sol.close()
+    out["full_workload_ms"] = {"rollout_soft": round(ms_roll, 3), "gradient": round(ms_grad, 3),
+                               "gradient_over_rollout": round(ms_grad / ms_roll, 2),
+                               "grad_variant": gv,
+                               "grad_variants_timed_ms": {str(k): round(v, 3) for k, v in gt.items()}}
+    target = np.array([h[-1] for h in res["paper"]["heldout"]])
+    for name, r in res.items():
+        H = np.array(r["heldout"])
+        T = np.array(r["ms"])
+        ttt = []
+        for s in range(n_seeds):
+            hit = np.nonzero(H[s] <= target[s])[0]
+            ttt.append(float(T[s, hit[0]]) if hit.size else float("inf"))
+        ttt = np.array(ttt)
+        out[name] = {
+            "median_time_to_target_ms": float(np.median(ttt)),
+            "reached": int(np.isfinite(ttt).sum()),
+            "median_heldout_cost_at_full_J": float(np.median(H[:, -1])),
+            "median_heldout_cost_per_rung": [round(float(v), 4) for v in np.median(H, axis=0)],
+            "median_solve_ms_per_rung": [round(float(v), 2) for v in np.median(T, axis=0)],
+        }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,12 +545,19 @@ def main(argv=None):
                     help="time the batched MPC workload (graph-captured receding-horizon steps)")
     ap.add_argument("--scenarios", type=int, default=256)
     ap.add_argument("--mpc-steps", type=int, default=10)
+    ap.add_argument("--moves", action="store_true",
+                    help="compare the paper's move with accepted random-walk and Langevin moves")
+    ap.add_argument("--seeds", type=int, default=10)
+    ap.add_argument("--eps-rw", type=float, default=1.0)
+    ap.add_argument("--eps-mala", type=float, default=0.3)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.rollout_only:
         return run_rollout_only(args, local)
     if args.batched:
         return run_batched(args, local)
+    if args.moves:
+        return run_moves(args, local)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local)

@@ -54,6 +54,12 @@ typedef enum {
 #define TMA_MAX_AIRCRAFT 32          /* N: one warp lane per aircraft */
 #define TMA_MAX_PARTICLES (1 << 22)  /* L: keeps the fixed-point CDF products in 128 bits */
 #define TMA_MAX_GRID_Z 16
+#define TMA_MAX_GRAD_HORIZON 320     /* H of tma_rollout_grad: checkpoints kept per thread */
+
+/* Move kinds of tma_set_move. */
+#define TMA_MOVE_PAPER 0   /* Gaussian random walk, clipped, no accept step (Algorithm 1) */
+#define TMA_MOVE_RWMH 1    /* random walk with a Metropolis-Hastings accept step */
+#define TMA_MOVE_MALA 2    /* Langevin proposal (gradient of the soft cost) with accept step */
 
 /* Scenario: the optimal-control problem of Sec. 2 and Sec. 3 (all host values). */
 typedef struct {
@@ -131,6 +137,12 @@ tma_status tma_set_state(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step
  * (float32 [M][H][P][2]).  Uses solver-owned scratch. */
 tma_status tma_wind_field(tma_solver *s, float *d_W, tma_stream_t stream);
 
+/* Random stream of the wind normals of this solver: 3 (default, the samples of
+ * the optimisation) or 8 (held-out samples, for evaluating a chosen control
+ * sequence on winds the optimisation did not see).  The next wind generation
+ * uses it; the current field is dropped. */
+tma_status tma_set_wind_stream(tma_solver *s, uint32_t stream);
+
 /* Rollout and costs (Algorithm 1 inner loop; Sec. 3.3-3.6, Sec. 7.1): for every
  * particle l < L of d_u (u[L][N][S][3]), every wind sample m < M of the
  * solver's current field and every aircraft, simulate H steps of Eq. (hor)
@@ -187,18 +199,89 @@ tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
 tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int32_t *h_variants,
                           float *h_ms);
 
+/* The same record for the kernel of tma_rollout_grad, tuned on its first use
+ * (tma_rollout_grad or tma_set_move with TMA_MOVE_MALA); *variant is -1 before. */
+tma_status tma_get_grad_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed,
+                               int32_t *h_variants, float *h_ms);
+
 /* Per-stage device time of the solver's launches (CUDA events recorded on the
  * launching stream around each stage when profiling is on).  Stages:
  * 0 wind generation, 1 initial controls, 2 rollout, 3 sample means, 4 LSE,
- * 5 resampling, 6 move, 7 selection.  tma_profile_read synchronises on the
- * recorded events, adds their durations to the totals and, if reset != 0,
+ * 5 resampling, 6 move, 7 selection, 8 gradient of the soft cost,
+ * 9 Metropolis-Hastings proposal and accept.  tma_profile_read synchronises on
+ * the recorded events, adds their durations to the totals and, if reset != 0,
  * clears the totals after copying them out. */
+#define TMA_N_STAGES 10
 typedef struct {
-    double ms[8];
-    uint64_t launches[8];
+    double ms[TMA_N_STAGES];
+    uint64_t launches[TMA_N_STAGES];
 } tma_profile;
 tma_status tma_profile_enable(tma_solver *s, int on);
 tma_status tma_profile_read(tma_solver *s, tma_profile *h_out, int reset);
+
+/* ------------------------------------------- gradient and accepted moves */
+
+/* Gradient of the soft cost (an extension: the paper's perturbation uses no
+ * gradient).  For particles l < L of d_u[L][N][S][3] (device) and the
+ * solver's current wind field, iteration J (keys the turbulence as in
+ * tma_rollout_cost): the objective C_l = sum_i (1/M) sum_m c_soft[i][m], the
+ * per-sample cost -ln J_T of Sec. 3.5-3.6 plus the softplus separation penalty
+ * mu sum sp_beta(min(1 - d_h/S_h, 1 - |dz|/S_v)) of Eq. (avoidance) in soft
+ * form, with the unary and control limits of Sec. 3.4 kept hard.  Writes
+ * d_cost[L] (+inf when any aircraft violates a hard limit in any sample),
+ * d_grad[L][N][S][3] = dC_l/du_l (zero for infeasible particles) and, if
+ * d_cbar_soft is not NULL, the per-aircraft means [N][L] (the same values as
+ * tma_rollout_cost's soft means).  Reverse mode over the discrete dynamics of
+ * Eq. (hor): limit, landing and interpolation-cell decisions are held at their
+ * forward values; states are recomputed from checkpoints taken every 10
+ * steps.  Valid for any sep_mode.  H must be <= TMA_MAX_GRAD_HORIZON
+ * (TMA_ERR_UNSUPPORTED otherwise).  Uses solver-owned scratch, allocated on the
+ * first call (not inside stream capture). */
+tma_status tma_rollout_grad(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *d_cost,
+                            float *d_grad, float *d_cbar_soft, tma_stream_t stream);
+
+/* Chooses the move between the iterations of tma_solve (Algorithm 1's
+ * perturbation step).  TMA_MOVE_PAPER (default): the paper's clipped Gaussian
+ * random walk.  TMA_MOVE_RWMH / TMA_MOVE_MALA (extensions, sep_mode != 0):
+ * after resampling, one Metropolis-Hastings step per particle with target
+ * exp(-kappa_J C(u)) (C as in tma_rollout_grad) and step eps (in units of the
+ * problem's move_sigma per control kind), starting at eps0 > 0 and adapted
+ * after every iteration: times 0.8 when fewer than half of the particles
+ * accepted, times 1.25 when more than 70 %.  See tma_mh_propose / tma_mh_accept
+ * for the proposal and the accept rule.  Allocates the move's scratch. */
+tma_status tma_set_move(tma_solver *s, int32_t kind, double eps0);
+
+/* Proposal of one Metropolis-Hastings move for particles l < L (device
+ * buffers [L][N][S][3]): with sigma = the problem's move_sigma per control kind
+ * and xi standard normal from random stream 5 of iteration J,
+ *   TMA_MOVE_RWMH   u' = u + eps sigma xi
+ *   TMA_MOVE_MALA   u' = u - (eps^2/2) kappa sigma^2 d_grad + eps sigma xi.
+ * d_inbox[l] = 1 when every control of u'_l lies in the control box (else the
+ * proposal will be rejected).  d_grad may be NULL for TMA_MOVE_RWMH. */
+tma_status tma_mh_propose(tma_solver *s, const float *d_u, const float *d_grad, int64_t L,
+                          int32_t J, double kappa, double eps, int32_t kind, float *d_u_prop,
+                          uint8_t *d_inbox, tma_stream_t stream);
+
+/* Accept step of that move: with C = sum_i d_cbar[i][l] and C' = sum_i
+ * d_cbar_prop[i][l] (per-aircraft soft means [N][L]),
+ *   log alpha = -kappa (C' - C) - (|z - z' + d g'|^2 - |z' - z + d g|^2) / (2 eps^2)
+ * for TMA_MOVE_MALA (z = u / sigma, g = sigma d_grad, g' = sigma d_grad_prop,
+ * d = (eps^2/2) kappa), -kappa (C' - C) for TMA_MOVE_RWMH; the particle moves
+ * when ln U < log alpha, U the 23-bit uniform of random stream 6 (FP64).  A
+ * proposal outside the box or with C' = +inf is rejected; from C = +inf any
+ * finite in-box proposal is accepted.  Writes d_u_out (may alias d_u) and,
+ * if not NULL, d_accepted[L] (0/1).  Gradients may be NULL for RWMH. */
+tma_status tma_mh_accept(tma_solver *s, const float *d_u, const float *d_u_prop,
+                         const float *d_cbar, const float *d_cbar_prop, const float *d_grad,
+                         const float *d_grad_prop, const uint8_t *d_inbox, int64_t L, int32_t J,
+                         double kappa, double eps, int32_t kind, float *d_u_out,
+                         uint8_t *d_accepted, tma_stream_t stream);
+
+/* Per-iteration record of the last tma_solve with an accepted move: for
+ * J < n, h_accepts[J] = particles that moved after iteration J and h_eps[J] =
+ * the step used there (either pointer may be NULL); n <= J_max - 1; syncs. */
+tma_status tma_mh_stats(tma_solver *s, uint32_t *h_accepts, double *h_eps, int32_t n,
+                        tma_stream_t stream);
 
 /* ------------------------------------------------------------ MPC plant */
 

@@ -60,7 +60,7 @@ class OrcProblem(C.Structure):
         ("pop_n", C.c_int * 2), ("pop_lo", C.c_double * 2), ("pop_hi", C.c_double * 2),
         ("popdense", C.POINTER(C.c_double)),
         ("P_runway", C.c_double), ("P_beta", C.c_double), ("P_chi", C.c_double),
-        ("P_vs", C.c_double), ("beta_f", C.c_double),
+        ("P_vs", C.c_double), ("beta_f", C.c_double), ("wind_stream", C.c_uint32),
     ]
 
 
@@ -131,6 +131,7 @@ class _Marshalled:
                   "v_max", "w_noise", "A_c", "P_runway", "P_beta", "P_chi", "P_vs", "beta_f"):
             setattr(s, n, float(getattr(p, n)))
         s.sep_mode = p.sep_mode
+        s.wind_stream = int(getattr(p, "wind_stream", 3))
         s.ctrl_lo[:], s.ctrl_hi[:], s.move_sigma[:] = p.ctrl_lo, p.ctrl_hi, p.move_sigma
         s.alpha_dep[:], s.alpha_arr[:] = p.alpha_dep, p.alpha_arr
         if p.popdense is not None:

@@ -140,7 +140,8 @@ void orc_wind_normals(const orc_problem *P, int m0, int mc, double *out)
         for (int k = 0; k < P->H; k++) {
             for (int64_t p = 0; p < Pn; p++) {
                 uint32_t w[4];
-                orc_draw(P, (uint32_t)p, (uint32_t)m << 8, (uint32_t)k, 3u, 0u, w);
+                orc_draw(P, (uint32_t)p, (uint32_t)m << 8, (uint32_t)k,
+                         P->wind_stream ? P->wind_stream : 3u, 0u, w);
                 double z0, z1;
                 orc_box_muller(w[0], w[1], &z0, &z1);
                 double *o = out + (((int64_t)mm * P->H + k) * Pn + p) * 2;

@@ -47,6 +47,8 @@ typedef struct {
     double pop_lo[2], pop_hi[2];
     const double *popdense;       /* [pop_n[0]][pop_n[1]] or NULL */
     double P_runway, P_beta, P_chi, P_vs, beta_f;
+    uint32_t wind_stream;         /* random stream of the wind normals: 3, or 8 for held-out
+                                     evaluation samples (0 reads as 3) */
 } orc_problem;
 
 typedef struct {

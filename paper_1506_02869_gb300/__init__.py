@@ -24,6 +24,8 @@ TMA_OK, TMA_ERR_INVALID_ARG, TMA_ERR_OOM, TMA_ERR_CUDA = 0, 1, 2, 3
 TMA_ERR_BOUNDS, TMA_ERR_TIMEOUT, TMA_WARN_DEGENERATE, TMA_ERR_UNSUPPORTED = 4, 5, 6, 7
 TMA_MAX_AIRCRAFT = 32
 TMA_MAX_PARTICLES = 1 << 22
+TMA_MAX_GRAD_HORIZON = 320
+TMA_MOVE_PAPER, TMA_MOVE_RWMH, TMA_MOVE_MALA = 0, 1, 2
 
 EXPORTS = [
     "tma_status_str", "tma_last_error_string", "tma_launch_count", "tma_create", "tma_destroy",
@@ -34,6 +36,8 @@ EXPORTS = [
     "tma_resample_noalloc", "tma_get_tuning", "tma_plant_step", "tma_get_state",
     "tma_batch_create", "tma_batch_destroy", "tma_batch_set_state", "tma_batch_solve",
     "tma_batch_mpc", "tma_batch_results", "tma_batch_latency", "tma_batch_live_steps",
+    "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
+    "tma_mh_stats", "tma_get_grad_tuning",
 ]
 
 
@@ -68,10 +72,11 @@ class TmaState(C.Structure):
 
 
 class TmaProfile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_uint64 * 8)]
+    _fields_ = [("ms", C.c_double * 10), ("launches", C.c_uint64 * 10)]
 
 
-STAGES = ("wind", "init", "rollout", "sample_mean", "lse", "resample", "move", "select")
+STAGES = ("wind", "init", "rollout", "sample_mean", "lse", "resample", "move", "select", "grad",
+          "mh")
 
 
 class TmaAircraft(C.Structure):
@@ -124,6 +129,7 @@ def lib():
                 "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_profile_enable": ([vp, C.c_int], C.c_int),
                 "tma_get_tuning": ([vp, P(i32), P(i32), P(i32), P(C.c_float)], C.c_int),
+                "tma_get_grad_tuning": ([vp, P(i32), P(i32), P(i32), P(C.c_float)], C.c_int),
                 "tma_plant_step": ([vp, vp, st], C.c_int),
                 "tma_get_state": ([vp, P(TmaState), P(u32), st], C.c_int),
                 "tma_batch_create": ([P(TmaProblem), P(P(TmaAircraft)), i32, P(vp)], C.c_int),
@@ -136,6 +142,13 @@ def lib():
                 "tma_batch_live_steps": ([vp, P(u64), st], C.c_int),
                 "tma_resample_noalloc": ([vp, i32, i64, u64, u32, u32, u32, vp, st], C.c_int),
                 "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
+                "tma_set_wind_stream": ([vp, u32], C.c_int),
+                "tma_rollout_grad": ([vp, vp, i64, i32, vp, vp, vp, st], C.c_int),
+                "tma_set_move": ([vp, i32, d], C.c_int),
+                "tma_mh_propose": ([vp, vp, vp, i64, i32, d, d, i32, vp, vp, st], C.c_int),
+                "tma_mh_accept": ([vp, vp, vp, vp, vp, vp, vp, vp, i64, i32, d, d, i32, vp, vp, st],
+                                  C.c_int),
+                "tma_mh_stats": ([vp, P(u32), P(d), i32, st], C.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -260,6 +273,10 @@ def tma_wind_field(h, out=None, stream=None):
     return out
 
 
+def tma_set_wind_stream(h, stream):
+    _check(lib().tma_set_wind_stream(h, int(stream)), "tma_set_wind_stream")
+
+
 def tma_rollout_cost(h, u, J, cbar, cbar_soft=None, stream=None):
     """u: cuda float32 [L][N][S][3]; writes cbar (and cbar_soft) [N][L]."""
     L = u.shape[0]
@@ -321,6 +338,14 @@ def tma_get_tuning(h):
     return v.value, {vs[k]: ms[k] for k in range(n.value)}
 
 
+def tma_get_grad_tuning(h):
+    """(chosen gradient-kernel variant, {variant: ms per launch} timed by its autotuner)."""
+    v, n = C.c_int32(), C.c_int32()
+    vs, ms = (C.c_int32 * 8)(), (C.c_float * 8)()
+    _check(lib().tma_get_grad_tuning(h, C.byref(v), C.byref(n), vs, ms), "tma_get_grad_tuning")
+    return v.value, {vs[k]: ms[k] for k in range(n.value)}
+
+
 def tma_profile_enable(h, on=True):
     _check(lib().tma_profile_enable(h, int(bool(on))), "tma_profile_enable")
 
@@ -330,6 +355,75 @@ def tma_profile_read(h, reset=True):
     prof = TmaProfile()
     _check(lib().tma_profile_read(h, C.byref(prof), int(bool(reset))), "tma_profile_read")
     return {name: (prof.ms[k], prof.launches[k]) for k, name in enumerate(STAGES)}
+
+
+# -------------------------------------------------- gradient and accepted moves
+
+def tma_rollout_grad(h, u, J, cost, grad, cbar_soft=None, stream=None):
+    """u: cuda float32 [L][N][S][3]; writes cost [L], grad [L][N][S][3] (and the
+    per-aircraft soft means [N][L])."""
+    _check(lib().tma_rollout_grad(h, _dptr(u), u.shape[0], int(J), _dptr(cost), _dptr(grad),
+                                  _dptr(cbar_soft), _stream(stream)), "tma_rollout_grad")
+
+
+def tma_set_move(h, kind, eps0=1.0):
+    _check(lib().tma_set_move(h, int(kind), float(eps0)), "tma_set_move")
+
+
+def tma_mh_propose(h, u, grad, J, kappa, eps, kind, u_prop, inbox, stream=None):
+    _check(lib().tma_mh_propose(h, _dptr(u), _dptr(grad), u.shape[0], int(J), float(kappa),
+                                float(eps), int(kind), _dptr(u_prop), _dptr(inbox),
+                                _stream(stream)), "tma_mh_propose")
+
+
+def tma_mh_accept(h, u, u_prop, cbar, cbar_prop, grad, grad_prop, inbox, J, kappa, eps, kind,
+                  u_out, accepted=None, stream=None):
+    _check(lib().tma_mh_accept(h, _dptr(u), _dptr(u_prop), _dptr(cbar), _dptr(cbar_prop),
+                               _dptr(grad), _dptr(grad_prop), _dptr(inbox), u.shape[0], int(J),
+                               float(kappa), float(eps), int(kind), _dptr(u_out), _dptr(accepted),
+                               _stream(stream)), "tma_mh_accept")
+
+
+def tma_mh_stats(h, n, stream=None):
+    """(accepted particles, step) per iteration of the last solve, n entries."""
+    acc = (C.c_uint32 * max(n, 1))()
+    eps = (C.c_double * max(n, 1))()
+    _check(lib().tma_mh_stats(h, acc, eps, int(n), _stream(stream)), "tma_mh_stats")
+    return np.array(acc[:n], np.int64), np.array(eps[:n])
+
+
+def _rollout_cost_function():
+    """torch.autograd.Function over tma_rollout_grad: C(u) [L] with dC/du."""
+    torch = _torch()
+
+    class RolloutCost(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u, solver, J):
+            u = u.detach().contiguous()
+            cost = torch.empty(u.shape[0], dtype=torch.float32, device=u.device)
+            grad = torch.empty_like(u)
+            tma_rollout_grad(solver.h, u, J, cost, grad)
+            ctx.save_for_backward(grad)
+            return cost
+
+        @staticmethod
+        def backward(ctx, g_cost):
+            (grad,) = ctx.saved_tensors
+            return g_cost.reshape(-1, 1, 1, 1) * grad, None, None
+
+    return RolloutCost
+
+
+_RolloutCost = None
+
+
+def rollout_cost_autograd(u, solver, J):
+    """Differentiable soft objective C(u) = sum_i cbar_soft[i] of each particle
+    (float32 [L]); backward multiplies the kernel's gradient."""
+    global _RolloutCost
+    if _RolloutCost is None:
+        _RolloutCost = _rollout_cost_function()
+    return _RolloutCost.apply(u, solver, J)
 
 
 # ------------------------------------------------------------- MPC plant
@@ -471,6 +565,7 @@ class Solver:
         torch = _torch()
         self.problem = problem
         self.N, self.S, self.L, self.M, self.H = (int(_get(problem, n)) for n in ("N", "S", "L", "M", "H"))
+        self.J_max = int(_get(problem, "J_max"))
         self.sep_mode = int(_get(problem, "sep_mode"))
         self.grid = tuple(int(v) for v in _get(problem, "grid"))
         self.device = torch.device(device if device is not None else "cuda")
@@ -532,6 +627,25 @@ class Solver:
 
     def best_index(self):
         return tma_best_index(self.h)
+
+    def rollout_grad(self, u, J, cbar=False):
+        """(cost [L], grad [L][N][S][3], per-aircraft soft means [N][L] or None)."""
+        torch = _torch()
+        L = u.shape[0]
+        cost = torch.empty(L, dtype=torch.float32, device=self.device)
+        grad = torch.empty_like(u)
+        cb = torch.empty((self.N, L), dtype=torch.float32, device=self.device) if cbar else None
+        tma_rollout_grad(self.h, u, J, cost, grad, cb)
+        return cost, grad, cb
+
+    def set_wind_stream(self, stream):
+        tma_set_wind_stream(self.h, stream)
+
+    def set_move(self, kind, eps0=1.0):
+        tma_set_move(self.h, kind, eps0)
+
+    def mh_stats(self):
+        return tma_mh_stats(self.h, self.J_max - 1)
 
 
 def lse(cbar, kappa):

@@ -289,7 +289,10 @@ static void free_all(tma_solver *s)
     void *ptrs[] = {s->d_dyn, s->d_Lxy, s->d_Btmp, s->d_W, s->d_u[0], s->d_u[1], s->d_cost_ms,
                     s->d_cost_ms_soft, s->d_cbar, s->d_cbar_soft, s->d_wtilde, s->d_anc,
                     s->d_popdense, s->d_work, s->d_best, s->d_best_sum, s->d_ninf, s->d_flags,
-                    s->d_live, s->d_best_u, s->d_probs1, s->d_scen1, s->d_seg_scen1};
+                    s->d_live, s->d_best_u, s->d_probs1, s->d_scen1, s->d_seg_scen1,
+                    s->d_gcost_ms, s->d_gpart, s->d_eps, s->d_nacc, s->d_acc_hist,
+                    s->d_eps_hist, s->d_u_prop, s->d_grad0, s->d_grad1, s->d_cbar0, s->d_cbar1,
+                    s->d_cost0, s->d_cost1, s->d_inbox};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -465,6 +468,7 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
             for (int c = 0; c <= r; ++c) w.Lz[r * TMA_MAX_GRID_Z + c] = (float)Rz[(size_t)r * nz + c];
         w.key0 = s->P.key0;
         w.key1 = s->P.key1;
+        w.stream = 3u;
         s->lda = lxy->lda;
         if ((e = alloc(&s->d_Lxy, lxy->L.size() * 4))) return fail(e);
         if ((e = cudaMemcpy(s->d_Lxy, lxy->L.data(), lxy->L.size() * 4, cudaMemcpyHostToDevice)))
@@ -546,6 +550,19 @@ tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int
     return TMA_OK;
 }
 
+tma_status tma_get_grad_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed,
+                               int32_t *h_variants, float *h_ms)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    if (variant) *variant = s->grad_variant;
+    if (n_timed) *n_timed = s->n_grad_tuned;
+    for (int c = 0; c < s->n_grad_tuned; ++c) {
+        if (h_variants) h_variants[c] = s->grad_tuned_variant[c];
+        if (h_ms) h_ms[c] = s->grad_tuned_ms[c];
+    }
+    return TMA_OK;
+}
+
 tma_status tma_profile_enable(tma_solver *s, int on)
 {
     if (!s) return TMA_ERR_INVALID_ARG;
@@ -566,7 +583,7 @@ tma_status tma_profile_read(tma_solver *s, tma_profile *h_out, int reset)
         s->event_pool.push_back(p.b);
     }
     s->pending.clear();
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < TMA_N_STAGES; ++k) {
         h_out->ms[k] = s->prof_ms[k];
         h_out->launches[k] = s->prof_n[k];
         if (reset) {
@@ -776,6 +793,316 @@ tma_status tma_init_controls(tma_solver *s, float *d_u, int64_t L, tma_stream_t 
     return TMA_OK;
 }
 
+// ------------------------------------------------------------------ gradient
+
+// Ranges of wind samples per gradient block: enough blocks for about two
+// waves of the device, at most one range per sample.
+static int grad_chunks(tma_solver *s, int64_t L, int variant)
+{
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (rollout_grad_occupancy(s->prob.N, variant, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const long long tiles = (L + kTileParticles - 1) / kTileParticles;
+    const long long want = 2LL * std::max(sms, 1) * per_sm;
+    long long c = (want + tiles - 1) / std::max(tiles, 1LL);
+    return (int)std::max(1LL, std::min<long long>(c, s->prob.M));
+}
+
+static tma_status ensure_grad_scratch(tma_solver *s, int64_t L, int nchunk)
+{
+    const tma_problem &p = s->prob;
+    if (!s->d_gcost_ms) {
+        cudaError_t e = alloc(&s->d_gcost_ms, (size_t)p.M * p.N * p.L * sizeof(float));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : record_cuda_error(e);
+    }
+    const size_t need = (size_t)nchunk * L * p.N * p.S * 3;
+    if (need > s->gpart_elems) {
+        if (s->d_gpart) cudaFree(s->d_gpart);
+        s->d_gpart = nullptr;
+        s->gpart_elems = 0;
+        cudaError_t e = alloc(&s->d_gpart, need * sizeof(float));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : record_cuda_error(e);
+        s->gpart_elems = need;
+    }
+    return TMA_OK;
+}
+
+// Choose the gradient kernel's launch-bound variant by timing every valid
+// candidate on this solver's workload (uniform controls, at most 4096
+// particles); cached per device and aircraft count.  The variants compute
+// the same arithmetic.
+static tma_status autotune_grad(tma_solver *s)
+{
+    if (s->grad_variant >= 0) return TMA_OK;
+    int cand[8];
+    const int nc = rollout_grad_variants(s->prob.N, cand);
+    s->grad_variant = cand[0];
+    s->n_grad_tuned = 0;
+    if (nc <= 1) return TMA_OK;
+    const std::string key = tune_key(s) + "|grad";
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            s->grad_variant = it->second;
+            return TMA_OK;
+        }
+    }
+    const int64_t Lp = std::min<int64_t>(s->prob.L, 4096);
+    const size_t nu = (size_t)Lp * s->prob.N * s->prob.S * 3;
+    int max_chunks = 1;
+    for (int c = 0; c < nc; ++c) max_chunks = std::max(max_chunks, grad_chunks(s, Lp, cand[c]));
+    tma_status r = ensure_grad_scratch(s, Lp, max_chunks);
+    if (r != TMA_OK) return r;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float *d_u = nullptr;
+    TMA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = alloc(&d_u, nu * sizeof(float));
+    float lo[3], hi[3], sg[3];
+    ctrl_f(s->prob, lo, hi, sg);
+    if (e == cudaSuccess && !s->wind_ready) {
+        r = gen_wind(s, st);
+        if (r != TMA_OK) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = launch_init_controls(s->P, s->d_dyn, lo, hi, d_u, Lp, st);
+    float best = 1e30f;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        const int nch = grad_chunks(s, Lp, cand[c]);
+        // one untimed launch, then two timed
+        e = launch_rollout_grad(s->P, s->d_dyn, d_u, s->d_W, Lp, 0, nch, s->d_gcost_ms, s->d_gpart,
+                                nullptr, nullptr, nullptr, st, cand[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)
+            e = launch_rollout_grad(s->P, s->d_dyn, d_u, s->d_W, Lp, 0, nch, s->d_gcost_ms,
+                                    s->d_gpart, nullptr, nullptr, nullptr, st, cand[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        s->grad_tuned_variant[s->n_grad_tuned] = cand[c];
+        s->grad_tuned_ms[s->n_grad_tuned] = ms / 2.0f;
+        ++s->n_grad_tuned;
+        if (ms < best) {
+            best = ms;
+            s->grad_variant = cand[c];
+        }
+    }
+    if (d_u) cudaFree(d_u);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (r != TMA_OK) return r;
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = s->grad_variant;
+    return TMA_OK;
+}
+
+static tma_status grad_into(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *cost,
+                            float *grad, float *cbar, cudaStream_t st)
+{
+    if (!s->wind_ready) {
+        tma_status r = gen_wind(s, st);
+        if (r != TMA_OK) return r;
+    }
+    tma_status r = autotune_grad(s);
+    if (r != TMA_OK) return r;
+    const int nchunk = grad_chunks(s, L, s->grad_variant);
+    r = ensure_grad_scratch(s, L, nchunk);
+    if (r != TMA_OK) return r;
+    StageTimer t(s, 8, st);
+    TMA_CUDA(launch_rollout_grad(s->P, s->d_dyn, d_u, s->d_W, L, J, nchunk, s->d_gcost_ms,
+                                 s->d_gpart, cost, grad, cbar, st, s->grad_variant));
+    return TMA_OK;
+}
+
+extern "C" tma_status tma_set_wind_stream(tma_solver *s, uint32_t stream)
+{
+    if (!s || (stream != 3u && stream != 8u)) return TMA_ERR_INVALID_ARG;
+    s->wind.stream = stream;
+    s->wind_ready = false;
+    return TMA_OK;
+}
+
+extern "C" tma_status tma_rollout_grad(tma_solver *s, const float *d_u, int64_t L, int32_t J,
+                                       float *d_cost, float *d_grad, float *d_cbar_soft,
+                                       tma_stream_t stream)
+{
+    if (!s || !d_u || !d_cost || !d_grad || L < 0 || L > s->prob.L || J < 0 || J > 0xFFFF)
+        return TMA_ERR_INVALID_ARG;
+    if (s->prob.H > TMA_MAX_GRAD_HORIZON) return TMA_ERR_UNSUPPORTED;
+    if (L == 0) return TMA_OK;
+    return grad_into(s, d_u, L, J, d_cost, d_grad, d_cbar_soft, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------- accepted moves
+
+static MhParams mh_params(const tma_solver *s, int kind)
+{
+    MhParams h;
+    std::memset(&h, 0, sizeof h);
+    h.N = s->prob.N;
+    h.S = s->prob.S;
+    h.langevin = kind == TMA_MOVE_MALA;
+    ctrl_f(s->prob, h.lo, h.hi, h.sigma);
+    h.key0 = s->P.key0;
+    h.key1 = s->P.key1;
+    return h;
+}
+
+static tma_status ensure_mh_scalars(tma_solver *s)
+{
+    if (s->d_eps) return TMA_OK;
+    const size_t nj = (size_t)std::max(s->prob.J_max, 1);
+    cudaError_t e = alloc(&s->d_eps, 2 * sizeof(double));
+    if (e == cudaSuccess) e = alloc(&s->d_nacc, sizeof(unsigned int));
+    if (e == cudaSuccess) e = alloc(&s->d_acc_hist, nj * sizeof(unsigned int));
+    if (e == cudaSuccess) e = alloc(&s->d_eps_hist, nj * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(s->d_nacc, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_acc_hist, 0, nj * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_eps_hist, 0, nj * sizeof(double));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : record_cuda_error(e);
+    return TMA_OK;
+}
+
+extern "C" tma_status tma_set_move(tma_solver *s, int32_t kind, double eps0)
+{
+    if (!s || kind < TMA_MOVE_PAPER || kind > TMA_MOVE_MALA) return TMA_ERR_INVALID_ARG;
+    if (kind == TMA_MOVE_PAPER) {
+        s->move_kind = kind;
+        return TMA_OK;
+    }
+    if (!(eps0 > 0.0) || !std::isfinite(eps0) || s->prob.sep_mode == 0) return TMA_ERR_INVALID_ARG;
+    if (kind == TMA_MOVE_MALA && s->prob.H > TMA_MAX_GRAD_HORIZON) return TMA_ERR_UNSUPPORTED;
+    tma_status r = ensure_mh_scalars(s);
+    if (r != TMA_OK) return r;
+    const tma_problem &p = s->prob;
+    const size_t nu = (size_t)p.L * p.N * p.S * 3, nc = (size_t)p.N * p.L;
+    cudaError_t e = cudaSuccess;
+    if (!s->d_u_prop) e = alloc(&s->d_u_prop, nu * 4);
+    if (e == cudaSuccess && !s->d_cbar0) e = alloc(&s->d_cbar0, nc * 4);
+    if (e == cudaSuccess && !s->d_cbar1) e = alloc(&s->d_cbar1, nc * 4);
+    if (e == cudaSuccess && !s->d_inbox) e = alloc(&s->d_inbox, (size_t)p.L);
+    if (kind == TMA_MOVE_MALA) {
+        if (e == cudaSuccess && !s->d_grad0) e = alloc(&s->d_grad0, nu * 4);
+        if (e == cudaSuccess && !s->d_grad1) e = alloc(&s->d_grad1, nu * 4);
+        if (e == cudaSuccess && !s->d_cost0) e = alloc(&s->d_cost0, (size_t)p.L * 4);
+        if (e == cudaSuccess && !s->d_cost1) e = alloc(&s->d_cost1, (size_t)p.L * 4);
+    }
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : record_cuda_error(e);
+    if (kind == TMA_MOVE_MALA) {
+        r = autotune_grad(s);
+        if (r == TMA_OK) r = ensure_grad_scratch(s, p.L, grad_chunks(s, p.L, s->grad_variant));
+        if (r != TMA_OK) return r;
+    }
+    s->move_kind = kind;
+    s->eps0 = eps0;
+    return TMA_OK;
+}
+
+static bool valid_mh(const tma_solver *s, int64_t L, int32_t J, double kappa, double eps, int kind)
+{
+    return s && L >= 0 && L <= s->prob.L && J >= 0 && J <= 0xFFFF && std::isfinite(kappa) &&
+           kappa >= 0.0 && eps > 0.0 && std::isfinite(eps) &&
+           (kind == TMA_MOVE_RWMH || kind == TMA_MOVE_MALA);
+}
+
+extern "C" tma_status tma_mh_propose(tma_solver *s, const float *d_u, const float *d_grad, int64_t L,
+                                     int32_t J, double kappa, double eps, int32_t kind,
+                                     float *d_u_prop, uint8_t *d_inbox, tma_stream_t stream)
+{
+    if (!valid_mh(s, L, J, kappa, eps, kind) || !d_u || !d_u_prop || !d_inbox ||
+        (kind == TMA_MOVE_MALA && !d_grad))
+        return TMA_ERR_INVALID_ARG;
+    if (L == 0) return TMA_OK;
+    tma_status r = ensure_mh_scalars(s);
+    if (r != TMA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    TMA_CUDA(cudaMemcpyAsync(s->d_eps + 1, &eps, sizeof(double), cudaMemcpyHostToDevice, st));
+    TMA_CUDA(launch_mh_propose(mh_params(s, kind), s->d_dyn, d_u, d_grad, L, J, (float)kappa,
+                               s->d_eps + 1, d_u_prop, d_inbox, st));
+    TMA_CUDA(cudaStreamSynchronize(st));     // the step lives in a stack variable
+    return TMA_OK;
+}
+
+extern "C" tma_status tma_mh_accept(tma_solver *s, const float *d_u, const float *d_u_prop,
+                                    const float *d_cbar, const float *d_cbar_prop,
+                                    const float *d_grad, const float *d_grad_prop,
+                                    const uint8_t *d_inbox, int64_t L, int32_t J, double kappa,
+                                    double eps, int32_t kind, float *d_u_out, uint8_t *d_accepted,
+                                    tma_stream_t stream)
+{
+    if (!valid_mh(s, L, J, kappa, eps, kind) || !d_u || !d_u_prop || !d_cbar || !d_cbar_prop ||
+        !d_inbox || !d_u_out || (kind == TMA_MOVE_MALA && (!d_grad || !d_grad_prop)))
+        return TMA_ERR_INVALID_ARG;
+    if (L == 0) return TMA_OK;
+    tma_status r = ensure_mh_scalars(s);
+    if (r != TMA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    TMA_CUDA(cudaMemcpyAsync(s->d_eps + 1, &eps, sizeof(double), cudaMemcpyHostToDevice, st));
+    TMA_CUDA(launch_mh_accept(mh_params(s, kind), s->d_dyn, d_u, d_u_prop, d_cbar, d_cbar_prop,
+                              d_grad, d_grad_prop, d_inbox, L, J, (float)kappa, s->d_eps + 1,
+                              d_u_out, nullptr, d_accepted, nullptr, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    return TMA_OK;
+}
+
+extern "C" tma_status tma_mh_stats(tma_solver *s, uint32_t *h_accepts, double *h_eps, int32_t n,
+                                   tma_stream_t stream)
+{
+    if (!s || n < 0 || n > std::max(s->prob.J_max - 1, 0)) return TMA_ERR_INVALID_ARG;
+    if (n == 0) return TMA_OK;
+    if (!s->d_acc_hist) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h_accepts)
+        TMA_CUDA(cudaMemcpyAsync(h_accepts, s->d_acc_hist, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    if (h_eps)
+        TMA_CUDA(cudaMemcpyAsync(h_eps, s->d_eps_hist, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
+    return TMA_OK;
+}
+
+// One accepted move of all particles at iteration J: u_cur holds the resampled
+// particles on entry and the moved ones on exit.
+static tma_status mh_move(tma_solver *s, float *u_cur, int J, cudaStream_t st)
+{
+    const tma_problem &p = s->prob;
+    const int kind = s->move_kind;
+    const float kappa = (float)kappa_of(J);
+    const MhParams h = mh_params(s, kind);
+    if (kind == TMA_MOVE_MALA) {
+        tma_status r = grad_into(s, u_cur, p.L, J, s->d_cost0, s->d_grad0, s->d_cbar0, st);
+        if (r != TMA_OK) return r;
+    } else {
+        tma_status r = rollout_into(s, u_cur, p.L, J, s->d_cbar, s->d_cbar0, st, false);
+        if (r != TMA_OK) return r;
+    }
+    {
+        StageTimer t(s, 9, st);
+        TMA_CUDA(launch_mh_propose(h, s->d_dyn, u_cur, s->d_grad0, p.L, J, kappa, s->d_eps,
+                                   s->d_u_prop, s->d_inbox, st));
+    }
+    if (kind == TMA_MOVE_MALA) {
+        tma_status r = grad_into(s, s->d_u_prop, p.L, J, s->d_cost1, s->d_grad1, s->d_cbar1, st);
+        if (r != TMA_OK) return r;
+    } else {
+        tma_status r = rollout_into(s, s->d_u_prop, p.L, J, s->d_cbar, s->d_cbar1, st, false);
+        if (r != TMA_OK) return r;
+    }
+    {
+        StageTimer t(s, 9, st);
+        TMA_CUDA(launch_mh_accept(h, s->d_dyn, u_cur, s->d_u_prop, s->d_cbar0, s->d_cbar1,
+                                  s->d_grad0, s->d_grad1, s->d_inbox, p.L, J, kappa, s->d_eps,
+                                  u_cur, nullptr, nullptr, s->d_nacc, st));
+        TMA_CUDA(launch_mh_adapt(s->d_eps, s->d_nacc, s->d_acc_hist, s->d_eps_hist, J, p.L, st));
+    }
+    return TMA_OK;
+}
+
 static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
 {
     const tma_problem &p = s->prob;
@@ -785,6 +1112,10 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
     if (r != TMA_OK) return r;
     TMA_CUDA(cudaMemsetAsync(s->d_flags, 0, 4, st));
     TMA_CUDA(cudaMemsetAsync(s->d_live, 0, 8, st));
+    if (s->move_kind != TMA_MOVE_PAPER) {
+        TMA_CUDA(cudaMemcpyAsync(s->d_eps, &s->eps0, sizeof(double), cudaMemcpyHostToDevice, st));
+        TMA_CUDA(cudaMemsetAsync(s->d_nacc, 0, sizeof(unsigned int), st));
+    }
     {
         StageTimer t(s, 1, st);
         TMA_CUDA(launch_init_controls(s->P, s->d_dyn, lo, hi, s->d_u[0], p.L, st));
@@ -809,10 +1140,16 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
             }
             {
                 StageTimer t(s, 6, st);
-                TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, sg, s->d_u[cur], s->d_anc, p.L, J,
-                                     s->d_u[cur ^ 1], st));
+                // the accepted moves start from the resampled particles themselves
+                const float zero[3] = {0.0f, 0.0f, 0.0f};
+                TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, s->move_kind == TMA_MOVE_PAPER ? sg : zero,
+                                     s->d_u[cur], s->d_anc, p.L, J, s->d_u[cur ^ 1], st));
             }
             cur ^= 1;
+            if (s->move_kind != TMA_MOVE_PAPER) {
+                r = mh_move(s, s->d_u[cur], J, st);
+                if (r != TMA_OK) return r;
+            }
         }
     }
     s->cur_u = cur;
@@ -1185,6 +1522,7 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
             const int nsc = std::min(gsz, n_scen - s0);
             WindC w;
             std::memset(&w, 0, sizeof w);
+            w.stream = 3u;
             w.M = nsc * p0.M;
             w.H = p0.H;
             w.nxy = nxy;

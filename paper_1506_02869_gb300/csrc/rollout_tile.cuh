@@ -100,6 +100,201 @@ __device__ __forceinline__ void tile_barrier(int id, int count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// State of one aircraft of one particle during a rollout (registers).
+struct AcState {
+    float x, y, z, v, chi;
+    Kahan F;                 // fuel burned
+    float zb, vb, cb;        // z, v, chi at the start of the current control segment
+    int seg, ks, knext;      // current segment, its first step, first step of the next
+    float uw, uh, ua;        // controls of the current segment
+    bool dead, landed;
+    float2 turb_next;        // second normal pair of the last even-step draw
+    float th;                // bearing atan2(y, x) of the step-(k+1) state
+    float beta;              // arrivals: glide angle of the step-(k+1) state
+};
+
+__device__ __forceinline__ void ac_init(AcState &s, const DynState *__restrict__ dyn, int i,
+                                        bool exists)
+{
+    s.x = dyn->x0[i][0];
+    s.y = dyn->x0[i][1];
+    s.z = dyn->x0[i][2];
+    s.v = dyn->x0[i][3];
+    s.chi = dyn->x0[i][4];
+    s.F = Kahan();
+    s.zb = s.vb = s.cb = 0.0f;
+    s.seg = -1;
+    s.ks = 0;
+    s.knext = 0;
+    s.uw = s.uh = s.ua = 0.0f;
+    s.dead = !exists;
+    s.landed = false;
+    s.turb_next = make_float2(0.0f, 0.0f);
+    s.th = s.beta = 0.0f;
+}
+
+// Per-step deviation sums of the objectives (Sec. 3.5, Sec. 7.1).
+struct CostSums {
+    Kahan sA, sB, sC;
+    float sN = 0.0f;
+    __device__ __forceinline__ void arrival(const ProblemC &P, const AircraftC &A, const AcState &s)
+    {
+        sA.add(angdist(s.chi - fmaf(2.0f, s.th, kPi)));
+        sB.add(fabsf(s.beta - P.beta_f));
+    }
+    __device__ __forceinline__ void departure(const ProblemC &P, const AircraftC &A, const AcState &s)
+    {
+        sA.add(angdist(s.th - A.thF));
+        sB.add(fabsf(A.Z - s.z));
+        sC.add(fabsf(s.v - A.vD));
+    }
+    __device__ __forceinline__ void noise(const ProblemC &P, const AircraftC &A, const AcState &s)
+    {
+        const float za = s.z * P.Ac_inv;
+        const float h = fmaxf(fmaf(-za, za, 1.0f), 0.0f);
+        sN = fmaf(h, popdense_at(P, s.x, s.y), sN);
+    }
+};
+
+// Advances one flying aircraft (not stopped before step k) by step k
+// (Sec. 3.3-3.4): control limits on the step-k values, explicit Euler step of
+// Eq. (hor) under wind and turbulence, unary limits and (arrivals) the landing
+// sector of Eq. (TO_init) on the step-(k+1) state.  When the aircraft is still
+// flying after the step, the visitor sees the new state (s.th, s.beta set):
+// visit.arrival or visit.departure, then visit.noise when the noise cost is
+// on.  Returns false when the control limits failed (the aircraft did not
+// move); otherwise s.dead / s.landed tell whether it stopped at this step.
+// ul = this particle's controls of this aircraft [S][3].
+template <class Visit>
+__device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, AcState &s,
+                                        const float *__restrict__ ul,
+                                        const float4 *__restrict__ Wk, float m0, uint32_t l,
+                                        uint32_t i, uint32_t m, int k, int J, uint32_t mpc,
+                                        Visit &visit)
+{
+    const float dt = P.dt;
+    if (k >= s.knext) {
+        // segment s = floor(k S / H) starts at step ceil(s H / S)
+        s.seg = (k * P.S) / P.H;
+        s.knext = ((s.seg + 1) * P.H + P.S - 1) / P.S;
+        s.ks = k;
+        s.uw = __ldg(ul + 3 * s.seg);
+        s.uh = __ldg(ul + 3 * s.seg + 1);
+        s.ua = __ldg(ul + 3 * s.seg + 2);
+        s.zb = s.z;
+        s.vb = s.v;
+        s.cb = s.chi;
+    }
+    const float mass = m0 - s.F.s;
+    // control-derived quantities and their limits (Sec. 3.4)
+    const float sg = __fdividef(s.uh, s.v);
+    bool ok = fabsf(sg) <= P.sgmax;
+    const float cg = sqrtf(fmaxf(1.0f - sg * sg, 0.0f));
+    const float tp = __fdividef(s.uw * s.v, kG0 * cg);
+    ok = ok && (fabsf(tp) < P.tpmax);
+    const float secphi = sqrtf(fmaf(tp, tp, 1.0f));
+    const float rho = 1.225f * exp2f(4.2559f * __log2f(fmaxf(fmaf(-2.2558e-5f, s.z, 1.0f), 1e-30f)));
+    const float qS = A.halfS * rho * s.v * s.v;
+    const float CL = __fdividef(mass * kG0 * cg * secphi, qS);
+    const float D = qS * fmaf(A.CD2, CL * CL, A.CD0);
+    const float T = fmaf(mass, fmaf(kG0, sg, s.ua), D);
+    ok = ok && (T >= A.Tmin) && (T <= A.Tmax);
+    if (!ok) {
+        s.dead = true;
+        return false;
+    }
+    // disturbance: wind field of sample m plus white turbulence
+    float2 w = wind_interp(wind_fetch(P, Wk, s.x, s.y, s.z));
+    float2 n;
+    if ((k & 1) == 0) {
+        const uint4 r = draw(P.key0, P.key1, l, i | (m << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
+        n = box_muller_fast(r.x, r.y);
+        s.turb_next = box_muller_fast(r.z, r.w);
+    } else {
+        n = s.turb_next;
+    }
+    w.x = fmaf(P.turb_sigma, n.x, w.x);
+    w.y = fmaf(P.turb_sigma, n.y, w.y);
+    // explicit Euler step of Eq. (hor); v sin(gamma) = hdot, the speed equation
+    // reduces to v += dt a and the heading equation to chi += dt w (coordinated
+    // turn).  Within a control segment z, v and chi are linear in time: they are
+    // evaluated from the segment's start values so that rounding does not
+    // accumulate.
+    float sc, cc;
+    sincos_reduced(s.chi, &sc, &cc);
+    const float vh = s.v * cg;
+    s.x = fmaf(dt, fmaf(vh, cc, w.x), s.x);
+    s.y = fmaf(dt, fmaf(vh, sc, w.y), s.y);
+    const float nk = (float)(k + 1 - s.ks) * dt;
+    s.z = fmaf(nk, s.uh, s.zb);
+    const float eta = A.Cf1 * fmaf(s.v, A.invCf2, 1.0f);
+    s.F.add(dt * eta * T);
+    s.v = fmaf(nk, s.ua, s.vb);
+    s.chi = fmaf(nk, s.uw, s.cb);
+    const float mass1 = m0 - s.F.s;
+    if (!(s.z >= P.z_min && s.z <= P.z_max && s.v >= P.v_min && s.v <= P.v_max &&
+          mass1 >= A.m_empty)) {
+        s.dead = true;
+    } else {
+        s.th = atan2f(s.y, s.x);
+        if (A.type == 0) {
+            // arrival: flow-field arc, glide angle and landing sector
+            const float r = sqrtf(fmaf(s.x, s.x, s.y * s.y));
+            const float ath = fabsf(s.th);
+            const float ratio = ath < 1e-3f ? fmaf(s.th * s.th, 1.0f / 6.0f, 1.0f)
+                                            : __fdividef(ath, fmaxf(__sinf(ath), 0.25f * ath));
+            s.beta = atan2f(s.z, r * ratio);
+            const float hdg = angdist(s.chi - kPi);
+            if (r <= P.P_runway && s.beta <= P.P_beta && s.x > 0.0f && ath <= P.P_chi &&
+                hdg <= P.P_chi && s.v <= P.P_vs) {
+                s.landed = true;
+            } else {
+                visit.arrival(P, A, s);
+            }
+        } else {
+            visit.departure(P, A, s);
+        }
+        if (P.w_noise != 0.0f && !s.landed) visit.noise(P, A, s);
+    }
+    return true;
+}
+
+// Departure altitude term: sup / inf of the per-step distance to Z reachable
+// from the current altitude at the maximum climb rate c (Sec. 3.5), in closed
+// form: sup = d0 + c (H+1)/2, inf = (K d0 - c K (K+1)/2) / H, K = min(H, floor(d0/c)).
+struct AltBounds {
+    float supB, invSupInf;
+};
+
+__device__ __forceinline__ AltBounds alt_bounds(const ProblemC &P, const AircraftC &A, float z0)
+{
+    const float d0 = fabsf(A.Z - z0);
+    const float supB = fmaf(P.climb_step, 0.5f * (float)(P.H + 1), d0);
+    const float Kf = fminf((float)P.H, floorf(__fdividef(d0, P.climb_step)));
+    const float infB = (Kf * d0 - P.climb_step * 0.5f * Kf * (Kf + 1.0f)) / (float)P.H;
+    return AltBounds{supB, 1.0f / (supB - infB)};
+}
+
+// J_T of Sec. 3.5 and Sec. 7.1 from the deviation sums and the fuel burned.
+__device__ __forceinline__ float total_objective(const ProblemC &P, const AircraftC &A,
+                                                 const CostSums &c, float Fs, AltBounds ab)
+{
+    const float invH = 1.0f / (float)P.H;
+    const float Jf = fmaf(-Fs, A.invFmax, 1.0f);
+    float Jsum;
+    if (A.type == 1) {
+        const float J1 = fmaf(-c.sA.s * invH, 1.0f / kPi, 1.0f);
+        const float J3 = (ab.supB - c.sB.s * invH) * ab.invSupInf;
+        const float J4 = fmaf(-c.sC.s * invH, A.invCmax, 1.0f);
+        Jsum = P.a_dep[0] * J1 + P.a_dep[1] * Jf + P.a_dep[2] * J3 + P.a_dep[3] * J4;
+    } else {
+        const float J1 = fmaf(-c.sA.s * invH, 1.0f / kPi, 1.0f);
+        const float J3 = fmaf(-c.sB.s * invH, 2.0f / kPi, 1.0f);
+        Jsum = P.a_arr[0] * J1 + P.a_arr[1] * J3 + P.a_arr[2] * Jf;
+    }
+    return (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-c.sN, invH, 1.0f);
+}
+
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
 // packed wind field Wm of sample m, and writes the per-sample costs
 // cost_ms[(m N + i) L + l] (and the softplus variant when cost_ms_soft is not
@@ -119,140 +314,38 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
     const bool exists = l < L;
     const AircraftC &A = P.ac[i];
     const uint32_t mpc = dyn->mpc_step;
-    const float dt = P.dt;
-
-    float x = dyn->x0[i][0], y = dyn->x0[i][1], z = dyn->x0[i][2];
-    float v = dyn->x0[i][3], chi = dyn->x0[i][4];
+    AcState s;
+    ac_init(s, dyn, i, exists);
     const float m0 = dyn->x0[i][5];
-    // departure altitude term: sup / inf of the per-step distance to Z reachable
-    // from the current altitude at the maximum climb rate c (Sec. 3.5), in closed
-    // form: sup = d0 + c (H+1)/2, inf = (K d0 - c K (K+1)/2) / H, K = min(H, floor(d0/c))
-    const float d0 = fabsf(A.Z - z);
-    const float supB = fmaf(P.climb_step, 0.5f * (float)(P.H + 1), d0);
-    const float Kf = fminf((float)P.H, floorf(__fdividef(d0, P.climb_step)));
-    const float infB = (Kf * d0 - P.climb_step * 0.5f * Kf * (Kf + 1.0f)) / (float)P.H;
-    const float invSupInf = 1.0f / (supB - infB);
-    Kahan F, sA, sB, sC;
-    float sN = 0.0f, soft = 0.0f;
-    bool dead = !exists, landed = false, sepv = false;
-    int seg = -1, ks = 0, knext = 0;
-    float uw = 0.0f, uh = 0.0f, ua = 0.0f;
-    // within a control segment z, v and chi are linear in time: evaluate them
-    // from the segment's start values so that rounding does not accumulate
-    float zb = 0.0f, vb = 0.0f, cb = 0.0f;
+    const AltBounds ab = alt_bounds(P, A, s.z);
+    CostSums cs;
+    float soft = 0.0f;
+    bool sepv = false;
     const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
-    float2 turb_next = make_float2(0.0f, 0.0f);
     unsigned int nlive = 0;
     const bool soft_on = cost_ms_soft != nullptr;
     const int plane = N * kPB;
 
     for (int k = 0; k < P.H; ++k) {
-        if (!dead && !landed) {
+        if (!s.dead && !s.landed) {
             ++nlive;
-            if (k >= knext) {
-                // segment s = floor(k S / H) starts at step ceil(s H / S)
-                seg = (k * P.S) / P.H;
-                knext = ((seg + 1) * P.H + P.S - 1) / P.S;
-                ks = k;
-                uw = __ldg(ul + 3 * seg);
-                uh = __ldg(ul + 3 * seg + 1);
-                ua = __ldg(ul + 3 * seg + 2);
-                zb = z;
-                vb = v;
-                cb = chi;
-            }
-            const float mass = m0 - F.s;
-            // control-derived quantities and their limits (Sec. 3.4)
-            const float sg = __fdividef(uh, v);
-            bool ok = fabsf(sg) <= P.sgmax;
-            const float cg = sqrtf(fmaxf(1.0f - sg * sg, 0.0f));
-            const float tp = __fdividef(uw * v, kG0 * cg);
-            ok = ok && (fabsf(tp) < P.tpmax);
-            const float secphi = sqrtf(fmaf(tp, tp, 1.0f));
-            const float rho = 1.225f * exp2f(4.2559f * __log2f(fmaxf(fmaf(-2.2558e-5f, z, 1.0f), 1e-30f)));
-            const float qS = A.halfS * rho * v * v;
-            const float CL = __fdividef(mass * kG0 * cg * secphi, qS);
-            const float D = qS * fmaf(A.CD2, CL * CL, A.CD0);
-            const float T = fmaf(mass, fmaf(kG0, sg, ua), D);
-            ok = ok && (T >= A.Tmin) && (T <= A.Tmax);
-            if (!ok) {
-                dead = true;
-            } else {
-                // disturbance: wind field of sample m plus white turbulence
-                float2 w = wind_interp(wind_fetch(P, Wm + (size_t)k * P.P, x, y, z));
-                float2 n;
-                if ((k & 1) == 0) {
-                    const uint4 r = draw(P.key0, P.key1, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8),
-                                         (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
-                    n = box_muller_fast(r.x, r.y);
-                    turb_next = box_muller_fast(r.z, r.w);
-                } else {
-                    n = turb_next;
-                }
-                w.x = fmaf(P.turb_sigma, n.x, w.x);
-                w.y = fmaf(P.turb_sigma, n.y, w.y);
-                // explicit Euler step of Eq. (hor); v sin(gamma) = hdot, the
-                // speed equation reduces to v += dt a and the heading equation
-                // to chi += dt w (coordinated turn)
-                float sc, cc;
-                sincos_reduced(chi, &sc, &cc);
-                const float vh = v * cg;
-                x = fmaf(dt, fmaf(vh, cc, w.x), x);
-                y = fmaf(dt, fmaf(vh, sc, w.y), y);
-                const float nk = (float)(k + 1 - ks) * dt;
-                z = fmaf(nk, uh, zb);
-                const float eta = A.Cf1 * fmaf(v, A.invCf2, 1.0f);
-                F.add(dt * eta * T);
-                v = fmaf(nk, ua, vb);
-                chi = fmaf(nk, uw, cb);
-                const float mass1 = m0 - F.s;
-                if (!(z >= P.z_min && z <= P.z_max && v >= P.v_min && v <= P.v_max &&
-                      mass1 >= A.m_empty)) {
-                    dead = true;
-                } else {
-                    const float th = atan2f(y, x);
-                    if (A.type == 0) {
-                        // arrival: flow-field arc, glide angle and landing sector
-                        const float r = sqrtf(fmaf(x, x, y * y));
-                        const float ath = fabsf(th);
-                        const float ratio = ath < 1e-3f ? fmaf(th * th, 1.0f / 6.0f, 1.0f)
-                                                        : __fdividef(ath, fmaxf(__sinf(ath), 0.25f * ath));
-                        const float beta = atan2f(z, r * ratio);
-                        const float hdg = angdist(chi - kPi);
-                        if (r <= P.P_runway && beta <= P.P_beta && x > 0.0f && ath <= P.P_chi &&
-                            hdg <= P.P_chi && v <= P.P_vs) {
-                            landed = true;
-                        } else {
-                            sA.add(angdist(chi - fmaf(2.0f, th, kPi)));
-                            sB.add(fabsf(beta - P.beta_f));
-                        }
-                    } else {
-                        sA.add(angdist(th - A.thF));
-                        sB.add(fabsf(A.Z - z));
-                        sC.add(fabsf(v - A.vD));
-                    }
-                    if (P.w_noise != 0.0f && !landed) {
-                        const float za = z * P.Ac_inv;
-                        const float h = fmaxf(fmaf(-za, za, 1.0f), 0.0f);
-                        sN = fmaf(h, popdense_at(P, x, y), sN);
-                    }
-                }
-            }
+            ac_step(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i, (uint32_t)m, k,
+                    J, mpc, cs);
         }
         // binary separation constraints at step k+1 among flying aircraft: every
         // thread publishes its position (a far-away altitude when not flying)
-        const bool act = !dead && !landed;
+        const bool act = !s.dead && !s.landed;
         float *buf = spos + (k & 1) * 3 * plane;
-        buf[i * kPB + j] = x;
-        buf[plane + i * kPB + j] = y;
-        buf[2 * plane + i * kPB + j] = act ? z : 1e30f;
+        buf[i * kPB + j] = s.x;
+        buf[plane + i * kPB + j] = s.y;
+        buf[2 * plane + i * kPB + j] = act ? s.z : 1e30f;
         tile_barrier(bar_id, bar_count);
         if (act) {
             for (int i2 = 0; i2 < N; ++i2) {
                 if (i2 == i) continue;
-                const float dx = x - buf[i2 * kPB + j];
-                const float dy = y - buf[plane + i2 * kPB + j];
-                const float adz = fabsf(z - buf[2 * plane + i2 * kPB + j]);
+                const float dx = s.x - buf[i2 * kPB + j];
+                const float dy = s.y - buf[plane + i2 * kPB + j];
+                const float adz = fabsf(s.z - buf[2 * plane + i2 * kPB + j]);
                 const float dh2 = fmaf(dx, dx, dy * dy);
                 if (dh2 < P.Sh2 && adz < P.Sv) sepv = true;
                 if (soft_on) {
@@ -264,26 +357,13 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
         }
     }
 
-    // objectives (Sec. 3.5, Sec. 7.1) and the per-sample cost -ln J_T
-    const float invH = 1.0f / (float)P.H;
-    const float Jf = fmaf(-F.s, A.invFmax, 1.0f);
-    float Jsum;
-    if (A.type == 1) {
-        const float J1 = fmaf(-sA.s * invH, 1.0f / kPi, 1.0f);
-        const float J3 = (supB - sB.s * invH) * invSupInf;
-        const float J4 = fmaf(-sC.s * invH, A.invCmax, 1.0f);
-        Jsum = P.a_dep[0] * J1 + P.a_dep[1] * Jf + P.a_dep[2] * J3 + P.a_dep[3] * J4;
-    } else {
-        const float J1 = fmaf(-sA.s * invH, 1.0f / kPi, 1.0f);
-        const float J3 = fmaf(-sB.s * invH, 2.0f / kPi, 1.0f);
-        Jsum = P.a_arr[0] * J1 + P.a_arr[1] * J3 + P.a_arr[2] * Jf;
-    }
-    const float JT = (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-sN, invH, 1.0f);
+    // the per-sample cost -ln J_T (Sec. 3.6)
+    const float JT = total_objective(P, A, cs, s.F.s, ab);
     const float c = -logf(fmaxf(JT, 1e-30f));
     if (exists) {
         const size_t o = ((size_t)m * N + i) * (size_t)L + l;
-        cost_ms[o] = (dead || sepv) ? __int_as_float(0x7f800000) : c;
-        if (soft_on) cost_ms_soft[o] = dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
+        cost_ms[o] = (s.dead || sepv) ? __int_as_float(0x7f800000) : c;
+        if (soft_on) cost_ms_soft[o] = s.dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
     }
     if (live != nullptr) {
         const unsigned int tot = __reduce_add_sync(0xffffffffu, exists ? nlive : 0u);

@@ -58,6 +58,7 @@ struct DynState {
 // Parameters of the wind-field generation kernels.
 struct WindC {
     int M, H, nxy, nz, ncol, ldb;
+    uint32_t stream;       // random stream of the normals: 3, or 8 for held-out samples
     float a, b, sigma;
     float Lz[TMA_MAX_GRID_Z * TMA_MAX_GRID_Z];
     uint32_t key0, key1;
@@ -72,6 +73,14 @@ struct BatchScen {
     long long items;      // its work items: M * ceil(nLb / T)
     int N, T;             // aircraft; particle tiles per CTA
     float ctrl_lo[3], ctrl_hi[3], move_sigma[3];
+    uint32_t key0, key1;
+};
+
+// Parameters of the Metropolis-Hastings move kernels (mala.cu).
+struct MhParams {
+    int N, S;
+    int langevin;          // 1: Langevin proposal and its proposal-density ratio
+    float sigma[3], lo[3], hi[3];
     uint32_t key0, key1;
 };
 
@@ -118,6 +127,29 @@ cudaError_t launch_select(const float *cbar, int N, int64_t L, int64_t *best, do
 size_t select_workspace(int64_t L);
 cudaError_t launch_gather_best(const float *u, const int64_t *best, int nctl_per_particle,
                                float *best_u, cudaStream_t st);
+
+// gradient of the soft cost (adjoint.cu): per-sample costs cost_ms[M][N][L],
+// partial gradients gpart[nchunk][L][N][S][3] over nchunk ranges of samples
+// (cost == nullptr: the main kernel only, for timing); variant indexes the
+// launch-bound table (rollout_grad_variants lists those valid for N)
+cudaError_t launch_rollout_grad(const ProblemC &P, const DynState *dyn, const float *u,
+                                const float *W, int64_t L, int J, int nchunk, float *cost_ms,
+                                float *gpart, float *cost, float *grad, float *cbar,
+                                cudaStream_t st, int variant);
+cudaError_t rollout_grad_occupancy(int N, int variant, int *blocks_per_sm);
+int rollout_grad_variants(int N, int *out);
+
+// Metropolis-Hastings moves (mala.cu)
+cudaError_t launch_mh_propose(const MhParams &h, const DynState *dyn, const float *u,
+                              const float *grad, int64_t L, int J, float kappa, const double *d_eps,
+                              float *u_prop, uint8_t *inbox, cudaStream_t st);
+cudaError_t launch_mh_accept(const MhParams &h, const DynState *dyn, const float *u, const float *up,
+                             const float *cbar, const float *cbarp, const float *g, const float *gp,
+                             const uint8_t *inbox, int64_t L, int J, float kappa,
+                             const double *d_eps, float *u_out, float *cbar_out, uint8_t *accepted,
+                             unsigned int *n_accept, cudaStream_t st);
+cudaError_t launch_mh_adapt(double *eps, unsigned int *n_accept, unsigned int *history,
+                            double *eps_history, int J, int64_t L, cudaStream_t st);
 
 // batched MPC (batch.cu)
 size_t batch_rollout_smem();
@@ -195,12 +227,30 @@ struct tma_solver {
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
-    double prof_ms[8] = {0};
-    uint64_t prof_n[8] = {0};
+    double prof_ms[TMA_N_STAGES] = {0};
+    uint64_t prof_n[TMA_N_STAGES] = {0};
     // one-scenario tables for the plant step (the batched plant kernel)
     tma::ProblemC *d_probs1 = nullptr;
     tma::BatchScen *d_scen1 = nullptr;
     int *d_seg_scen1 = nullptr;
+    // gradient scratch (allocated on first use)
+    float *d_gcost_ms = nullptr;        // [M][N][L]
+    float *d_gpart = nullptr;           // [nchunk][L][N][S][3]
+    size_t gpart_elems = 0;
+    int grad_variant = -1;              // autotuned launch variant of the gradient kernel
+    int n_grad_tuned = 0;
+    int grad_tuned_variant[8] = {0};
+    float grad_tuned_ms[8] = {0};
+    // accepted moves (tma_set_move)
+    int move_kind = 0;
+    double eps0 = 1.0;
+    double *d_eps = nullptr;            // [0] adapted step, [1] step of a stage call
+    unsigned int *d_nacc = nullptr;
+    unsigned int *d_acc_hist = nullptr; // [J_max]
+    double *d_eps_hist = nullptr;       // [J_max]
+    float *d_u_prop = nullptr, *d_grad0 = nullptr, *d_grad1 = nullptr;
+    float *d_cbar0 = nullptr, *d_cbar1 = nullptr, *d_cost0 = nullptr, *d_cost1 = nullptr;
+    uint8_t *d_inbox = nullptr;
     // autotuned launch variant of the rollout kernel and the timings behind it
     int rollout_variant = -1;
     int n_tuned = 0;

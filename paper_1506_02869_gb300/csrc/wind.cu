@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128) wind_normals_ar_kernel(const WindC w,
         for (int iz = 0; iz < TMA_MAX_GRID_Z; ++iz) {
             if (iz < nz) {
                 const uint4 r = draw(w.key0, w.key1, (uint32_t)(q * nz + iz), (uint32_t)m << 8,
-                                     (uint32_t)k, 3u, 0u, mpc);
+                                     (uint32_t)k, w.stream, 0u, mpc);
                 const float2 n = box_muller(r.x, r.y);
                 if (k == 0) {
                     B[0][iz] = n.x;

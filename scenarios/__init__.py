@@ -94,6 +94,7 @@ class Problem:
     P_chi: float = 20 * DEG
     P_vs: float = 90.0
     beta_f: float = 3 * DEG
+    wind_stream: int = 3                         # 8: held-out evaluation wind samples
     aircraft: Optional[np.ndarray] = None        # AIRCRAFT_DTYPE[N]
 
     def copy(self, **kw) -> "Problem":

@@ -26,7 +26,8 @@ _wind_cache = {}
 
 def oracle_wind(p):
     key = (p.seed, p.scenario_id, p.mpc_step, p.M, p.H, tuple(p.grid), tuple(p.box_lo),
-           tuple(p.box_hi), p.dt, p.lam_t, p.beta_xy, p.gam_z, p.wind_sigma)
+           tuple(p.box_hi), p.dt, p.lam_t, p.beta_xy, p.gam_z, p.wind_sigma,
+           getattr(p, "wind_stream", 3))
     if key not in _wind_cache:
         if len(_wind_cache) > 4:
             _wind_cache.clear()

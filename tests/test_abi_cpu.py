@@ -145,3 +145,21 @@ def test_batch_create_rejects_invalid_batches(lib):
     assert create([structs[0], bad_grid])[0] == pkg.TMA_ERR_INVALID_ARG
     assert lib.tma_batch_mpc(None, 1, 1, None) == pkg.TMA_ERR_INVALID_ARG
     assert lib.tma_plant_step(None, None, None) == pkg.TMA_ERR_INVALID_ARG
+
+
+def test_gradient_and_move_calls_reject_invalid_arguments(lib):
+    null = C.c_void_p()
+    L = lib
+    assert L.tma_rollout_grad(null, null, 1, 0, null, null, null, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_set_move(null, pkg.TMA_MOVE_MALA, 1.0) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_mh_propose(null, null, null, 1, 0, 1.0, 1.0, 2, null, null, null) == \
+        pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_mh_accept(null, null, null, null, null, null, null, null, 1, 0, 1.0, 1.0, 2, null,
+                           null, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_mh_stats(null, None, None, 1, null) == pkg.TMA_ERR_INVALID_ARG
+
+
+def test_profile_struct_has_every_stage():
+    src = open(HEADER).read()
+    n = int(re.search(r"#define TMA_N_STAGES (\d+)", src).group(1))
+    assert len(pkg.TmaProfile._fields_[0][1]()) == n == len(pkg.STAGES)

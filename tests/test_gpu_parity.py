@@ -42,6 +42,18 @@ def test_wind_field_matches_oracle(torch, pkg, cfg, M, H):
     solver.close()
 
 
+def test_held_out_wind_stream_matches_oracle(torch, pkg):
+    p = S.shrink(S.config4(), L=32, M=3, H=12)
+    solver = pkg.Solver(p)
+    w3 = solver.wind_field().double().cpu().numpy()
+    solver.set_wind_stream(8)
+    w8 = solver.wind_field().double().cpu().numpy()
+    solver.close()
+    ref8 = O.wind_field(p.copy(wind_stream=8))
+    assert np.abs(w8 - ref8).max() / p.wind_sigma < 2e-5
+    assert np.abs(w3 - ref8).max() > 0.5 * p.wind_sigma      # an independent field
+
+
 # ---------------------------------------------------------------- rollout
 
 def _rollout_case(torch, pkg, p, u, J, pidx=None, soft=False, what=""):

@@ -130,3 +130,15 @@ def test_positions_outside_box_use_face_values():
     W[..., 1] = np.where(X == xs[-1], 4.0, -9.0)     # only the x_hi face blows +4 in y
     traj = _straight(p, W)
     assert np.allclose(traj[:, 0, 1], 4.0 * p.dt * np.arange(p.H + 1), atol=1e-9)
+
+
+def test_held_out_wind_stream_is_independent():
+    """Stream 8 gives the same distribution as stream 3 (the model of Sec. 3.9.1)
+    and independent draws."""
+    p = S.shrink(S.config1(), M=4, H=6)
+    v3 = O.wind_normals(p)
+    v8 = O.wind_normals(p.copy(wind_stream=8))
+    assert v3.shape == v8.shape
+    assert abs(np.corrcoef(v3.ravel(), v8.ravel())[0, 1]) < 0.05
+    assert abs(v8.std() - 1.0) < 0.05 and abs(v8.mean()) < 0.05
+    assert np.array_equal(O.wind_normals(p.copy(wind_stream=3)), v3)
