@@ -17,6 +17,7 @@ cores (rank 0 only) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -60,6 +61,21 @@ def flops_per_unit(p):
     frac_arr = float(np.mean(p.aircraft["type"] == 0))
     return base + wind + turb + euler + frac_arr * arr + (1 - frac_arr) * dep + noise + \
         pair * (p.N - 1) / 2.0
+
+
+# DRAM bytes (read + write) of one full-size rollout launch of the 8-aircraft
+# workload, from a one-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, iteration 20 of a solve); valid only for the kernel
+# sources it was taken on.
+ROLLOUT_TRAFFIC = {"bytes_per_launch": 1.00e9 + 68.23e6, "sources_sha256_16": "e3608d6f27f3ab21"}
+
+
+def rollout_sources_digest():
+    h = hashlib.sha256()
+    for f in ("rollout.cu", "rollout_tile.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1506_02869_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -297,7 +313,9 @@ def run_ours(args, world, rank, local):
     total_ms = sum(v[0] for v in prof.values())
     roofline = {
         "bound": "alu", "kernel": "rollout_kernel", "achieved": achieved, "peak": peak,
-        "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+        "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+        "traffic": (ROLLOUT_TRAFFIC["bytes_per_launch"]
+                    if rollout_sources_digest() == ROLLOUT_TRAFFIC["sources_sha256_16"] else None),
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
         "flops_per_unit": fpu, "live_units_per_launch": live_per_launch,
         "units_per_launch": p.L * p.M * p.N * p.H, "launch_ms": roll_ms / roll_n if roll_n else None,
@@ -316,7 +334,7 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "L": p.L, "M": p.M, "N": p.N, "H": p.H, "J_max": p.J_max,
                    "grid": list(p.grid), "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (wind field 503 MB per solve)"},
+                   "l2": "inputs larger than L2 (packed wind field 1.0 GB per solve)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x0.numel() * 8),
                 "d2h_bytes_per_step": int(out_h.numel() * 4 + 8 + 4)},
         "gpu_launches": int(launches),
@@ -350,23 +368,136 @@ def run_rollout_only(args, local):
 
     torch.cuda.set_device(local)
     pkg.build()
-    p = S.config2().copy(L=args.particles or 4096)
+    p = S.make_config(args.config).copy(L=args.particles or 4096)
     solver = pkg.Solver(p)
-    u = solver.init_controls()
+    if args.late:
+        # the particles of a finished solve: the live mix of the late iterations
+        solver.solve()
+        u = solver.particles()
+        J0 = p.J_max - 1
+    else:
+        u = solver.init_controls()
+        J0 = 0
+    soft = p.sep_mode != 0        # the solve's rollout computes the soft costs too
     for _ in range(args.warmup):
-        solver.rollout_cost(u, 0)
+        solver.rollout_cost(u, J0, soft=soft)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for j in range(args.steps):
-        solver.rollout_cost(u, j)
+        solver.rollout_cost(u, J0, soft=soft)
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / max(args.steps, 1)
     units = p.L * p.M * p.N * p.H
-    print(json.dumps({"mode": "rollout-only", "particles": p.L, "ms_per_rollout": ms,
+    print(json.dumps({"mode": "rollout-only", "config": args.config, "N": p.N, "late": bool(args.late),
+                      "particles": p.L, "ms_per_rollout": ms,
                       "units_per_s": units / (ms * 1e-3), "live_steps": solver.live_steps()}))
     solver.close()
+    return 0
+
+
+def run_grad_only(args, local):
+    """Small gradient-only case for kernel profiling: the softplus-separation
+    workload (12 aircraft, M 16, H 60) with `--particles` particles, uniform
+    controls, K gradient passes."""
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+    import scenarios as S
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    p = S.config4().copy(L=args.particles or 4096)
+    solver = pkg.Solver(p)
+    if args.late:
+        solver.solve()
+        u = solver.particles()
+        J0 = p.J_max - 1
+    else:
+        u = solver.init_controls()
+        J0 = 0
+    for _ in range(args.warmup):
+        solver.rollout_grad(u, J0)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for j in range(args.steps):
+        solver.rollout_grad(u, J0)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / max(args.steps, 1)
+    units = p.L * p.M * p.N * p.H
+    print(json.dumps({"mode": "grad-only", "late": bool(args.late), "particles": p.L, "ms_per_gradient": ms,
+                      "units_per_s": units / (ms * 1e-3),
+                      "grad_tuning": pkg.tma_get_grad_tuning(solver.h)}))
+    solver.close()
+    return 0
+
+
+def run_stages(args, local):
+    """The HBM-side stages between rollouts on the 24-aircraft workload (L 262144):
+    FP64 log-weight normalisation, systematic resampling and gather + move, each
+    timed alone with CUDA events (median of K launches, inputs larger than L2).
+    Algorithmic bytes per (aircraft, particle): normalisation 4 B read + 8 B
+    written; resampling 8 B read + 4 B written; move 4 B ancestor + 48 B parent +
+    48 B child."""
+    import numpy as np
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+    import scenarios as S
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    p = S.config3()
+    N, L = p.N, p.L
+    g = torch.Generator(device="cuda").manual_seed(7)
+    cbar = (2.0 * torch.rand((N, L), device="cuda", generator=g)).float()
+    cbar[torch.rand((N, L), device="cuda", generator=g) < 0.05] = float("inf")
+    wt = torch.empty((N, L), dtype=torch.float64, device="cuda")
+    anc = torch.empty((N, L), dtype=torch.int32, device="cuda")
+    sol = pkg.Solver(p)
+    u = sol.init_controls()
+    u2 = torch.empty_like(u)
+    lwork = torch.empty(pkg.lib().tma_lse_workspace(N, L), dtype=torch.uint8, device="cuda")
+    rwork = torch.empty(pkg.lib().tma_resample_workspace(N, L), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def med_ms(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(max(args.steps, 1)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    kappa = 11.0
+    ms = {
+        "lse": med_ms(lambda: pkg.tma_lse(cbar, kappa, wt, work=lwork)),
+        "resample": med_ms(lambda: pkg.tma_resample(wt, p.seed, 0, 3, 0, anc, work=rwork)),
+        "move": med_ms(lambda: pkg.tma_move(sol.h, u, anc, 3, u2)),
+    }
+    sol.close()
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_source = "measured" if peaks.get("hbm_gbs") else "fallback"
+    n = N * L
+    algo = {"lse": 12, "resample": 12, "move": 100}
+    out = {"mode": "stages", "workload": "tma-24ac-L262144 (nseg 24)", "elements": n,
+           "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_source, "stages": {}}
+    for k, v in ms.items():
+        gbs = algo[k] * n / (v * 1e-3) / 1e9
+        out["stages"][k] = {"ms": round(v, 4), "algorithmic_bytes_per_element": algo[k],
+                            "achieved_gbs": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm, 3)}
+    # the normalisation evaluates one FP64 exp per element
+    out["stages"]["lse"]["fp64_exp_per_s"] = round(n / (ms["lse"] * 1e-3), 1)
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -545,6 +676,14 @@ def main(argv=None):
                     help="time the batched MPC workload (graph-captured receding-horizon steps)")
     ap.add_argument("--scenarios", type=int, default=256)
     ap.add_argument("--mpc-steps", type=int, default=10)
+    ap.add_argument("--config", type=int, default=2,
+                    help="workload of --rollout-only (1-4)")
+    ap.add_argument("--stages", action="store_true",
+                    help="time normalisation, resampling and move alone on the 24-aircraft sizes")
+    ap.add_argument("--late", action="store_true",
+                    help="profiling cases: use the particles of a finished solve (late iterations)")
+    ap.add_argument("--grad-only", action="store_true",
+                    help="time only the gradient pass on --particles particles (profiling case)")
     ap.add_argument("--moves", action="store_true",
                     help="compare the paper's move with accepted random-walk and Langevin moves")
     ap.add_argument("--seeds", type=int, default=10)
@@ -558,6 +697,10 @@ def main(argv=None):
         return run_batched(args, local)
     if args.moves:
         return run_moves(args, local)
+    if args.grad_only:
+        return run_grad_only(args, local)
+    if args.stages:
+        return run_stages(args, local)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local)

@@ -186,6 +186,11 @@ tma_status tma_solve(tma_solver *s, float *d_best_u, double *h_best_cost, tma_st
 tma_status tma_solve_host(tma_solver *s, const tma_state *h_x0, uint32_t mpc_step, float *h_best_u,
                           double *h_best_cost, tma_stream_t stream);
 
+/* The particle set of the last tma_solve after its final iteration (the set
+ * the selection of Sec. 3.8 chose from): d_u_out[L][N][S][3] (device,
+ * caller-owned), L <= the solver's L (the first L particles). */
+tma_status tma_get_particles(tma_solver *s, float *d_u_out, int64_t L, tma_stream_t stream);
+
 /* Index of the particle chosen by the last tma_solve (host); syncs. */
 tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
 
@@ -292,6 +297,21 @@ tma_status tma_mh_stats(tma_solver *s, uint32_t *h_accepts, double *h_eps, int32
  * state replaces the solver's state on the device and the MPC step advances by
  * one (the next solve draws new random numbers).  Syncs the stream. */
 tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream);
+/* Receding-horizon control of Fig. 1 (Sec. 2): n_steps times, one tma_solve
+ * from the current state followed by tma_plant_step with the chosen controls.
+ * h_traj[n_steps][N] (host) receives the state after each plant step and, if
+ * not NULL, h_costs[n_steps] the chosen particle's cost sum of each solve.
+ * Syncs once per step.  Returns TMA_WARN_DEGENERATE when some solve had an all-
+ * zero weight segment. */
+tma_status tma_mpc_run(tma_solver *s, int32_t n_steps, tma_state *h_traj, double *h_costs,
+                       tma_stream_t stream);
+
+/* Sticky device status of the solves since the last call: bit 0 some weight
+ * segment was all zero (identity ancestors were used), bit 1 the chosen
+ * particle had an infeasible aircraft (no particle satisfied every limit).
+ * Clears the word; syncs. */
+tma_status tma_get_error(tma_solver *s, uint32_t *h_err, tma_stream_t stream);
+
 /* The solver's current state h_x[N] (host) and MPC step; syncs. */
 tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream);
 

@@ -37,7 +37,7 @@ EXPORTS = [
     "tma_batch_create", "tma_batch_destroy", "tma_batch_set_state", "tma_batch_solve",
     "tma_batch_mpc", "tma_batch_results", "tma_batch_latency", "tma_batch_live_steps",
     "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
-    "tma_mh_stats", "tma_get_grad_tuning",
+    "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
 ]
 
 
@@ -121,6 +121,7 @@ def lib():
                 "tma_solve": ([vp, vp, P(d), st], C.c_int),
                 "tma_solve_host": ([vp, P(TmaState), u32, vp, P(d), st], C.c_int),
                 "tma_best_index": ([vp, P(i64), st], C.c_int),
+                "tma_get_particles": ([vp, vp, i64, st], C.c_int),
                 "tma_lse_workspace": ([i32, i64], sz),
                 "tma_lse": ([vp, i32, i64, d, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_resample_workspace": ([i32, i64], sz),
@@ -132,6 +133,8 @@ def lib():
                 "tma_get_grad_tuning": ([vp, P(i32), P(i32), P(i32), P(C.c_float)], C.c_int),
                 "tma_plant_step": ([vp, vp, st], C.c_int),
                 "tma_get_state": ([vp, P(TmaState), P(u32), st], C.c_int),
+                "tma_mpc_run": ([vp, i32, P(TmaState), P(d), st], C.c_int),
+                "tma_get_error": ([vp, P(u32), st], C.c_int),
                 "tma_batch_create": ([P(TmaProblem), P(P(TmaAircraft)), i32, P(vp)], C.c_int),
                 "tma_batch_destroy": ([vp], None),
                 "tma_batch_set_state": ([vp, P(TmaState), P(u32), st], C.c_int),
@@ -324,6 +327,13 @@ def tma_solve_host(h, x0, mpc_step, best_u_host, stream=None):
     return st, c.value
 
 
+def tma_get_particles(h, out, stream=None):
+    """Copy the last solve's particle set into out (cuda float32 [L][N][S][3])."""
+    _check(lib().tma_get_particles(h, _dptr(out), out.shape[0], _stream(stream)),
+           "tma_get_particles")
+    return out
+
+
 def tma_best_index(h, stream=None):
     v = C.c_int64()
     _check(lib().tma_best_index(h, C.byref(v), _stream(stream)), "tma_best_index")
@@ -432,6 +442,23 @@ def tma_plant_step(h, u, stream=None):
     """Advance the solver's true state by one step with the segment-0 controls of
     u (cuda float32 [N][S][3])."""
     _check(lib().tma_plant_step(h, _dptr(u), _stream(stream)), "tma_plant_step")
+
+
+def tma_mpc_run(h, n_steps, N, stream=None):
+    """n receding-horizon steps (solve + plant): (states [n][N][6], best costs [n], status)."""
+    traj = (TmaState * max(n_steps * N, 1))()
+    costs = (C.c_double * max(n_steps, 1))()
+    st = lib().tma_mpc_run(h, int(n_steps), traj, costs, _stream(stream))
+    _check(st, "tma_mpc_run", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+    x = np.array([[getattr(traj[t * N + i], f) for f in ("x", "y", "z", "v", "chi", "m")]
+                  for t in range(n_steps) for i in range(N)]).reshape(n_steps, N, 6)
+    return x, np.array(costs[:n_steps]), st
+
+
+def tma_get_error(h, stream=None):
+    v = C.c_uint32()
+    _check(lib().tma_get_error(h, C.byref(v), _stream(stream)), "tma_get_error")
+    return v.value
 
 
 def tma_get_state(h, N, stream=None):
@@ -627,6 +654,12 @@ class Solver:
 
     def best_index(self):
         return tma_best_index(self.h)
+
+    def particles(self, L=None):
+        torch = _torch()
+        L = self.L if L is None else L
+        out = torch.empty((L, self.N, self.S, 3), dtype=torch.float32, device=self.device)
+        return tma_get_particles(self.h, out)
 
     def rollout_grad(self, u, J, cbar=False):
         """(cost [L], grad [L][N][S][3], per-aircraft soft means [N][L] or None)."""

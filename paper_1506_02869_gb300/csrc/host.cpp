@@ -288,7 +288,7 @@ static void free_all(tma_solver *s)
 {
     void *ptrs[] = {s->d_dyn, s->d_Lxy, s->d_Btmp, s->d_W, s->d_u[0], s->d_u[1], s->d_cost_ms,
                     s->d_cost_ms_soft, s->d_cbar, s->d_cbar_soft, s->d_wtilde, s->d_anc,
-                    s->d_popdense, s->d_work, s->d_best, s->d_best_sum, s->d_ninf, s->d_flags,
+                    s->d_popdense, s->d_work, s->d_best, s->d_best_sum, s->d_ninf, s->d_flags, s->d_err,
                     s->d_live, s->d_best_u, s->d_probs1, s->d_scen1, s->d_seg_scen1,
                     s->d_gcost_ms, s->d_gpart, s->d_eps, s->d_nacc, s->d_acc_hist,
                     s->d_eps_hist, s->d_u_prop, s->d_grad0, s->d_grad1, s->d_cbar0, s->d_cbar1,
@@ -493,6 +493,8 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
         if ((e = alloc(&s->d_best_sum, 8))) return fail(e);
         if ((e = alloc(&s->d_ninf, 4))) return fail(e);
         if ((e = alloc(&s->d_flags, 4))) return fail(e);
+        if ((e = alloc(&s->d_err, 4))) return fail(e);
+        if ((e = cudaMemset(s->d_err, 0, 4))) return fail(e);
         if ((e = alloc(&s->d_live, 8))) return fail(e);
         if ((e = alloc(&s->d_best_u, N * p.S * 3 * 4))) return fail(e);
         if ((e = alloc(&s->d_dyn, sizeof(DynState)))) return fail(e);
@@ -1156,7 +1158,8 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
     {
         StageTimer t(s, 7, st);
         TMA_CUDA(launch_select(cb, p.N, p.L, s->d_best, s->d_best_sum, s->d_ninf, s->d_work, st));
-        TMA_CUDA(launch_gather_best(s->d_u[cur], s->d_best, p.N * p.S * 3, s->d_best_u, st));
+        TMA_CUDA(launch_gather_best(s->d_u[cur], s->d_best, p.N * p.S * 3, s->d_best_u, st,
+                                    s->d_flags, s->d_ninf, s->d_err));
     }
     (void)degenerate;
     return TMA_OK;
@@ -1201,6 +1204,15 @@ tma_status tma_solve_host(tma_solver *s, const tma_state *h_x0, uint32_t mpc_ste
     TMA_CUDA(cudaStreamSynchronize(st));
     if (h_best_cost) *h_best_cost = cost;
     return (flags & 1u) ? TMA_WARN_DEGENERATE : TMA_OK;
+}
+
+tma_status tma_get_particles(tma_solver *s, float *d_u_out, int64_t L, tma_stream_t stream)
+{
+    if (!s || !d_u_out || L < 0 || L > s->prob.L) return TMA_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)L * s->prob.N * s->prob.S * 3 * sizeof(float);
+    TMA_CUDA(cudaMemcpyAsync(d_u_out, s->d_u[s->cur_u], bytes, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return TMA_OK;
 }
 
 tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream)
@@ -1279,10 +1291,9 @@ tma_status tma_select(const float *d_cbar, int32_t N, int64_t L, int64_t *d_best
 
 // --------------------------------------------------------------- MPC plant
 
-tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream)
+// The plant step of Fig. 1, stream-ordered (no sync).
+static tma_status plant_async(tma_solver *s, const float *d_u, cudaStream_t st)
 {
-    if (!s || !d_u) return TMA_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
     if (!s->d_probs1) {
         cudaError_t e = alloc(&s->d_probs1, sizeof(ProblemC));
         if (!e) e = alloc(&s->d_scen1, sizeof(BatchScen));
@@ -1301,9 +1312,66 @@ tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream)
     TMA_CUDA(cudaMemcpyAsync(s->d_scen1, &sc, sizeof sc, cudaMemcpyHostToDevice, st));
     TMA_CUDA(launch_plant_step(s->d_probs1, s->d_scen1, s->d_seg_scen1, s->prob.N, 1, s->d_dyn,
                                s->d_W, d_u, s->prob.S, st));
-    TMA_CUDA(cudaStreamSynchronize(st));
     s->mpc_step += 1;
     s->wind_ready = false;
+    return TMA_OK;
+}
+
+tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream)
+{
+    if (!s || !d_u) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    tma_status r = plant_async(s, d_u, st);
+    if (r != TMA_OK) return r;
+    TMA_CUDA(cudaStreamSynchronize(st));
+    return TMA_OK;
+}
+
+tma_status tma_mpc_run(tma_solver *s, int32_t n_steps, tma_state *h_traj, double *h_costs,
+                       tma_stream_t stream)
+{
+    if (!s || n_steps < 0 || (n_steps > 0 && !h_traj) ||
+        (uint64_t)s->mpc_step + (uint64_t)n_steps > 0xFFFFu)
+        return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<DynState> states((size_t)n_steps);
+    std::vector<double> costs((size_t)n_steps);
+    unsigned int deg = 0;
+    for (int t = 0; t < n_steps; ++t) {
+        bool d = false;
+        tma_status r = solve_device(s, st, &d);
+        if (r != TMA_OK) return r;
+        TMA_CUDA(cudaMemcpyAsync(&costs[t], s->d_best_sum, 8, cudaMemcpyDeviceToHost, st));
+        unsigned int flags = 0;
+        TMA_CUDA(cudaMemcpyAsync(&flags, s->d_flags, 4, cudaMemcpyDeviceToHost, st));
+        r = plant_async(s, s->d_best_u, st);
+        if (r != TMA_OK) return r;
+        TMA_CUDA(cudaMemcpyAsync(&states[t], s->d_dyn, sizeof(DynState), cudaMemcpyDeviceToHost, st));
+        TMA_CUDA(cudaStreamSynchronize(st));
+        deg |= flags & 1u;
+    }
+    for (int t = 0; t < n_steps; ++t) {
+        for (int i = 0; i < s->prob.N; ++i) {
+            tma_state &x = h_traj[(size_t)t * s->prob.N + i];
+            x.x = states[t].x0[i][0];
+            x.y = states[t].x0[i][1];
+            x.z = states[t].x0[i][2];
+            x.v = states[t].x0[i][3];
+            x.chi = states[t].x0[i][4];
+            x.m = states[t].x0[i][5];
+        }
+        if (h_costs) h_costs[t] = costs[t];
+    }
+    return deg ? TMA_WARN_DEGENERATE : TMA_OK;
+}
+
+tma_status tma_get_error(tma_solver *s, uint32_t *h_err, tma_stream_t stream)
+{
+    if (!s || !h_err) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    TMA_CUDA(cudaMemcpyAsync(h_err, s->d_err, 4, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaMemsetAsync(s->d_err, 0, 4, st));
+    TMA_CUDA(cudaStreamSynchronize(st));
     return TMA_OK;
 }
 

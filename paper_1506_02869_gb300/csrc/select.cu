@@ -83,11 +83,16 @@ __global__ void __launch_bounds__(256) select_final(const Cand *__restrict__ par
     }
 }
 
+// Copies the chosen particle's controls; when err is given, also ORs the
+// solve's status into the sticky error word: bit 0 a weight segment was all
+// zero (flags bit 0), bit 1 the chosen particle has an infeasible aircraft.
 __global__ void gather_best_kernel(const float *__restrict__ u, const long long *__restrict__ best,
-                                   int n, float *__restrict__ out)
+                                   int n, float *__restrict__ out, const unsigned int *flags,
+                                   const int *ninf, unsigned int *err)
 {
     const long long b = *best;
     for (int j = threadIdx.x; j < n; j += blockDim.x) out[j] = u[(size_t)b * n + j];
+    if (err && threadIdx.x == 0) *err |= (*flags & 1u) | (*ninf > 0 ? 2u : 0u);
 }
 
 constexpr int kSelBlocks = 592;   // 4 x 148 resident blocks; the second pass reads 592 candidates
@@ -114,9 +119,11 @@ cudaError_t launch_select(const float *cbar, int N, int64_t L, int64_t *best, do
 }
 
 cudaError_t launch_gather_best(const float *u, const int64_t *best, int n, float *best_u,
-                               cudaStream_t st)
+                               cudaStream_t st, const unsigned int *flags, const int *ninf,
+                               unsigned int *err)
 {
-    gather_best_kernel<<<1, 256, 0, st>>>(u, reinterpret_cast<const long long *>(best), n, best_u);
+    gather_best_kernel<<<1, 256, 0, st>>>(u, reinterpret_cast<const long long *>(best), n, best_u,
+                                          flags, ninf, err);
     count_launch();
     return cudaGetLastError();
 }

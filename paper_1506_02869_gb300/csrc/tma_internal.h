@@ -126,7 +126,8 @@ cudaError_t launch_select(const float *cbar, int N, int64_t L, int64_t *best, do
                           int *ninf, void *work, cudaStream_t st);
 size_t select_workspace(int64_t L);
 cudaError_t launch_gather_best(const float *u, const int64_t *best, int nctl_per_particle,
-                               float *best_u, cudaStream_t st);
+                               float *best_u, cudaStream_t st, const unsigned int *flags = nullptr,
+                               const int *ninf = nullptr, unsigned int *err = nullptr);
 
 // gradient of the soft cost (adjoint.cu): per-sample costs cost_ms[M][N][L],
 // partial gradients gpart[nchunk][L][N][S][3] over nchunk ranges of samples
@@ -213,6 +214,7 @@ struct tma_solver {
     double *d_best_sum = nullptr;
     int32_t *d_ninf = nullptr;
     unsigned int *d_flags = nullptr;
+    unsigned int *d_err = nullptr;      // sticky error word (tma_get_error)
     unsigned long long *d_live = nullptr;
     float *d_best_u = nullptr;
     int cur_u = 0;

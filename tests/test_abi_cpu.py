@@ -163,3 +163,11 @@ def test_profile_struct_has_every_stage():
     src = open(HEADER).read()
     n = int(re.search(r"#define TMA_N_STAGES (\d+)", src).group(1))
     assert len(pkg.TmaProfile._fields_[0][1]()) == n == len(pkg.STAGES)
+
+
+def test_mpc_and_error_calls_reject_invalid_arguments(lib):
+    null = C.c_void_p()
+    assert lib.tma_mpc_run(null, 1, None, None, null) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_get_error(null, None, null) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_get_particles(null, null, 1, null) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_set_wind_stream(null, 8) == pkg.TMA_ERR_INVALID_ARG

@@ -131,3 +131,29 @@ def test_batch_rejects_mismatched_shapes(torch, pkg):
     ps[1] = ps[1].copy(M=ps[0].M + 1)
     with pytest.raises(pkg.TmaError):
         pkg.tma_batch_create(ps)
+
+
+def test_mpc_run_equals_the_solve_and_plant_loop(torch, pkg):
+    p = S.shrink(S.config1(), L=512, M=3, H=20, J_max=4)
+    sol = pkg.Solver(p)
+    traj, costs, st = pkg.tma_mpc_run(sol.h, 3, p.N)
+    assert pkg.tma_get_error(sol.h) == 0
+    sol.close()
+    sol = pkg.Solver(p)
+    for t in range(3):
+        bu, c, _ = sol.solve()
+        pkg.tma_plant_step(sol.h, bu)
+        x, mpc = pkg.tma_get_state(sol.h, p.N)
+        assert np.array_equal(x, traj[t]) and c == costs[t]
+    assert mpc == p.mpc_step + 3
+    sol.close()
+
+
+def test_error_word_reports_an_infeasible_choice(torch, pkg):
+    p = S.shrink(S.config1(), L=256, M=2, H=10, J_max=2).copy(z_min=5500.0)
+    sol = pkg.Solver(p)
+    sol.solve()
+    sol.solve()
+    assert pkg.tma_get_error(sol.h) & 2
+    assert pkg.tma_get_error(sol.h) == 0        # cleared by the read
+    sol.close()
