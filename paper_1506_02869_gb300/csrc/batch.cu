@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
             rollout_tile(Ps, dyns + s, u + sc.u_off, W + sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0, i,
                          threadIdx.x & 31, m, J, cost_ms + cbase,
                          cost_ms_soft ? cost_ms_soft + cbase : nullptr, live,
-                         spos + (size_t)t * 6 * sc.N * kPB, 1, active * 32);
+                         spos + (size_t)t * tile_smem_words(sc.N), 1, active * 32);
         }
         __syncthreads();
     }
@@ -372,7 +372,7 @@ inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) /
 
 }  // namespace
 
-size_t batch_rollout_smem() { return (size_t)6 * 32 * kPB * sizeof(float); }
+size_t batch_rollout_smem() { return (size_t)tile_smem_words(32) * sizeof(float); }
 
 cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
                                  long long n_items, const DynState *dyns, const float *u,

@@ -84,7 +84,7 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
     const long long nLb = (L + kPB - 1) / kPB;
     const unsigned grid = (unsigned)(nLb * P.M);
     const int block = P.N * kPB;
-    const size_t smem = (size_t)2 * 3 * P.N * kPB * sizeof(float);
+    const size_t smem = (size_t)tile_smem_words(P.N) * sizeof(float);
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
     switch (variant) {
     case 0: rollout_kernel<256, 4><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;

@@ -295,11 +295,21 @@ __device__ __forceinline__ float total_objective(const ProblemC &P, const Aircra
     return (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-c.sN, invH, 1.0f);
 }
 
+// Shared-memory words of one tile: positions [2][3][N][32] (double-buffered by
+// step) and separation flags [N][32].
+__host__ __device__ constexpr int tile_smem_words(int N) { return 7 * N * kTileParticles; }
+
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
 // packed wind field Wm of sample m, and writes the per-sample costs
 // cost_ms[(m N + i) L + l] (and the softplus variant when cost_ms_soft is not
-// null).  spos is the tile's [2][3][N][32] float buffer; every warp of the
+// null).  spos is the tile's tile_smem_words(N) buffer; every warp of the
 // tile must call this with the same barrier (bar_id, bar_count threads).
+//
+// Separation (Eq. (avoidance)) in hard-only mode checks every unordered pair
+// once: warp i takes the partners i+1 .. i+floor((N-1)/2) (mod N), and for even
+// N also i+N/2 when i < N/2, so every warp has the same load; a violation marks
+// both aircraft (the partner through its flag in shared memory).  With the
+// softplus penalty every warp sums its own N-1 terms.
 __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
                                              const float *__restrict__ u,
                                              const float4 *__restrict__ Wm, long long L,
@@ -325,6 +335,10 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
     unsigned int nlive = 0;
     const bool soft_on = cost_ms_soft != nullptr;
     const int plane = N * kPB;
+    int *vflag = reinterpret_cast<int *>(spos + 6 * plane);
+    vflag[i * kPB + j] = 0;       // ordered before any partner's mark by the step-0 barrier
+    const int n_half = (N - 1) >> 1;
+    const int n_pairs = n_half + (((N & 1) == 0 && i < (N >> 1)) ? 1 : 0);
 
     for (int k = 0; k < P.H; ++k) {
         if (!s.dead && !s.landed) {
@@ -340,7 +354,7 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
         buf[plane + i * kPB + j] = s.y;
         buf[2 * plane + i * kPB + j] = act ? s.z : 1e30f;
         tile_barrier(bar_id, bar_count);
-        if (act) {
+        if (act && soft_on) {
             for (int i2 = 0; i2 < N; ++i2) {
                 if (i2 == i) continue;
                 const float dx = s.x - buf[i2 * kPB + j];
@@ -348,13 +362,28 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
                 const float adz = fabsf(s.z - buf[2 * plane + i2 * kPB + j]);
                 const float dh2 = fmaf(dx, dx, dy * dy);
                 if (dh2 < P.Sh2 && adz < P.Sv) sepv = true;
-                if (soft_on) {
-                    const float g = fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f),
-                                          fmaf(-adz, P.Sv_inv, 1.0f));
-                    soft += softplus(g, P.sp_beta, P.sp_inv_beta);
+                const float g = fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f),
+                                      fmaf(-adz, P.Sv_inv, 1.0f));
+                soft += softplus(g, P.sp_beta, P.sp_inv_beta);
+            }
+        } else if (act) {
+            int i2 = i;
+            for (int t = 0; t < n_pairs; ++t) {
+                i2 = (i2 + 1 == N) ? 0 : i2 + 1;
+                const float dx = s.x - buf[i2 * kPB + j];
+                const float dy = s.y - buf[plane + i2 * kPB + j];
+                const float adz = fabsf(s.z - buf[2 * plane + i2 * kPB + j]);
+                if (fmaf(dx, dx, dy * dy) < P.Sh2 && adz < P.Sv) {
+                    sepv = true;
+                    vflag[i2 * kPB + j] = 1;
                 }
             }
         }
+    }
+    if (!soft_on) {
+        // marks made by partners that checked their pairs with this aircraft
+        tile_barrier(bar_id, bar_count);
+        sepv = sepv || vflag[i * kPB + j] != 0;
     }
 
     // the per-sample cost -ln J_T (Sec. 3.6)
