@@ -379,7 +379,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
                         // function, from one exponential of -|beta g|
                         const float bg = P.sp_beta * gmin;
                         const float e = __expf(-fabsf(bg));
-                        soft += (fmaxf(bg, 0.0f) + log1pf(e)) * P.sp_inv_beta;
+                        soft += (fmaxf(bg, 0.0f) + log1p_unit(e)) * P.sp_inv_beta;
                         const float sig = (bg >= 0.0f ? 1.0f : e) / (1.0f + e);
                         const float w = sep_c * sig;
                         if (ghh <= gvv) {

@@ -15,6 +15,8 @@
 //                     true state (the "Plant" of Fig. 1) and advances its MPC
 //                     step on the device, so that MPC steps can be replayed as
 //                     one CUDA graph.
+#include <algorithm>
+
 #include "rollout_tile.cuh"
 
 namespace tma {
@@ -372,7 +374,15 @@ inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) /
 
 }  // namespace
 
-size_t batch_rollout_smem() { return (size_t)tile_smem_words(32) * sizeof(float); }
+// A CTA of 32 warps holds floor(32 / N) tiles of N warps: the most shared
+// memory over every aircraft count.
+size_t batch_rollout_smem()
+{
+    size_t best = 0;
+    for (int n = 1; n <= kMaxN; ++n)
+        best = std::max(best, (size_t)(32 / n) * tile_smem_words(n) * sizeof(float));
+    return best;
+}
 
 cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
                                  long long n_items, const DynState *dyns, const float *u,

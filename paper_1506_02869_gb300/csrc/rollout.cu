@@ -86,13 +86,23 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
     const int block = P.N * kPB;
     const size_t smem = (size_t)tile_smem_words(P.N) * sizeof(float);
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    // above the default 48 KB of dynamic shared memory the kernel must opt in
+#define TMA_ROLLOUT(T, B)                                                                        \
+    do {                                                                                         \
+        if (smem > 48 * 1024)                                                                    \
+            cudaFuncSetAttribute(rollout_kernel<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                     \
+        rollout_kernel<T, B><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms,  \
+                                                        cost_ms_soft, live);                     \
+    } while (0)
     switch (variant) {
-    case 0: rollout_kernel<256, 4><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
-    case 1: rollout_kernel<256, 3><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
-    case 2: rollout_kernel<512, 2><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
-    case 3: rollout_kernel<512, 1><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
-    default: rollout_kernel<1024, 1><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live); break;
+    case 0: TMA_ROLLOUT(256, 4); break;
+    case 1: TMA_ROLLOUT(256, 3); break;
+    case 2: TMA_ROLLOUT(512, 2); break;
+    case 3: TMA_ROLLOUT(512, 1); break;
+    default: TMA_ROLLOUT(1024, 1); break;
     }
+#undef TMA_ROLLOUT
     count_launch();
     return cudaGetLastError();
 }

@@ -87,10 +87,19 @@ __device__ __forceinline__ float popdense_at(const ProblemC &P, float x, float y
     return fmaf(t0, b - a, a);
 }
 
+// ln(1 + e) for 0 <= e <= 1: e itself below 2^-12 (error below e^2/2 < 2^-13 e),
+// else the hardware logarithm of 1 + e (absolute error near 2^-24).
+__device__ __forceinline__ float log1p_unit(float e)
+{
+    return e < 2.44140625e-4f ? e : __logf(1.0f + e);
+}
+
+// Softplus penalty ln(1 + exp(beta g)) / beta of Eq. (avoidance) in soft form,
+// as max(beta g, 0) + ln(1 + exp(-|beta g|)).
 __device__ __forceinline__ float softplus(float g, float beta, float inv_beta)
 {
     const float bg = beta * g;
-    return bg > 0.0f ? (bg + log1pf(__expf(-bg))) * inv_beta : log1pf(__expf(bg)) * inv_beta;
+    return (fmaxf(bg, 0.0f) + log1p_unit(__expf(-fabsf(bg)))) * inv_beta;
 }
 
 constexpr int kPB = kTileParticles;
@@ -295,9 +304,14 @@ __device__ __forceinline__ float total_objective(const ProblemC &P, const Aircra
     return (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-c.sN, invH, 1.0f);
 }
 
-// Shared-memory words of one tile: positions [2][3][N][32] (double-buffered by
-// step) and separation flags [N][32].
-__host__ __device__ constexpr int tile_smem_words(int N) { return 7 * N * kTileParticles; }
+// Shared memory of one tile (32-bit words): positions float4 [2][N][32]
+// (double-buffered by step), separation flags [N][32], and the received
+// separation penalties [2][N][floor((N-1)/2) + 1][32] of the soft form.
+__host__ __device__ constexpr int tile_pair_slots(int N) { return (N - 1) / 2 + 1; }
+__host__ __device__ constexpr int tile_smem_words(int N)
+{
+    return (9 * N + 2 * N * tile_pair_slots(N)) * kTileParticles;
+}
 
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
 // packed wind field Wm of sample m, and writes the per-sample costs
@@ -305,11 +319,13 @@ __host__ __device__ constexpr int tile_smem_words(int N) { return 7 * N * kTileP
 // null).  spos is the tile's tile_smem_words(N) buffer; every warp of the
 // tile must call this with the same barrier (bar_id, bar_count threads).
 //
-// Separation (Eq. (avoidance)) in hard-only mode checks every unordered pair
-// once: warp i takes the partners i+1 .. i+floor((N-1)/2) (mod N), and for even
-// N also i+N/2 when i < N/2, so every warp has the same load; a violation marks
-// both aircraft (the partner through its flag in shared memory).  With the
-// softplus penalty every warp sums its own N-1 terms.
+// Separation (Eq. (avoidance)) checks every unordered pair once: warp i takes
+// the partners i+d, d = 1 .. floor((N-1)/2) (mod N), and for even N also
+// d = N/2 when i < N/2, so every warp has the same load.  A violation marks both
+// aircraft (the partner through its flag in shared memory).  The softplus
+// penalty of a pair enters both aircraft's costs: the owner adds it and stores
+// it in the partner's slot d-1; after the next step's barrier every aircraft
+// adds its received slots in a fixed order (deterministic sums).
 __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
                                              const float *__restrict__ u,
                                              const float4 *__restrict__ Wm, long long L,
@@ -335,10 +351,15 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
     unsigned int nlive = 0;
     const bool soft_on = cost_ms_soft != nullptr;
     const int plane = N * kPB;
-    int *vflag = reinterpret_cast<int *>(spos + 6 * plane);
+    float4 *pos = reinterpret_cast<float4 *>(spos);                 // [2][N][32]
+    int *vflag = reinterpret_cast<int *>(spos + 8 * plane);        // [N][32]
+    float *recv = spos + 9 * plane;                                 // [2][N][slots][32]
+    const int slots = tile_pair_slots(N);
     vflag[i * kPB + j] = 0;       // ordered before any partner's mark by the step-0 barrier
     const int n_half = (N - 1) >> 1;
-    const int n_pairs = n_half + (((N & 1) == 0 && i < (N >> 1)) ? 1 : 0);
+    const bool even = (N & 1) == 0;
+    const int n_pairs = n_half + ((even && i < (N >> 1)) ? 1 : 0);
+    const int n_recv = n_half + ((even && i >= (N >> 1)) ? 1 : 0);
 
     for (int k = 0; k < P.H; ++k) {
         if (!s.dead && !s.landed) {
@@ -349,41 +370,53 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
         // binary separation constraints at step k+1 among flying aircraft: every
         // thread publishes its position (a far-away altitude when not flying)
         const bool act = !s.dead && !s.landed;
-        float *buf = spos + (k & 1) * 3 * plane;
-        buf[i * kPB + j] = s.x;
-        buf[plane + i * kPB + j] = s.y;
-        buf[2 * plane + i * kPB + j] = act ? s.z : 1e30f;
+        float4 *buf = pos + (k & 1) * plane;
+        buf[i * kPB + j] = make_float4(s.x, s.y, act ? s.z : 1e30f, 0.0f);
         tile_barrier(bar_id, bar_count);
-        if (act && soft_on) {
-            for (int i2 = 0; i2 < N; ++i2) {
-                if (i2 == i) continue;
-                const float dx = s.x - buf[i2 * kPB + j];
-                const float dy = s.y - buf[plane + i2 * kPB + j];
-                const float adz = fabsf(s.z - buf[2 * plane + i2 * kPB + j]);
+        if (soft_on) {
+            // penalties the partners computed for this aircraft at the previous step
+            if (k > 0) {
+                const float *rr = recv + ((((k - 1) & 1) * N + i) * slots) * kPB + j;
+                for (int d = 0; d < n_recv; ++d) soft += rr[d * kPB];
+            }
+            float *rw = recv + ((k & 1) * N * slots) * kPB + j;
+            int i2 = i;
+            for (int d = 0; d < n_pairs; ++d) {
+                i2 = (i2 + 1 == N) ? 0 : i2 + 1;
+                const float4 q = buf[i2 * kPB + j];
+                const float dx = s.x - q.x, dy = s.y - q.y, adz = fabsf(s.z - q.z);
                 const float dh2 = fmaf(dx, dx, dy * dy);
-                if (dh2 < P.Sh2 && adz < P.Sv) sepv = true;
-                const float g = fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f),
-                                      fmaf(-adz, P.Sv_inv, 1.0f));
-                soft += softplus(g, P.sp_beta, P.sp_inv_beta);
+                float pen = 0.0f;
+                if (act) {
+                    if (dh2 < P.Sh2 && adz < P.Sv) {
+                        sepv = true;
+                        vflag[i2 * kPB + j] = 1;
+                    }
+                    pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
+                                   P.sp_beta, P.sp_inv_beta);
+                    soft += pen;
+                }
+                rw[(i2 * slots + d) * kPB] = pen;
             }
         } else if (act) {
             int i2 = i;
-            for (int t = 0; t < n_pairs; ++t) {
+            for (int d = 0; d < n_pairs; ++d) {
                 i2 = (i2 + 1 == N) ? 0 : i2 + 1;
-                const float dx = s.x - buf[i2 * kPB + j];
-                const float dy = s.y - buf[plane + i2 * kPB + j];
-                const float adz = fabsf(s.z - buf[2 * plane + i2 * kPB + j]);
-                if (fmaf(dx, dx, dy * dy) < P.Sh2 && adz < P.Sv) {
+                const float4 q = buf[i2 * kPB + j];
+                const float dx = s.x - q.x, dy = s.y - q.y;
+                if (fmaf(dx, dx, dy * dy) < P.Sh2 && fabsf(s.z - q.z) < P.Sv) {
                     sepv = true;
                     vflag[i2 * kPB + j] = 1;
                 }
             }
         }
     }
-    if (!soft_on) {
-        // marks made by partners that checked their pairs with this aircraft
-        tile_barrier(bar_id, bar_count);
-        sepv = sepv || vflag[i * kPB + j] != 0;
+    // marks and penalties the partners wrote at the last step
+    tile_barrier(bar_id, bar_count);
+    sepv = sepv || vflag[i * kPB + j] != 0;
+    if (soft_on) {
+        const float *rr = recv + ((((P.H - 1) & 1) * N + i) * slots) * kPB + j;
+        for (int d = 0; d < n_recv; ++d) soft += rr[d * kPB];
     }
 
     // the per-sample cost -ln J_T (Sec. 3.6)
