@@ -20,6 +20,14 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["wind.cu", "rollout.cu", "adjoint.cu", "mala.cu", "resample.cu", "move.cu", "select.cu",
            "batch.cu", "host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Every CUDA translation unit: single-precision square roots and divisions by
+# the hardware approximations (a few ulp), denormals flushed.  All units share
+# the flags, so that code compiled in several of them (the step function, the
+# Box-Muller transform) gives the same bits everywhere -- the batched path
+# reproduces the single-scenario one, the gradient's forward pass decides every
+# limit as the rollout does.  Double precision is not affected.
+FAST_MATH_SOURCES = {s for s in SOURCES if s.endswith(".cu")}
+FAST_MATH_FLAGS = ["-prec-sqrt=false", "-prec-div=false", "-ftz=true"]
 
 
 def nvcc_path() -> str:
@@ -39,9 +47,11 @@ def _headers():
     return hs
 
 
-def _flags(ptxas_verbose=False):
+def _flags(ptxas_verbose=False, src=""):
     f = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "-I", INCLUDE, "-I", CSRC]
+    if src in FAST_MATH_SOURCES:
+        f += FAST_MATH_FLAGS
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -63,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
 
     def compile_one(job):
         s, o = job
-        cmd = [nvcc] + _flags(ptxas_verbose) + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc] + _flags(ptxas_verbose, os.path.basename(s)) + ["-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {s}:\n{r.stdout}\n{r.stderr}")
