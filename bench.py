@@ -544,6 +544,30 @@ def run_batched(args, local):
                     "solve_latency_ms_p99": float(np.percentile(lat, 99))}
     out["live_steps_last_solve"] = pkg.tma_batch_live_steps(b)
     pkg.tma_batch_destroy(b)
+    # the plain form on the same GPU: one solver per scenario, solved one after
+    # the other (solve + plant step per MPC step)
+    sols = [pkg.Solver(p) for p in ps]
+    for sol in sols[:2]:
+        sol.solve()
+    torch.cuda.synchronize()
+    lat = []
+    ms_total = 0.0
+    for _ in range(args.mpc_steps):
+        for sol in sols:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bu, _, _ = sol.solve()
+            pkg.tma_plant_step(sol.h, bu)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ms_total += ms
+            lat.append(ms)
+    for sol in sols:
+        sol.close()
+    out["single"] = {"value": units / (ms_total * 1e-3), "ms_per_step": ms_total,
+                     "solve_latency_ms_p50": float(np.percentile(lat, 50)),
+                     "solve_latency_ms_p99": float(np.percentile(lat, 99))}
     print(json.dumps(out), flush=True)
     return 0
 

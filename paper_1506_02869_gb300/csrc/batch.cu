@@ -2,11 +2,14 @@
 // uneven aircraft counts (one SMC solve per scenario per MPC step, Sec. 2 and
 // Algorithm 1), all scenarios in single launches.
 //
-//   rollout_batched   persistent kernel: every CTA pulls work items
-//                     (scenario s, wind sample m, group of particle tiles) from
-//                     an atomic queue; a CTA of 32 warps packs floor(32 / N_s)
-//                     tiles of 32 particles, each tile N_s warps, so small and
-//                     large scenarios share the machine without a launch per
+//   rollout_batched   persistent kernel: a CTA of 32 warps holds
+//                     min(15, floor(32 / N_s)) tile slots of N_s warps; each slot
+//                     claims tiles (wind sample m, 32 particles) of the current
+//                     scenario from that scenario's atomic counter and
+//                     synchronises only its own warps (a named barrier per
+//                     slot), so a slow tile does not hold the others.  All CTAs
+//                     walk the scenarios in the same order; small and large
+//                     scenarios share the machine without a launch per
 //                     scenario.  The arithmetic is the single-scenario tile's.
 //   batch_*           the remaining stages over all scenarios at once; weight
 //                     segments are (scenario, aircraft) pairs, so LSE and
@@ -34,56 +37,53 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fm
 
 // ------------------------------------------------------------------ rollout
 
+
 __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
     const ProblemC *__restrict__ probs, const BatchScen *__restrict__ scen, int n_scen,
-    long long n_items, const DynState *__restrict__ dyns, const float *__restrict__ u,
-    const float4 *__restrict__ W, long long L, int nLb, int J, float *__restrict__ cost_ms,
-    float *__restrict__ cost_ms_soft, unsigned long long *__restrict__ live,
-    unsigned long long *__restrict__ queue)
+    const DynState *__restrict__ dyns, const float *__restrict__ u, const float4 *__restrict__ W,
+    long long L, int nLb, int J, float *__restrict__ cost_ms, float *__restrict__ cost_ms_soft,
+    unsigned long long *__restrict__ live, unsigned long long *__restrict__ claimed)
 {
     __shared__ ProblemC Ps;
-    __shared__ long long item_sh;
+    __shared__ long long slot_item[15];
+    __shared__ int skip_sh;
     extern __shared__ float spos[];
-    int cur_s = -1;
-    const int w = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = (long long)atomicAdd(queue, 1ull);
-        __syncthreads();
-        const long long item = item_sh;
-        if (item >= n_items) break;
-        // scenario of the item: the last s with item_off <= item
-        int lo = 0, hi = n_scen - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (scen[mid].item_off <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const int s = lo;
-        if (s != cur_s) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Every CTA walks the scenarios in the same order, so the CTAs of the device
+    // share one scenario (and its wind field in L2) at a time.
+    for (int s = 0; s < n_scen; ++s) {
+        if (threadIdx.x == 0)
+            skip_sh = *reinterpret_cast<volatile unsigned long long *>(claimed + s) >=
+                      (unsigned long long)scen[s].items;
+        __syncthreads();            // also: the previous scenario's slots are done with Ps
+        if (skip_sh) continue;
+        {
             const int nw = (int)(sizeof(ProblemC) / sizeof(int));
             const int *src = reinterpret_cast<const int *>(probs + s);
             int *dst = reinterpret_cast<int *>(&Ps);
             for (int t = threadIdx.x; t < nw; t += blockDim.x) dst[t] = src[t];
-            cur_s = s;
         }
         __syncthreads();
         const BatchScen sc = scen[s];
-        const long long ngroups = (nLb + sc.T - 1) / sc.T;
-        const long long r = item - sc.item_off;
-        const int m = (int)(r / ngroups);
-        const long long g = r - (long long)m * ngroups;
-        const int tiles = (int)min((long long)sc.T, (long long)nLb - g * sc.T);
-        const int active = tiles * sc.N;
-        if (w < active) {
-            const int t = w / sc.N, i = w - t * sc.N;
-            const long long l0 = (g * sc.T + t) * kPB;
+        if (w < sc.T * sc.N) {
+            // tile slot q of N warps: claims tiles (wind sample, 32 particles) of
+            // this scenario one at a time and synchronises its own warps only
+            const int q = w / sc.N, i = w - q * sc.N;
+            const int bar = 1 + q, cnt = sc.N * 32;
+            float *tsp = spos + (size_t)q * tile_smem_words(sc.N);
             const size_t cbase = (size_t)sc.seg_off * Ps.M * (size_t)L;
-            rollout_tile(Ps, dyns + s, u + sc.u_off, W + sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0, i,
-                         threadIdx.x & 31, m, J, cost_ms + cbase,
-                         cost_ms_soft ? cost_ms_soft + cbase : nullptr, live,
-                         spos + (size_t)t * tile_smem_words(sc.N), 1, active * 32);
+            for (;;) {
+                if (i == 0 && lane == 0) slot_item[q] = (long long)atomicAdd(claimed + s, 1ull);
+                tile_barrier(bar, cnt);
+                const long long it = slot_item[q];
+                if (it >= sc.items) break;
+                const int m = (int)(it / nLb);
+                const long long l0 = (it - (long long)m * nLb) * kPB;
+                rollout_tile(Ps, dyns + s, u + sc.u_off, W + sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0,
+                             i, lane, m, J, cost_ms + cbase,
+                             cost_ms_soft ? cost_ms_soft + cbase : nullptr, live, tsp, bar, cnt);
+            }
         }
-        __syncthreads();
     }
 }
 
@@ -385,17 +385,17 @@ size_t batch_rollout_smem()
 }
 
 cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
-                                 long long n_items, const DynState *dyns, const float *u,
-                                 const float *W, long long L, int J, float *cost_ms,
-                                 float *cost_ms_soft, unsigned long long *live,
-                                 unsigned long long *queue, int grid, cudaStream_t st)
+                                 const DynState *dyns, const float *u, const float *W, long long L,
+                                 int J, float *cost_ms, float *cost_ms_soft,
+                                 unsigned long long *live, unsigned long long *claimed, int grid,
+                                 cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(claimed, 0, sizeof(unsigned long long) * (size_t)n_scen, st);
     if (e != cudaSuccess) return e;
     const int nLb = (int)((L + kPB - 1) / kPB);
     rollout_batched_kernel<<<grid, 1024, batch_rollout_smem(), st>>>(
-        probs, scen, n_scen, n_items, dyns, u, reinterpret_cast<const float4 *>(W), L, nLb, J, cost_ms,
-        cost_ms_soft, live, queue);
+        probs, scen, n_scen, dyns, u, reinterpret_cast<const float4 *>(W), L, nLb, J, cost_ms,
+        cost_ms_soft, live, claimed);
     count_launch();
     return cudaGetLastError();
 }

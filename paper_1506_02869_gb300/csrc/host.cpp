@@ -1439,8 +1439,8 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
     const bool soft = b->sep_mode != 0;
     float *cb = b->sep_mode == 1 ? b->d_cbar_soft : b->d_cbar;
     for (int J = 0; J < b->J_max; ++J) {
-        TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->n_items, b->d_dyns,
-                                      b->d_u[cur], b->d_W, L, J, b->d_cost_ms,
+        TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, b->d_u[cur],
+                                      b->d_W, L, J, b->d_cost_ms,
                                       soft ? b->d_cost_ms_soft : nullptr, b->d_live, b->d_queue,
                                       b->grid, st));
         TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms, b->d_scen, b->d_seg_scen, b->nseg, L, b->M,
@@ -1528,9 +1528,8 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
             sc.seg_off = b->nseg;
             sc.w_off = (long long)s * p.M * p.H * (long long)P;
             sc.N = p.N;
-            sc.T = 32 / p.N;
-            sc.items = (long long)p.M * ((nLb + sc.T - 1) / sc.T);
-            sc.item_off = items;
+            sc.T = std::min(15, 32 / p.N);   // one named barrier (ids 1..15) per tile
+            sc.items = (long long)p.M * nLb;
             for (int c = 0; c < 3; ++c) {
                 sc.ctrl_lo[c] = (float)p.ctrl_lo[c];
                 sc.ctrl_hi[c] = (float)p.ctrl_hi[c];
@@ -1632,7 +1631,7 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
         if ((e = alloc(&b->d_t_start, 8))) return fail(e);
         if ((e = alloc(&b->d_t_end, 8 * (size_t)n_scen))) return fail(e);
         if ((e = alloc(&b->d_live, 8))) return fail(e);
-        if ((e = alloc(&b->d_queue, 8))) return fail(e);
+        if ((e = alloc(&b->d_queue, 8 * (size_t)n_scen))) return fail(e);
         if ((e = alloc(&b->d_flags, 4))) return fail(e);
         if ((e = cudaMemcpy(b->d_probs, pc.data(), sizeof(ProblemC) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
         if ((e = cudaMemcpy(b->d_scen, b->scen.data(), sizeof(BatchScen) * n_scen, cudaMemcpyHostToDevice))) return fail(e);

@@ -69,9 +69,8 @@ struct BatchScen {
     long long u_off;      // floats: controls u_s[L][N][S][3]
     long long seg_off;    // first segment (aircraft) of the scenario
     long long w_off;      // float4s: packed wind field [M][H][P]
-    long long item_off;   // first work item of the scenario in the persistent queue
-    long long items;      // its work items: M * ceil(nLb / T)
-    int N, T;             // aircraft; particle tiles per CTA
+    long long items;      // its tiles: M * ceil(L / 32) (wind sample, 32 particles)
+    int N, T;             // aircraft; tile slots per CTA
     float ctrl_lo[3], ctrl_hi[3], move_sigma[3];
     uint32_t key0, key1;
 };
@@ -155,11 +154,12 @@ cudaError_t launch_mh_adapt(double *eps, unsigned int *n_accept, unsigned int *h
 // batched MPC (batch.cu)
 size_t batch_rollout_smem();
 int batch_rollout_grid();
+// claimed: one tile counter per scenario (zeroed by the launcher)
 cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
-                                 long long n_items, const DynState *dyns, const float *u,
-                                 const float *W, long long L, int J, float *cost_ms,
-                                 float *cost_ms_soft, unsigned long long *live,
-                                 unsigned long long *queue, int grid, cudaStream_t st);
+                                 const DynState *dyns, const float *u, const float *W, long long L,
+                                 int J, float *cost_ms, float *cost_ms_soft,
+                                 unsigned long long *live, unsigned long long *claimed, int grid,
+                                 cudaStream_t st);
 cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen,
                                      const int *seg_scen, long long nseg, long long L, int M,
                                      float *cbar, cudaStream_t st);
