@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
     unsigned long long *__restrict__ live, unsigned long long *__restrict__ claimed)
 {
     __shared__ ProblemC Ps;
+    __shared__ BatchScen Sc;
     __shared__ long long slot_item[15];
     __shared__ int skip_sh;
     extern __shared__ float spos[];
@@ -62,26 +63,29 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
             const int *src = reinterpret_cast<const int *>(probs + s);
             int *dst = reinterpret_cast<int *>(&Ps);
             for (int t = threadIdx.x; t < nw; t += blockDim.x) dst[t] = src[t];
+            if (threadIdx.x == 0) Sc = scen[s];
         }
         __syncthreads();
-        const BatchScen sc = scen[s];
-        if (w < sc.T * sc.N) {
+        const int Ns = Sc.N;
+        if (w < Sc.T * Ns) {
             // tile slot q of N warps: claims tiles (wind sample, 32 particles) of
-            // this scenario one at a time and synchronises its own warps only
-            const int q = w / sc.N, i = w - q * sc.N;
-            const int bar = 1 + q, cnt = sc.N * 32;
-            float *tsp = spos + (size_t)q * tile_smem_words(sc.N);
-            const size_t cbase = (size_t)sc.seg_off * Ps.M * (size_t)L;
+            // this scenario one at a time and synchronises its own warps only;
+            // the scenario's offsets stay in shared memory (Sc), not in registers
+            const int q = w / Ns, i = w - q * Ns;
+            const int bar = 1 + q, cnt = Ns * 32;
             for (;;) {
                 if (i == 0 && lane == 0) slot_item[q] = (long long)atomicAdd(claimed + s, 1ull);
                 tile_barrier(bar, cnt);
                 const long long it = slot_item[q];
-                if (it >= sc.items) break;
+                if (it >= Sc.items) break;
                 const int m = (int)(it / nLb);
                 const long long l0 = (it - (long long)m * nLb) * kPB;
-                rollout_tile(Ps, dyns + s, u + sc.u_off, W + sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0,
-                             i, lane, m, J, cost_ms + cbase,
-                             cost_ms_soft ? cost_ms_soft + cbase : nullptr, live, tsp, bar, cnt);
+                const TileResult r = rollout_tile(
+                    Ps, dyns + s, u + Sc.u_off, W + Sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0, i, lane,
+                    m, J, cost_ms_soft != nullptr, spos + (size_t)q * tile_smem_words(Ns), bar, cnt);
+                const size_t cbase = (size_t)Sc.seg_off * Ps.M * (size_t)L;
+                store_tile(r, Ns, L, l0 + lane, i, lane, m, cost_ms + cbase,
+                           cost_ms_soft ? cost_ms_soft + cbase : nullptr, live);
             }
         }
     }

@@ -32,8 +32,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const 
     extern __shared__ float spos[];
     const int m = blockIdx.x / nLb;            // wind sample: block-uniform
     const long long l0 = (long long)(blockIdx.x - m * nLb) * kPB;
-    rollout_tile(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0, threadIdx.x >> 5, threadIdx.x & 31, m,
-                 J, cost_ms, cost_ms_soft, live, spos, 0, blockDim.x);
+    const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
+    const TileResult r = rollout_tile(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0, i, j, m, J,
+                                      cost_ms_soft != nullptr, spos, 0, blockDim.x);
+    store_tile(r, P.N, L, l0 + j, i, j, m, cost_ms, cost_ms_soft, live);
 }
 
 // Mean over wind samples: cbar[i][l] = (1/M) sum_m cost_ms[m][i][l], +inf when any

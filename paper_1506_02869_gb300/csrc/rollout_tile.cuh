@@ -314,10 +314,11 @@ __host__ __device__ constexpr int tile_smem_words(int N)
 }
 
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
-// packed wind field Wm of sample m, and writes the per-sample costs
-// cost_ms[(m N + i) L + l] (and the softplus variant when cost_ms_soft is not
-// null).  spos is the tile's tile_smem_words(N) buffer; every warp of the
-// tile must call this with the same barrier (bar_id, bar_count threads).
+// packed wind field Wm of sample m and returns its per-sample costs (the
+// softplus variant when soft_on); the caller stores them (store_tile), so
+// that no output pointer is live during the steps.  spos is the tile's
+// tile_smem_words(N) buffer; every warp of the tile must call this with the
+// same barrier (bar_id, bar_count threads).
 //
 // Separation (Eq. (avoidance)) checks every unordered pair once: warp i takes
 // the partners i+d, d = 1 .. floor((N-1)/2) (mod N), and for even N also
@@ -326,14 +327,18 @@ __host__ __device__ constexpr int tile_smem_words(int N)
 // penalty of a pair enters both aircraft's costs: the owner adds it and stores
 // it in the partner's slot d-1; after the next step's barrier every aircraft
 // adds its received slots in a fixed order (deterministic sums).
-__device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
-                                             const float *__restrict__ u,
-                                             const float4 *__restrict__ Wm, long long L,
-                                             long long l0, int i, int j, int m, int J,
-                                             float *__restrict__ cost_ms,
-                                             float *__restrict__ cost_ms_soft,
-                                             unsigned long long *__restrict__ live, float *spos,
-                                             int bar_id, int bar_count)
+struct TileResult {
+    float cost;         // -ln J_T, +inf if infeasible or separation violated (hard)
+    float cost_soft;    // with the softplus penalty, +inf if infeasible
+    unsigned int live;  // aircraft-steps simulated by this thread
+};
+
+__device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
+                                                   const float *__restrict__ u,
+                                                   const float4 *__restrict__ Wm, long long L,
+                                                   long long l0, int i, int j, int m, int J,
+                                                   bool soft_on, float *spos, int bar_id,
+                                                   int bar_count)
 {
     const int N = P.N;
     const long long l = l0 + j;
@@ -349,7 +354,6 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
     bool sepv = false;
     const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
     unsigned int nlive = 0;
-    const bool soft_on = cost_ms_soft != nullptr;
     const int plane = N * kPB;
     float4 *pos = reinterpret_cast<float4 *>(spos);                 // [2][N][32]
     int *vflag = reinterpret_cast<int *>(spos + 8 * plane);        // [N][32]
@@ -422,13 +426,27 @@ __device__ __forceinline__ void rollout_tile(const ProblemC &P, const DynState *
     // the per-sample cost -ln J_T (Sec. 3.6)
     const float JT = total_objective(P, A, cs, s.F.s, ab);
     const float c = -logf(fmaxf(JT, 1e-30f));
-    if (exists) {
+    TileResult r;
+    r.cost = (s.dead || sepv) ? __int_as_float(0x7f800000) : c;
+    r.cost_soft = s.dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
+    r.live = exists ? nlive : 0u;
+    return r;
+}
+
+// Stores one thread's tile result: cost_ms[(m N + i) L + l] (and the soft
+// variant when cost_ms_soft is not null); adds the warp's live steps.
+__device__ __forceinline__ void store_tile(const TileResult &r, int N, long long L, long long l,
+                                           int i, int j, int m, float *__restrict__ cost_ms,
+                                           float *__restrict__ cost_ms_soft,
+                                           unsigned long long *__restrict__ live)
+{
+    if (l < L) {
         const size_t o = ((size_t)m * N + i) * (size_t)L + l;
-        cost_ms[o] = (s.dead || sepv) ? __int_as_float(0x7f800000) : c;
-        if (soft_on) cost_ms_soft[o] = s.dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
+        cost_ms[o] = r.cost;
+        if (cost_ms_soft) cost_ms_soft[o] = r.cost_soft;
     }
     if (live != nullptr) {
-        const unsigned int tot = __reduce_add_sync(0xffffffffu, exists ? nlive : 0u);
+        const unsigned int tot = __reduce_add_sync(0xffffffffu, r.live);
         if (j == 0 && tot) atomicAdd(live, (unsigned long long)tot);
     }
 }
