@@ -287,6 +287,52 @@ __device__ __forceinline__ void step_adjoint(const ProblemC &P, const AircraftC 
     X = nX; Y = nY; Z = nZ; V = nV; CH = nC; FF = nF;
 }
 
+// Derivative of one pair's separation penalty (weight w = 2 mu sigma(beta g) / M)
+// with respect to this aircraft's position, from the differences own - partner.
+__device__ __forceinline__ void pair_grad(const ProblemC &P, float w, float dx, float dy, float dz,
+                                          float &sx, float &sy, float &sz)
+{
+    const float dh = sqrtf(fmaf(dx, dx, dy * dy));
+    const float ghh = fmaf(-dh, P.Sh_inv, 1.0f);
+    const float gvv = fmaf(-fabsf(dz), P.Sv_inv, 1.0f);
+    if (ghh <= gvv) {
+        if (dh > 0.0f) {
+            const float eh = w * P.Sh_inv / dh;
+            sx = fmaf(-eh, dx, sx);
+            sy = fmaf(-eh, dy, sy);
+        }
+    } else {
+        sz = fmaf(-w * P.Sv_inv, sgnf(dz), sz);
+    }
+}
+
+// The penalty of a pair and the logistic weight of its derivative, from one
+// exponential of -|beta g| (0, 0 when either aircraft is not flying: its
+// published altitude is far away).
+__device__ __forceinline__ float2 pair_penalty(const ProblemC &P, float dx, float dy, float dz)
+{
+    const float dh = sqrtf(fmaf(dx, dx, dy * dy));
+    const float gmin = fminf(fmaf(-dh, P.Sh_inv, 1.0f), fmaf(-fabsf(dz), P.Sv_inv, 1.0f));
+    const float bg = P.sp_beta * gmin;
+    const float e = __expf(-fabsf(bg));
+    return make_float2((fmaxf(bg, 0.0f) + log1p_unit(e)) * P.sp_inv_beta,
+                       (bg >= 0.0f ? 1.0f : e) / (1.0f + e));
+}
+
+// Pairs are computed once (as in the rollout) when the received slots fit in
+// shared memory; above this aircraft count every aircraft computes its N-1.
+constexpr int kGradPairOnceMaxN = 16;
+
+// Positions are triple-buffered by step: a receiver reads its partners'
+// positions of step k-1 at step k, after the step-k barrier; a partner can
+// overwrite that buffer only at step k+2, after the step-(k+1) barrier, which
+// the receiver reaches after its read.
+__host__ __device__ constexpr int grad_smem_words(int N)
+{
+    return 12 * N * kTileParticles +                                              // positions
+           (N <= kGradPairOnceMaxN ? 4 * N * tile_pair_slots(N) * kTileParticles : 0);  // slots
+}
+
 template <int kMaxThreads, int kMinBlocks>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
 rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const float *__restrict__ u,
@@ -308,6 +354,16 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
     if (exists)
         for (int n = 0; n < nS3; ++n) gout[n] = 0.0f;
     const int plane = N * kPB;
+    // shared memory: positions float4 [3][N][32], then (pair-once) the received
+    // (penalty, logistic weight) float2 [2][N][slots][32]
+    float4 *pos = reinterpret_cast<float4 *>(spos);
+    float2 *slots = reinterpret_cast<float2 *>(spos + 12 * plane);
+    const bool pair_once = N <= kGradPairOnceMaxN;
+    const int n_slots = tile_pair_slots(N);
+    const int n_half = (N - 1) >> 1;
+    const bool even_n = (N & 1) == 0;
+    const int n_pairs = n_half + ((even_n && i < (N >> 1)) ? 1 : 0);
+    const int n_recv = n_half + ((even_n && i >= (N >> 1)) ? 1 : 0);
     const float invM = 1.0f / (float)P.M;
     const float sep_c = 2.0f * P.mu_sep * invM;        // each pair enters two aircraft's costs
     const int mb = chunk * m_per_block, me = min(P.M, mb + m_per_block);
@@ -360,40 +416,73 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
                     upd |= 1u << t;
                 const bool act = !r.dead && !r.landed;
                 float sx = tg.sx, sy = tg.sy, sz = tg.sz, sv = tg.sv, sc = tg.sc;
-                float *buf = spos + (k & 1) * 3 * plane;
-                buf[i * kPB + j] = r.x;
-                buf[plane + i * kPB + j] = r.y;
-                buf[2 * plane + i * kPB + j] = act ? r.z : 1e30f;
+                float4 *buf = pos + (k % 3) * plane;
+                buf[i * kPB + j] = make_float4(r.x, r.y, act ? r.z : 1e30f, 0.0f);
                 tile_barrier(0, blockDim.x);
-                if (act) {
+                if (pair_once) {
+                    // pairs the partners computed for this aircraft at the previous
+                    // step: penalty, and the derivative from both positions of then
+                    if (k > k0) {
+                        const float2 *rr = slots + ((((k - 1) & 1) * N + i) * n_slots) * kPB + j;
+                        const float4 *pb = pos + ((k - 1) % 3) * plane;
+                        float px = 0.f, py = 0.f, pz = 0.f;
+                        int o = i;
+                        for (int d = 0; d < n_recv; ++d) {
+                            o = (o == 0) ? N - 1 : o - 1;
+                            const float2 ps = rr[d * kPB];
+                            soft += ps.x;
+                            if (ps.y != 0.0f) {
+                                const float4 q = pb[o * kPB + j];
+                                pair_grad(P, sep_c * ps.y, hx[t] - q.x, hy[t] - q.y, hz[t] - q.z,
+                                          px, py, pz);
+                            }
+                        }
+                        rx[t - 1] += px; ry[t - 1] += py; rz[t - 1] += pz;
+                    }
+                    float2 *rw = slots + ((k & 1) * N * n_slots) * kPB + j;
+                    int i2 = i;
+                    for (int d = 0; d < n_pairs; ++d) {
+                        i2 = (i2 + 1 == N) ? 0 : i2 + 1;
+                        float2 ps = make_float2(0.0f, 0.0f);
+                        if (act) {
+                            const float4 q = buf[i2 * kPB + j];
+                            const float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
+                            ps = pair_penalty(P, dx, dy, dz);
+                            soft += ps.x;
+                            if (ps.y != 0.0f) pair_grad(P, sep_c * ps.y, dx, dy, dz, sx, sy, sz);
+                        }
+                        rw[(i2 * n_slots + d) * kPB] = ps;
+                    }
+                } else if (act) {
                     for (int i2 = 0; i2 < N; ++i2) {
                         if (i2 == i) continue;
-                        const float dx = r.x - buf[i2 * kPB + j];
-                        const float dy = r.y - buf[plane + i2 * kPB + j];
-                        const float dz = r.z - buf[2 * plane + i2 * kPB + j];
-                        const float dh = sqrtf(fmaf(dx, dx, dy * dy));
-                        const float ghh = fmaf(-dh, P.Sh_inv, 1.0f);
-                        const float gvv = fmaf(-fabsf(dz), P.Sv_inv, 1.0f);
-                        const float gmin = fminf(ghh, gvv);
-                        // softplus (the penalty) and its derivative, the logistic
-                        // function, from one exponential of -|beta g|
-                        const float bg = P.sp_beta * gmin;
-                        const float e = __expf(-fabsf(bg));
-                        soft += (fmaxf(bg, 0.0f) + log1p_unit(e)) * P.sp_inv_beta;
-                        const float sig = (bg >= 0.0f ? 1.0f : e) / (1.0f + e);
-                        const float w = sep_c * sig;
-                        if (ghh <= gvv) {
-                            if (dh > 0.0f) {
-                                const float eh = w * P.Sh_inv / dh;
-                                sx = fmaf(-eh, dx, sx);
-                                sy = fmaf(-eh, dy, sy);
-                            }
-                        } else {
-                            sz = fmaf(-w * P.Sv_inv, sgnf(dz), sz);
-                        }
+                        const float4 q = buf[i2 * kPB + j];
+                        const float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
+                        const float2 ps = pair_penalty(P, dx, dy, dz);
+                        soft += ps.x;
+                        if (ps.y != 0.0f) pair_grad(P, sep_c * ps.y, dx, dy, dz, sx, sy, sz);
                     }
                 }
                 rx[t] = sx; ry[t] = sy; rz[t] = sz; rv[t] = sv; rc[t] = sc;
+            }
+            if (pair_once) {
+                // pairs of the interval's last step, received after one more barrier
+                tile_barrier(0, blockDim.x);
+                const int k = k1 - 1, t = k - k0;
+                const float2 *rr = slots + (((k & 1) * N + i) * n_slots) * kPB + j;
+                const float4 *pb = pos + (k % 3) * plane;
+                float px = 0.f, py = 0.f, pz = 0.f;
+                int o = i;
+                for (int d = 0; d < n_recv; ++d) {
+                    o = (o == 0) ? N - 1 : o - 1;
+                    const float2 ps = rr[d * kPB];
+                    soft += ps.x;
+                    if (ps.y != 0.0f) {
+                        const float4 q = pb[o * kPB + j];
+                        pair_grad(P, sep_c * ps.y, r.x - q.x, r.y - q.y, r.z - q.z, px, py, pz);
+                    }
+                }
+                rx[t] += px; ry[t] += py; rz[t] += pz;
             }
             // reverse sweep of the interval
             for (int k = k1 - 1; k >= k0; --k) {
@@ -512,8 +601,14 @@ cudaError_t rollout_grad_occupancy(int N, int variant, int *blocks_per_sm)
 {
     const int block = N * kPB;
     const size_t smem = (size_t)2 * 3 * N * kPB * sizeof(float);
-#define TMA_OCC(T, B) \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rollout_grad_kernel<T, B>, block, smem)
+#define TMA_OCC(T, B)                                                                            \
+    do {                                                                                         \
+        if (smem > 48 * 1024)                                                                    \
+            cudaFuncSetAttribute(rollout_grad_kernel<T, B>,                                      \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rollout_grad_kernel<T, B>, \
+                                                             block, smem);                       \
+    } while (0)
     TMA_GRAD_VARIANT_SWITCH(valid_variant(N, variant), TMA_OCC)
 #undef TMA_OCC
     return cudaSuccess;
@@ -530,11 +625,16 @@ cudaError_t launch_rollout_grad(const ProblemC &P, const DynState *dyn, const fl
     nchunk = (P.M + m_per_block - 1) / m_per_block;
     const unsigned grid = (unsigned)(nLb * nchunk);
     const int block = P.N * kPB;
-    const size_t smem = (size_t)2 * 3 * P.N * kPB * sizeof(float);
+    const size_t smem = (size_t)grad_smem_words(P.N) * sizeof(float);
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
 #define TMA_LAUNCH(T, B)                                                                   \
-    rollout_grad_kernel<T, B><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, m_per_block, \
-                                                         J, cost_ms, gpart)
+    do {                                                                                   \
+        if (smem > 48 * 1024)                                                              \
+            cudaFuncSetAttribute(rollout_grad_kernel<T, B>,                                \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        rollout_grad_kernel<T, B><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb,   \
+                                                             m_per_block, J, cost_ms, gpart); \
+    } while (0)
     TMA_GRAD_VARIANT_SWITCH(valid_variant(P.N, variant), TMA_LAUNCH)
 #undef TMA_LAUNCH
     count_launch();
