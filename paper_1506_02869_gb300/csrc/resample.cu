@@ -32,12 +32,24 @@ constexpr int kThreads = 256;
 constexpr int kPer = 8;
 constexpr int kChunk = kThreads * kPer;  // 2048
 
+// padded shared-memory index of chunk element j (one extra word per 16)
+__device__ __forceinline__ int spad(int j) { return j + (j >> 4); }
+
+// q = floor(w 2^40) for w in (0, 1); w >= 1 (and +inf) counts as 2^40; NaN,
+// zero, subnormals and negative values as 0.  Scaling by a power of two is
+// exact, so the floor is read from the IEEE bits with integer instructions
+// only: w = m 2^(e - 1075) with the 53-bit significand m and the exponent field
+// e, hence w 2^40 = m 2^(e - 1035) and floor = m >> (1035 - e).
 __device__ __forceinline__ unsigned long long qfix(double w)
 {
-    // q = floor(w 2^40) for w in (0, 1); >= 1 counts as 1; NaN and <= 0 as 0
-    if (w >= 1.0) return 1ull << 40;
-    if (w > 0.0) return (unsigned long long)(w * 1099511627776.0);
-    return 0ull;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(w);
+    const unsigned long long frac = u & ((1ull << 52) - 1);
+    const int e = (int)((u >> 52) & 0x7ff);
+    if (u >> 63) return 0ull;                                 // negative
+    if (e >= 1023) return (e == 0x7ff && frac) ? 0ull : 1ull << 40;   // NaN, or w >= 1
+    const int shift = 1035 - e;
+    if (e == 0 || shift >= 64) return 0ull;                   // zero, subnormal, below 2^-40
+    return (frac | (1ull << 52)) >> shift;
 }
 
 // Block-wide reduction; `identity` pads the lanes beyond the number of warps.
@@ -155,10 +167,20 @@ __global__ void __launch_bounds__(kThreads) res_chunk_sum(const double *__restri
     const double *row = wtilde + (size_t)s * L;
     const long long base = (long long)c * kChunk;
     unsigned long long acc = 0;
+    if (base + kChunk <= L && (((size_t)s * L + base) & 1) == 0) {
+        // full chunk, 16-byte aligned: two values per load
+        const double2 *row2 = reinterpret_cast<const double2 *>(row + base);
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const long long idx = base + threadIdx.x + j * kThreads;
-        if (idx < L) acc += qfix(__ldg(row + idx));
+        for (int j = 0; j < kPer / 2; ++j) {
+            const double2 v = __ldg(row2 + threadIdx.x + j * kThreads);
+            acc += qfix(v.x) + qfix(v.y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long idx = base + threadIdx.x + j * kThreads;
+            if (idx < L) acc += qfix(__ldg(row + idx));
+        }
     }
     acc = block_reduce(acc, AddU64(), sh, 0ull);
     if (threadIdx.x == 0) cq[(size_t)s * nchunk + c] = acc;
@@ -189,7 +211,9 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
                                                        const SegKey *__restrict__ seg_keys,
                                                        const DynState *__restrict__ dyns)
 {
-    __shared__ unsigned long long Ssm[kChunk];
+    // S_j * D of the chunk (128-bit, hi and lo words), padded; the chunk's last S_j
+    __shared__ unsigned long long SDh[kChunk + kChunk / 16], SDl[kChunk + kChunk / 16];
+    __shared__ unsigned long long s_last;
     __shared__ unsigned long long wtot[kThreads / 32];
     __shared__ unsigned long long sh[32];
     __shared__ long long range[2];
@@ -215,17 +239,31 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         return;
     }
 
-    // inclusive prefix of q over the chunk: load, per-thread serial scan of kPer
-    // consecutive values, warp scan of thread totals, block scan of warp totals
+    // inclusive prefix of q over the chunk: every thread loads its kPer
+    // consecutive values (16-byte loads where aligned), scans them in registers;
+    // warp scan of the thread totals, block scan of the warp totals.  The chunk's
+    // prefix goes to shared memory padded by one word per 16 (no bank conflicts)
+    // for the searches.
     const double *row = wtilde + (size_t)s * L;
-    for (int j = threadIdx.x; j < kChunk; j += kThreads)
-        Ssm[j] = j < len ? qfix(__ldg(row + base + j)) : 0ull;
-    __syncthreads();
+    const int j0 = threadIdx.x * kPer;
+    unsigned long long qv[kPer];
+    if (len == kChunk && (((size_t)s * L + base) & 1) == 0) {
+        const double2 *p2 = reinterpret_cast<const double2 *>(row + base + j0);
+#pragma unroll
+        for (int j = 0; j < kPer / 2; ++j) {
+            const double2 v = __ldg(p2 + j);
+            qv[2 * j] = qfix(v.x);
+            qv[2 * j + 1] = qfix(v.y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) qv[j] = j0 + j < len ? qfix(__ldg(row + base + j0 + j)) : 0ull;
+    }
     unsigned long long run = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
-        run += Ssm[threadIdx.x * kPer + j];
-        Ssm[threadIdx.x * kPer + j] = run;
+        run += qv[j];
+        qv[j] = run;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long incl = run;
@@ -239,8 +277,16 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
     unsigned long long woff = 0;
     for (int w = 0; w < wid; ++w) woff += wtot[w];
     const unsigned long long add = before + woff + (incl - run);
+    // the searches compare thresholds against S_j * D: form the products once
+    const unsigned long long D = (unsigned long long)L << 32;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) Ssm[threadIdx.x * kPer + j] += add;
+    for (int j = 0; j < kPer; ++j) {
+        const unsigned long long S = qv[j] + add;
+        const U128 p = mul64x64(S, D);
+        SDh[spad(j0 + j)] = p.hi;
+        SDl[spad(j0 + j)] = p.lo;
+        if (j0 + j == len - 1) s_last = S;
+    }
     __syncthreads();
 
     uint32_t r;
@@ -252,9 +298,8 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
         r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
     }
-    const unsigned long long D = (unsigned long long)L << 32;
     if (threadIdx.x == 0) range[0] = count_below(before, total, D, r, L);
-    if (threadIdx.x == 32) range[1] = count_below(Ssm[len - 1], total, D, r, L);
+    if (threadIdx.x == 32) range[1] = count_below(s_last, total, D, r, L);
     __syncthreads();
     const long long lo = range[0], hi = range[1];
     for (long long l = lo + threadIdx.x; l < hi; l += kThreads) {
@@ -262,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         int jlo = 0, jhi = len - 1;  // smallest j with S_j * D > target
         while (jlo < jhi) {
             const int mid = (jlo + jhi) >> 1;
-            if (lt128(target, mul64x64(Ssm[mid], D))) jhi = mid;
+            if (lt128(target, U128{SDh[spad(mid)], SDl[spad(mid)]})) jhi = mid;
             else jlo = mid + 1;
         }
         a[l] = (int32_t)(base + jlo);
