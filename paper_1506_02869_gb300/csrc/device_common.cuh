@@ -50,10 +50,12 @@ __device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb)
 
 // The same transform with the hardware approximations of log, sin and cos
 // (absolute errors near 2^-21 on these argument ranges); the angle is taken in
-// [-pi, pi) so that no range reduction is needed.
+// [-pi, pi) so that no range reduction is needed.  Near u = 1 the approximate
+// logarithm can come out just above 0; the radius argument is clamped at 0 so
+// that it never yields NaN.
 __device__ __forceinline__ float2 box_muller_fast(uint32_t xa, uint32_t xb)
 {
-    const float r = sqrtf(-2.0f * __logf(uniform23(xa)));
+    const float r = sqrtf(fmaxf(-2.0f * __logf(uniform23(xa)), 0.0f));
     float s, c;
     __sincosf(fmaf(6.28318530717958647692f, uniform23(xb), -3.14159265358979323846f), &s, &c);
     return make_float2(-r * c, -r * s);
