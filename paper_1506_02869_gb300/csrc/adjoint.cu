@@ -82,14 +82,15 @@ __device__ __forceinline__ void wind_grad(const ProblemC &P, const float4 *__res
 {
     const WindFetch f = wind_fetch(P, Wk, x, y, z);
     float2 c00, c01, c10, c11, e00, e01, e10, e11;
-    c00.x = fmaf(f.tz, f.a00.z - f.a00.x, f.a00.x); c00.y = fmaf(f.tz, f.a00.w - f.a00.y, f.a00.y);
-    c01.x = fmaf(f.tz, f.a01.z - f.a01.x, f.a01.x); c01.y = fmaf(f.tz, f.a01.w - f.a01.y, f.a01.y);
-    c10.x = fmaf(f.tz, f.a10.z - f.a10.x, f.a10.x); c10.y = fmaf(f.tz, f.a10.w - f.a10.y, f.a10.y);
-    c11.x = fmaf(f.tz, f.a11.z - f.a11.x, f.a11.x); c11.y = fmaf(f.tz, f.a11.w - f.a11.y, f.a11.y);
-    e00 = make_float2(f.a00.z - f.a00.x, f.a00.w - f.a00.y);
-    e01 = make_float2(f.a01.z - f.a01.x, f.a01.w - f.a01.y);
-    e10 = make_float2(f.a10.z - f.a10.x, f.a10.w - f.a10.y);
-    e11 = make_float2(f.a11.z - f.a11.x, f.a11.w - f.a11.y);
+    // records hold (value, difference to the node one level up)
+    c00.x = fmaf(f.tz, f.a00.z, f.a00.x); c00.y = fmaf(f.tz, f.a00.w, f.a00.y);
+    c01.x = fmaf(f.tz, f.a01.z, f.a01.x); c01.y = fmaf(f.tz, f.a01.w, f.a01.y);
+    c10.x = fmaf(f.tz, f.a10.z, f.a10.x); c10.y = fmaf(f.tz, f.a10.w, f.a10.y);
+    c11.x = fmaf(f.tz, f.a11.z, f.a11.x); c11.y = fmaf(f.tz, f.a11.w, f.a11.y);
+    e00 = make_float2(f.a00.z, f.a00.w);
+    e01 = make_float2(f.a01.z, f.a01.w);
+    e10 = make_float2(f.a10.z, f.a10.w);
+    e11 = make_float2(f.a11.z, f.a11.w);
     float2 c0, c1, e0, e1;
     c0.x = fmaf(f.ty, c01.x - c00.x, c00.x); c0.y = fmaf(f.ty, c01.y - c00.y, c00.y);
     c1.x = fmaf(f.ty, c11.x - c10.x, c10.x); c1.y = fmaf(f.ty, c11.y - c10.y, c10.y);

@@ -21,8 +21,8 @@ constexpr float kPi = 3.14159265358979323846f;
 
 // Trilinear interpolation of one wind field (Sec. 3.9.1) at a position clamped
 // into the grid box: wind_fetch locates the cell and loads its four packed
-// columns (float4 per node: own (x, y) value and the value one level up),
-// wind_interp combines them.
+// columns (float4 per node: own (x, y) value and the difference to the node one
+// level up), wind_interp combines them.
 struct WindFetch {
     float4 a00, a01, a10, a11;
     float tx, ty, tz;
@@ -59,15 +59,48 @@ __device__ __forceinline__ WindFetch wind_fetch(const ProblemC &P, const float4 
 __device__ __forceinline__ float2 wind_interp(const WindFetch &f)
 {
     float2 c00, c01, c10, c11, c0, c1, r;
-    c00.x = fmaf(f.tz, f.a00.z - f.a00.x, f.a00.x); c00.y = fmaf(f.tz, f.a00.w - f.a00.y, f.a00.y);
-    c01.x = fmaf(f.tz, f.a01.z - f.a01.x, f.a01.x); c01.y = fmaf(f.tz, f.a01.w - f.a01.y, f.a01.y);
-    c10.x = fmaf(f.tz, f.a10.z - f.a10.x, f.a10.x); c10.y = fmaf(f.tz, f.a10.w - f.a10.y, f.a10.y);
-    c11.x = fmaf(f.tz, f.a11.z - f.a11.x, f.a11.x); c11.y = fmaf(f.tz, f.a11.w - f.a11.y, f.a11.y);
+    c00.x = fmaf(f.tz, f.a00.z, f.a00.x); c00.y = fmaf(f.tz, f.a00.w, f.a00.y);
+    c01.x = fmaf(f.tz, f.a01.z, f.a01.x); c01.y = fmaf(f.tz, f.a01.w, f.a01.y);
+    c10.x = fmaf(f.tz, f.a10.z, f.a10.x); c10.y = fmaf(f.tz, f.a10.w, f.a10.y);
+    c11.x = fmaf(f.tz, f.a11.z, f.a11.x); c11.y = fmaf(f.tz, f.a11.w, f.a11.y);
     c0.x = fmaf(f.ty, c01.x - c00.x, c00.x); c0.y = fmaf(f.ty, c01.y - c00.y, c00.y);
     c1.x = fmaf(f.ty, c11.x - c10.x, c10.x); c1.y = fmaf(f.ty, c11.y - c10.y, c10.y);
     r.x = fmaf(f.tx, c1.x - c0.x, c0.x);
     r.y = fmaf(f.tx, c1.y - c0.y, c0.y);
     return r;
+}
+
+// Angle of (x, y) in (-pi, pi], as atan2: t = min/max of |x|, |y| in [0, 1],
+// atan(t) = t P(t^2) with the degree-8 polynomial of a weighted least-squares
+// fit on Chebyshev nodes (fit_atan.py beside this file; 1e-7 rad in FP32),
+// then the octant.  (0, 0) gives 0.
+__device__ __forceinline__ float atan2_poly(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float s = t * t;
+    float p = 2.932487579e-03f;
+    p = fmaf(p, s, -1.641217540e-02f);
+    p = fmaf(p, s, 4.327672817e-02f);
+    p = fmaf(p, s, -7.556783848e-02f);
+    p = fmaf(p, s, 1.066743802e-01f);
+    p = fmaf(p, s, -1.421109512e-01f);
+    p = fmaf(p, s, 1.999369316e-01f);
+    p = fmaf(p, s, -3.333313793e-01f);
+    p = fmaf(p, s, 9.999999938e-01f);
+    float a = t * p;
+    if (ay > ax) a = 1.57079632679489662f - a;
+    if (x < 0.0f) a = 3.14159265358979324f - a;
+    return copysignf(a, y);
+}
+
+// 2^x by the hardware approximation (relative error near 2^-22).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Population density of Sec. 7.1: bilinear between grid nodes, 0 outside.
@@ -202,7 +235,7 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
     const float tp = __fdividef(s.uw * s.v, kG0 * cg);
     ok = ok && (fabsf(tp) < P.tpmax);
     const float secphi = sqrtf(fmaf(tp, tp, 1.0f));
-    const float rho = 1.225f * exp2f(4.2559f * __log2f(fmaxf(fmaf(-2.2558e-5f, s.z, 1.0f), 1e-30f)));
+    const float rho = 1.225f * ex2_approx(4.2559f * __log2f(fmaxf(fmaf(-2.2558e-5f, s.z, 1.0f), 1e-30f)));
     const float qS = A.halfS * rho * s.v * s.v;
     const float CL = __fdividef(mass * kG0 * cg * secphi, qS);
     const float D = qS * fmaf(A.CD2, CL * CL, A.CD0);
@@ -245,14 +278,14 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
           mass1 >= A.m_empty)) {
         s.dead = true;
     } else {
-        s.th = atan2f(s.y, s.x);
+        s.th = atan2_poly(s.y, s.x);
         if (A.type == 0) {
             // arrival: flow-field arc, glide angle and landing sector
             const float r = sqrtf(fmaf(s.x, s.x, s.y * s.y));
             const float ath = fabsf(s.th);
             const float ratio = ath < 1e-3f ? fmaf(s.th * s.th, 1.0f / 6.0f, 1.0f)
                                             : __fdividef(ath, fmaxf(__sinf(ath), 0.25f * ath));
-            s.beta = atan2f(s.z, r * ratio);
+            s.beta = atan2_poly(s.z, r * ratio);
             const float hdg = angdist(s.chi - kPi);
             if (r <= P.P_runway && s.beta <= P.P_beta && s.x > 0.0f && ath <= P.P_chi &&
                 hdg <= P.P_chi && s.v <= P.P_vs) {

@@ -8,8 +8,10 @@
 // Btmp[q][((m H + k) nz + iz) 2 + c] for horizontal node q.
 // Kernel 2 applies the horizontal factor as one lower-triangular matrix
 // product over q (an FP32 register-tiled GEMM) and scatters into the
-// rollout's packed layout: float4 per node (its own value and the value one
-// level up), so that trilinear interpolation needs four aligned 16-byte loads.
+// rollout's packed layout: float4 per node; kernel 3 turns the upper half of
+// every record into the difference to the node one level up, so that the
+// trilinear interpolation needs four aligned 16-byte loads and no subtraction
+// in the vertical direction.
 #include "device_common.cuh"
 #include "tma_internal.h"
 
@@ -135,6 +137,17 @@ __global__ void __launch_bounds__(256) wind_gemm_kernel(const WindC w, const flo
     }
 }
 
+// rec = (W_x, W_y, W_x one level up, W_y one level up) -> (W_x, W_y, dW_x, dW_y)
+__global__ void __launch_bounds__(256) wind_diff_kernel(float4 *__restrict__ W, long long n)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float4 r = W[t];
+    r.z -= r.x;
+    r.w -= r.y;
+    W[t] = r;
+}
+
 }  // namespace
 
 cudaError_t launch_wind_normals_ar(const WindC &w, const DynState *dyn, float *Btmp,
@@ -152,6 +165,11 @@ cudaError_t launch_wind_gemm(const WindC &w, const float *Lxy, int lda, const fl
 {
     dim3 grid(w.ldb / 128, (w.nxy + 127) / 128);
     wind_gemm_kernel<<<grid, 256, 0, st>>>(w, Lxy, lda, Btmp, W);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)(w.ncol / (2 * w.nz)) * w.nxy * w.nz;   // records
+    wind_diff_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<float4 *>(W), n);
     count_launch();
     return cudaGetLastError();
 }
