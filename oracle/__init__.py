@@ -61,6 +61,7 @@ class OrcProblem(C.Structure):
         ("popdense", C.POINTER(C.c_double)),
         ("P_runway", C.c_double), ("P_beta", C.c_double), ("P_chi", C.c_double),
         ("P_vs", C.c_double), ("beta_f", C.c_double), ("wind_stream", C.c_uint32),
+        ("wind_mode", C.c_int), ("wind_chol", C.POINTER(C.c_double)),
     ]
 
 
@@ -97,6 +98,8 @@ def lib():
                                            P(d)]
             _lib.orc_mh_accept.restype = None
             _lib.orc_plant_step.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), P(d), P(d)]
+            _lib.orc_particle_wind.argtypes = [P(OrcProblem), i64, i32, P(d)]
+            _lib.orc_particle_wind.restype = None
             _lib.orc_kappa.argtypes = [i32]
             _lib.orc_kappa.restype = i32
             _lib.orc_lse.argtypes = [P(d), i32, i32, d, P(d), P(d), P(d)]
@@ -132,6 +135,13 @@ class _Marshalled:
             setattr(s, n, float(getattr(p, n)))
         s.sep_mode = p.sep_mode
         s.wind_stream = int(getattr(p, "wind_stream", 3))
+        s.wind_mode = int(getattr(p, "wind_mode", 0))
+        if s.wind_mode == 1:
+            # Qhat: lower Cholesky factor of R_hat on the 2x2x2 corner grid (a library step)
+            if tuple(p.grid) != (2, 2, 2):
+                raise ValueError("wind mode 1 uses the 2x2x2 grid of the box corners")
+            self.chol = np.ascontiguousarray(np.linalg.cholesky(wind_covariance(p)), np.float64)
+            s.wind_chol = _ptr(self.chol, C.c_double)
         s.ctrl_lo[:], s.ctrl_hi[:], s.move_sigma[:] = p.ctrl_lo, p.ctrl_hi, p.move_sigma
         s.alpha_dep[:], s.alpha_arr[:] = p.alpha_dep, p.alpha_arr
         if p.popdense is not None:
@@ -220,6 +230,14 @@ def wind_covariance(p):
 def wind_ar_coefficient(p):
     """a = exp(-dt / G_t), with G_t = 1/lam_t (reading R11)."""
     return math.exp(-p.dt * p.lam_t)
+
+
+def particle_wind(p, l, m):
+    """Mode-1 wind of particle l, sample m: [H][8][2] on the box corners (reading R18)."""
+    out = np.empty((p.H, 8, 2), np.float64)
+    mm = _Marshalled(p)
+    lib().orc_particle_wind(mm.ps, int(l), int(m), _ptr(out, C.c_double))
+    return out
 
 
 def wind_normals(p, m0=0, mc=None):

@@ -152,6 +152,38 @@ void orc_wind_normals(const orc_problem *P, int m0, int mc, double *out)
     }
 }
 
+/* Mode 1 (reading R18): a wind field per (particle, sample) on the 2x2x2 grid of
+ * the box corners, as the paper draws it inside its GPU kernel (Sec. 6).  The
+ * recursion W(0) = Qhat v(0), W(k+1) = a W(k) + Q v(k+1), Q = sqrt(1 - a^2) Qhat,
+ * is written W(k) = Qhat B(k) with B(0) = v(0), B(k) = a B(k-1) + sqrt(1-a^2) v(k).
+ * The normals come from random stream 9: counter (c0 = l, c1 = 4 m + r, q = k) for
+ * r = 0..3; draw r gives node 2r (words 0, 1: v_X, v_Y) and node 2r+1 (words 2, 3). */
+void orc_particle_wind(const orc_problem *P, int64_t l, int m, double *out)
+{
+    const double a = exp(-P->dt * P->lam_t), b = sqrt(1.0 - a * a);
+    double B[8][2];
+    for (int k = 0; k < P->H; k++) {
+        for (int r = 0; r < 4; r++) {
+            uint32_t w[4];
+            orc_draw(P, (uint32_t)l, (uint32_t)(4 * m + r), (uint32_t)k, 9u, 0u, w);
+            double v[4];
+            orc_box_muller(w[0], w[1], &v[0], &v[1]);
+            orc_box_muller(w[2], w[3], &v[2], &v[3]);
+            for (int h = 0; h < 2; h++)
+                for (int c = 0; c < 2; c++) {
+                    const int n = 2 * r + h;
+                    B[n][c] = k == 0 ? v[2 * h + c] : a * B[n][c] + b * v[2 * h + c];
+                }
+        }
+        for (int n = 0; n < 8; n++)
+            for (int c = 0; c < 2; c++) {
+                double s = 0.0;
+                for (int j = 0; j <= n; j++) s += P->wind_chol[n * 8 + j] * B[j][c];
+                out[((int64_t)k * 8 + n) * 2 + c] = s;
+            }
+    }
+}
+
 /* trilinear interpolation of one wind field W_k[p][2] */
 static void trilinear(const orc_problem *P, const double *Wk, double x, double y, double z,
                       double *wx, double *wy)
@@ -274,6 +306,12 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
     const double sgmax = sin(P->gamma_max), tpmax = tan(P->phi_max);
     const double Sh2 = P->sep_h * P->sep_h, Sv = P->sep_v;
     int64_t nlive = 0;
+    double *own = NULL;
+    if (P->wind_mode == 1) {      /* this particle's own field for this sample */
+        own = (double *)malloc(sizeof(double) * (size_t)H * 16);
+        orc_particle_wind(P, l, m, own);
+        Wm = own;
+    }
 
     for (int i = 0; i < N; i++) {
         acst *s = &st[i];
@@ -471,6 +509,7 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
     }
     if (smg) *smg = smin;
     if (live) *live += nlive;
+    free(own);
 }
 
 void orc_rollout(const orc_problem *P, const orc_aircraft *A, const double *W, int m0, int mc,
@@ -615,11 +654,12 @@ double orc_rollout_grad(const orc_problem *P, const orc_aircraft *A, const doubl
     const int64_t Pn = (int64_t)P->grid[0] * P->grid[1] * P->grid[2];
     const double dt = P->dt, sgmax = sin(P->gamma_max), tpmax = tan(P->phi_max);
     const double Sh = P->sep_h, Sv = P->sep_v, bet = P->sp_beta, mu = P->mu_sep;
+    for (int n = 0; n < N * S * 3; n++) grad[n] = 0.0;
+    if (P->wind_mode != 0) return NAN;      /* the gradient uses the shared wind field */
     gstep *tr = (gstep *)malloc(sizeof(gstep) * (size_t)(H + 1) * N);
     double *gs = (double *)calloc((size_t)N * S * 3, sizeof(double));
     double total = 0.0;
     int infeasible = 0;
-    for (int n = 0; n < N * S * 3; n++) grad[n] = 0.0;
 
     for (int m = 0; m < M && !infeasible; m++) {
         const double *Wm = W + (int64_t)m * H * Pn * 2;

@@ -49,6 +49,10 @@ typedef struct {
     double P_runway, P_beta, P_chi, P_vs, beta_f;
     uint32_t wind_stream;         /* random stream of the wind normals: 3, or 8 for held-out
                                      evaluation samples (0 reads as 3) */
+    int wind_mode;                /* 0 one field per wind sample shared by all particles;
+                                     1 a field per (particle, sample) on the 2x2x2 grid of
+                                     the box corners (the paper's scheme) */
+    const double *wind_chol;      /* mode 1: lower Cholesky factor of R_hat, 8 x 8 row-major */
 } orc_problem;
 
 typedef struct {
@@ -72,6 +76,11 @@ void orc_draw(const orc_problem *P, uint32_t c0, uint32_t c1, uint32_t q, uint32
 /* Standard normals v_X, v_Y of the wind model for samples m0..m0+mc-1:
  * out[mc][H][P][2]. */
 void orc_wind_normals(const orc_problem *P, int m0, int mc, double *out);
+
+/* Mode 1 wind of particle l, sample m: out[H][8][2] = (W_X, W_Y) at the eight
+ * box-corner nodes, W(k) = Qhat B(k), B(0) = v(0), B(k) = a B(k-1) + sqrt(1-a^2) v(k)
+ * (the recursion of Sec. 3.9.1), v from random stream 9. */
+void orc_particle_wind(const orc_problem *P, int64_t l, int m, double *out);
 
 /* Rollout of particles `pidx` (global indices) under wind samples m0..m0+mc-1.
  * W holds those samples: W[mc][H][P][2].  u[Lsub][N][S][3].

@@ -142,3 +142,76 @@ def test_held_out_wind_stream_is_independent():
     assert abs(np.corrcoef(v3.ravel(), v8.ravel())[0, 1]) < 0.05
     assert abs(v8.std() - 1.0) < 0.05 and abs(v8.mean()) < 0.05
     assert np.array_equal(O.wind_normals(p.copy(wind_stream=3)), v3)
+
+
+# ---------------------------------------------------------------- per-particle wind (mode 1)
+
+def _mode1(p=None, **kw):
+    base = S.shrink(S.config1(), M=3, H=8, grid=(2, 2, 2)) if p is None else p
+    return base.copy(wind_mode=1, **kw)
+
+
+def test_particle_wind_is_the_paper_recursion():
+    """W(0) = Qhat v(0), W(k+1) = a W(k) + Q v(k+1) with QQ^T = (1-a^2) R_hat and
+    Qhat Qhat^T = R_hat (Sec. 3.9.1), factorised here independently, with the
+    normals of random stream 9 re-derived from the counter layout."""
+    p = _mode1()
+    R = O.wind_covariance(p)
+    a = O.wind_ar_coefficient(p)
+    Qhat = np.linalg.cholesky(R)
+    Q = np.linalg.cholesky((1 - a * a) * R)
+    for l, m in ((0, 0), (7, 2), (2 ** 31 + 5, 1)):
+        got = O.particle_wind(p, l, m)
+        W = np.zeros((8, 2))
+        for k in range(p.H):
+            v = np.empty((8, 2))
+            for r in range(4):
+                w = O.draw(p, l & 0xFFFFFFFF, 4 * m + r, k, 9, 0)
+                v[2 * r] = O.box_muller(w[0], w[1])
+                v[2 * r + 1] = O.box_muller(w[2], w[3])
+            W = Qhat @ v if k == 0 else a * W + Q @ v
+            assert np.allclose(got[k], W, rtol=1e-12, atol=1e-12), (l, m, k)
+
+
+def test_particle_wind_statistics():
+    """Across particles the field at every step has covariance R_hat, and the
+    lag-one correlation of a node is a."""
+    p = _mode1(S.shrink(S.config1(), M=1, H=4, grid=(2, 2, 2)).copy(lam_t=0.02))
+    R = O.wind_covariance(p)
+    a = O.wind_ar_coefficient(p)
+    n = 6000
+    F = np.stack([O.particle_wind(p, l, 0) for l in range(n)])      # [n][H][8][2]
+    for k in (0, 3):
+        X = F[:, k, :, 0]
+        C = np.cov(X.T)
+        assert np.allclose(C, R, atol=5 * R[0, 0] * np.sqrt(2.0 / n)), k
+    x0, x1 = F[:, 2, 3, 1], F[:, 3, 3, 1]
+    rho = np.corrcoef(x0, x1)[0, 1]
+    assert abs(rho - a) < 4 * (1 - a * a) / np.sqrt(n) + 0.01
+
+
+def test_particle_wind_differs_between_particles_and_samples():
+    p = _mode1()
+    w00, w10, w01 = O.particle_wind(p, 0, 0), O.particle_wind(p, 1, 0), O.particle_wind(p, 0, 1)
+    assert not np.allclose(w00, w10) and not np.allclose(w00, w01)
+    assert np.array_equal(w00, O.particle_wind(p, 0, 0))
+
+
+def test_mode1_rollout_uses_each_particles_own_field():
+    """With the control sequence shared, two particles differ only by their
+    random streams; with turbulence off, two samples of one particle differ
+    only by their wind field, and the rollout's interpolation of that field is
+    the trilinear interpolation of the corner values."""
+    p = _mode1(turb_sigma=0.0)
+    rng = np.random.default_rng(3)
+    u = np.repeat(S.mild_controls(p, 1, rng).astype(np.float64), 2, axis=0)
+    r = O.rollout(p, u, 0, pidx=np.array([4, 9]))
+    assert not np.allclose(r["cost_soft"][0], r["cost_soft"][1])
+    r2 = O.rollout(p, u[:1], 0, pidx=np.array([4]))
+    assert np.array_equal(r2["cost_soft"][0], r["cost_soft"][0])
+    # the trajectory of sample m under mode 1 equals the mode-0 trajectory run
+    # on that particle's field
+    Wl = O.particle_wind(p, 4, 1)
+    t1, _, _ = O.trajectory(p, u[0], np.zeros((p.H, 8, 2)), l=4, m=1)
+    t0, _, _ = O.trajectory(p.copy(wind_mode=0), u[0], Wl, l=4, m=1)
+    assert np.array_equal(t1, t0)
