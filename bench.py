@@ -369,6 +369,9 @@ def run_rollout_only(args, local):
     torch.cuda.set_device(local)
     pkg.build()
     p = S.make_config(args.config).copy(L=args.particles or 4096)
+    if args.wind != "shared":
+        # the 2x2x2 grid of the box corners: one shared field, or one per particle
+        p = p.copy(grid=(2, 2, 2), wind_mode=1 if args.wind == "own" else 0)
     solver = pkg.Solver(p)
     if args.late:
         # the particles of a finished solve: the live mix of the late iterations
@@ -391,6 +394,7 @@ def run_rollout_only(args, local):
     ms = ev0.elapsed_time(ev1) / max(args.steps, 1)
     units = p.L * p.M * p.N * p.H
     print(json.dumps({"mode": "rollout-only", "config": args.config, "N": p.N, "late": bool(args.late),
+                      "wind": args.wind,
                       "particles": p.L, "ms_per_rollout": ms,
                       "units_per_s": units / (ms * 1e-3), "live_steps": solver.live_steps()}))
     solver.close()
@@ -715,6 +719,9 @@ def main(argv=None):
                     help="time only the gradient pass on --particles particles (profiling case)")
     ap.add_argument("--moves", action="store_true",
                     help="compare the paper's move with accepted random-walk and Langevin moves")
+    ap.add_argument("--wind", choices=("shared", "corners", "own"), default="shared",
+                    help="--rollout-only: the workload's shared field, a shared field on the 2x2x2 "
+                         "corner grid, or every particle's own field on that grid")
     ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--eps-rw", type=float, default=1.0)
     ap.add_argument("--eps-mala", type=float, default=0.3)

@@ -92,6 +92,11 @@ typedef struct {
     double pop_lo[2], pop_hi[2];
     const double *popdense;   /* host [pop_n[0]][pop_n[1]]; copied by tma_create */
     double P_runway, P_beta, P_chi, P_vs, beta_f;  /* landing sector (Eq. (TO_init)), glide angle */
+    int32_t wind_mode;        /* 0: one wind field per sample, shared by all particles (grid as
+                                 above); 1: a field per (particle, sample) on the 2x2x2 grid of the
+                                 box corners (grid must be 2,2,2), drawn inside the rollout from
+                                 random stream 9 -- the paper's scheme (Sec. 3.9.1, Sec. 6).
+                                 tma_rollout_grad and the accepted moves need mode 0. */
 } tma_problem;
 
 typedef struct {

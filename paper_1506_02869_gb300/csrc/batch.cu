@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
                 const long long l0 = (it - (long long)m * nLb) * kPB;
                 const TileResult r = rollout_tile(
                     Ps, dyns + s, u + Sc.u_off, W + Sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0, i, lane,
-                    m, J, cost_ms_soft != nullptr, spos + (size_t)q * tile_smem_words(Ns), bar, cnt);
+                    m, J, cost_ms_soft != nullptr, spos + (size_t)q * tile_smem_words(Ns, Ps.wind_mode),
+                    bar, cnt);
                 const size_t cbase = (size_t)Sc.seg_off * Ps.M * (size_t)L;
                 store_tile(r, Ns, L, l0 + lane, i, lane, m, cost_ms + cbase,
                            cost_ms_soft ? cost_ms_soft + cbase : nullptr, live);
@@ -317,8 +318,9 @@ __global__ void stamp_start(unsigned long long *t0)
 
 // The true system of Fig. 1: every aircraft flies its scenario's chosen
 // controls of the first segment for one step dt.  The disturbance is the
-// scenario's wind field of sample 0 at step 0 plus white turbulence from
-// random stream 7; the climb angle is kept below 90 degrees and the thrust
+// scenario's wind field of sample 0 at step 0 (in wind mode 1: step 0 of the
+// corner-grid field of the reserved particle index 0xFFFFFFFF, sample 0) plus
+// white turbulence from random stream 7; the climb angle is kept below 90 degrees and the thrust
 // within its limits (the plant cannot refuse a command), and the speed and
 // fuel follow from the applied thrust.  The state is written back for the
 // next MPC step.
@@ -351,7 +353,22 @@ __global__ void __launch_bounds__(128) plant_step_kernel(const ProblemC *__restr
     const float CL = mass * kG0 * cg * secphi / qS;
     const float D = qS * fmaf(A.CD2, CL * CL, A.CD0);
     const float T = clampf(fmaf(mass, fmaf(kG0, sg, ua), D), A.Tmin, A.Tmax);
-    float2 w = wind_interp(wind_fetch(P, W + sc.w_off, x, y, z));
+    float2 w;
+    if (P.wind_mode == 1) {
+        float B[16];                   // B(0) = v(0): draws r = 0..3 of stream 9
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 e = draw(P.key0, P.key1, 0xFFFFFFFFu, (uint32_t)q, 0u, 9u, 0u, d.mpc_step);
+            const float2 v0 = box_muller(e.x, e.y), v1 = box_muller(e.z, e.w);
+            B[4 * q] = v0.x;
+            B[4 * q + 1] = v0.y;
+            B[4 * q + 2] = v1.x;
+            B[4 * q + 3] = v1.y;
+        }
+        w = particle_wind_at<1>(P, B, x, y, z);
+    } else {
+        w = wind_interp(wind_fetch(P, W + sc.w_off, x, y, z));
+    }
     const uint4 r = draw(P.key0, P.key1, 0u, (uint32_t)i, 0u, 7u, 0u, d.mpc_step);
     const float2 n = box_muller(r.x, r.y);
     w.x = fmaf(P.turb_sigma, n.x, w.x);
@@ -384,7 +401,7 @@ size_t batch_rollout_smem()
 {
     size_t best = 0;
     for (int n = 1; n <= kMaxN; ++n)
-        best = std::max(best, (size_t)(32 / n) * tile_smem_words(n) * sizeof(float));
+        best = std::max(best, (size_t)std::min(15, 32 / n) * tile_smem_words(n, 1) * sizeof(float));
     return best;
 }
 

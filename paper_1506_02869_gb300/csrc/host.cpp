@@ -164,6 +164,9 @@ static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
     for (int d = 0; d < 3; ++d)
         if (p->grid[d] < 2 || !(p->box_hi[d] > p->box_lo[d])) return TMA_ERR_INVALID_ARG;
     if (p->grid[2] > TMA_MAX_GRID_Z) return TMA_ERR_INVALID_ARG;
+    if (p->wind_mode != 0 && p->wind_mode != 1) return TMA_ERR_INVALID_ARG;
+    if (p->wind_mode == 1 && (p->grid[0] != 2 || p->grid[1] != 2 || p->grid[2] != 2))
+        return TMA_ERR_INVALID_ARG;
     if ((long long)p->grid[0] * p->grid[1] > 16384) return TMA_ERR_INVALID_ARG;
     if (!(p->sep_h > 0) || !(p->sep_v > 0) || p->sep_mode < 0 || p->sep_mode > 2)
         return TMA_ERR_INVALID_ARG;
@@ -207,6 +210,29 @@ static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraf
         P.inv_h[d] = (float)((p.grid[d] - 1) / (p.box_hi[d] - p.box_lo[d]));
     }
     P.dt = (float)p.dt;
+    P.wind_mode = p.wind_mode;
+    if (p.wind_mode == 1) {
+        // Qhat for the field of one (particle, sample): Cholesky factor (FP64) of
+        // R_hat = sigma^2 exp(-beta |dxy|) exp(-gamma |dz|) over the eight box
+        // corners, node index (ix * 2 + iy) * 2 + iz
+        std::vector<double> R(64);
+        for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b) {
+                const int ax = a >> 2, ay = (a >> 1) & 1, az = a & 1;
+                const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
+                const double dx = (ax - bx) * (p.box_hi[0] - p.box_lo[0]);
+                const double dy = (ay - by) * (p.box_hi[1] - p.box_lo[1]);
+                const double dz = (az - bz) * (p.box_hi[2] - p.box_lo[2]);
+                R[a * 8 + b] = p.wind_sigma * p.wind_sigma * std::exp(-p.beta_xy * std::sqrt(dx * dx + dy * dy)) *
+                               std::exp(-p.gam_z * std::fabs(dz));
+            }
+        if (cholesky_lower(R, 8))
+            for (int n = 0, k = 0; n < 8; ++n)
+                for (int j = 0; j <= n; ++j) P.wchol[k++] = (float)R[n * 8 + j];
+        const double a = std::exp(-p.dt * p.lam_t);
+        P.wind_a = (float)a;
+        P.wind_b = (float)std::sqrt(std::max(0.0, 1.0 - a * a));
+    }
     P.turb_sigma = (float)p.turb_sigma;
     P.sgmax = (float)std::sin(p.gamma_max);
     P.tpmax = (float)std::tan(p.phi_max);
@@ -365,7 +391,8 @@ static std::string tune_key(const tma_solver *s)
     cudaDeviceProp prop;
     char key[320];
     if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) prop.name[0] = 0;
-    snprintf(key, sizeof key, "%s|N=%d|pop=%d", prop.name, s->prob.N, s->prob.pop_n[0] > 0);
+    snprintf(key, sizeof key, "%s|N=%d|pop=%d|wind=%d", prop.name, s->prob.N, s->prob.pop_n[0] > 0,
+             s->prob.wind_mode);
     return key;
 }
 
@@ -721,7 +748,8 @@ tma_status tma_wind_field(tma_solver *s, float *d_W, tma_stream_t stream)
 static tma_status rollout_into(tma_solver *s, const float *d_u, int64_t L, int32_t J, float *cbar,
                                float *cbar_soft, cudaStream_t st, bool reset_live)
 {
-    if (!s->wind_ready) {
+    // wind mode 1 draws each particle's field inside the rollout: no shared field
+    if (!s->wind_ready && s->P.wind_mode == 0) {
         tma_status r = gen_wind(s, st);
         if (r != TMA_OK) return r;
     }
@@ -936,7 +964,7 @@ extern "C" tma_status tma_rollout_grad(tma_solver *s, const float *d_u, int64_t 
 {
     if (!s || !d_u || !d_cost || !d_grad || L < 0 || L > s->prob.L || J < 0 || J > 0xFFFF)
         return TMA_ERR_INVALID_ARG;
-    if (s->prob.H > TMA_MAX_GRAD_HORIZON) return TMA_ERR_UNSUPPORTED;
+    if (s->prob.H > TMA_MAX_GRAD_HORIZON || s->prob.wind_mode != 0) return TMA_ERR_UNSUPPORTED;
     if (L == 0) return TMA_OK;
     return grad_into(s, d_u, L, J, d_cost, d_grad, d_cbar_soft, (cudaStream_t)stream);
 }
@@ -979,7 +1007,8 @@ extern "C" tma_status tma_set_move(tma_solver *s, int32_t kind, double eps0)
         return TMA_OK;
     }
     if (!(eps0 > 0.0) || !std::isfinite(eps0) || s->prob.sep_mode == 0) return TMA_ERR_INVALID_ARG;
-    if (kind == TMA_MOVE_MALA && s->prob.H > TMA_MAX_GRAD_HORIZON) return TMA_ERR_UNSUPPORTED;
+    if (kind == TMA_MOVE_MALA && (s->prob.H > TMA_MAX_GRAD_HORIZON || s->prob.wind_mode != 0))
+        return TMA_ERR_UNSUPPORTED;
     tma_status r = ensure_mh_scalars(s);
     if (r != TMA_OK) return r;
     const tma_problem &p = s->prob;
@@ -1301,7 +1330,7 @@ static tma_status plant_async(tma_solver *s, const float *d_u, cudaStream_t st)
         if (!e) e = cudaMemset(s->d_seg_scen1, 0, sizeof(int) * TMA_MAX_AIRCRAFT);
         if (e) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : cuda_fail(e);
     }
-    if (!s->wind_ready) {
+    if (!s->wind_ready && s->P.wind_mode == 0) {
         tma_status r = gen_wind(s, st);
         if (r != TMA_OK) return r;
     }
@@ -1414,7 +1443,7 @@ static bool same_shape(const tma_problem &a, const tma_problem &b)
 {
     bool ok = a.L == b.L && a.M == b.M && a.H == b.H && a.S == b.S && a.J_max == b.J_max &&
               a.dt == b.dt && a.beta_xy == b.beta_xy && a.gam_z == b.gam_z && a.lam_t == b.lam_t &&
-              a.wind_sigma == b.wind_sigma && a.sep_mode == b.sep_mode;
+              a.wind_sigma == b.wind_sigma && a.sep_mode == b.sep_mode && a.wind_mode == b.wind_mode;
     for (int d = 0; d < 3; ++d)
         ok = ok && a.grid[d] == b.grid[d] && a.box_lo[d] == b.box_lo[d] && a.box_hi[d] == b.box_hi[d];
     return ok;
@@ -1425,7 +1454,8 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
     const long long L = b->L;
     const size_t P = (size_t)b->probs[0].grid[0] * b->probs[0].grid[1] * b->probs[0].grid[2];
     TMA_CUDA(launch_stamp_start(b->d_t_start, st));
-    for (size_t g = 0; g < b->wind_groups.size(); ++g) {
+    // wind mode 1 (the same for the whole batch) draws each particle's field in the rollout
+    for (size_t g = 0; g < b->wind_groups.size() && b->probs[0].wind_mode == 0; ++g) {
         const WindC &w = b->wind_groups[g];
         const int s0 = b->group_start[g];
         TMA_CUDA(launch_batch_wind_normals(w, s0, b->M, b->d_scen, b->d_dyns, b->d_Btmp, st));

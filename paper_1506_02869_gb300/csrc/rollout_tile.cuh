@@ -137,6 +137,56 @@ __device__ __forceinline__ float softplus(float g, float beta, float inv_beta)
 
 constexpr int kPB = kTileParticles;
 
+// Mode-1 wind (a field per (particle, sample) on the 2x2x2 grid of the box
+// corners, the paper's scheme): the state B of the particle's eight nodes lives
+// in the tile's shared buffer pw[2 (step parity)][16 (node * 2 + component)][32
+// lanes].  Draw r = 0..3 of random stream 9 (counter l, 4 m + r, step k) gives
+// nodes 2r and 2r + 1; warp r mod N draws it.  B(0) = v(0), B(k) = a B(k-1) +
+// sqrt(1 - a^2) v(k), W(k) = Qhat B(k) (Sec. 3.9.1).
+__device__ __forceinline__ void particle_wind_step(const ProblemC &P, float *pw, int i, int N, int j,
+                                                   uint32_t l, int m, int k, uint32_t mpc)
+{
+    float *dst = pw + (k & 1) * 16 * kPB + j;
+    const float *src = pw + ((k + 1) & 1) * 16 * kPB + j;     // B(k-1)
+    for (int r = i; r < 4; r += N) {
+        const uint4 d = draw(P.key0, P.key1, l, (uint32_t)(4 * m + r), (uint32_t)k, 9u, 0u, mpc);
+        const float2 v0 = box_muller_fast(d.x, d.y), v1 = box_muller_fast(d.z, d.w);
+        const float v[4] = {v0.x, v0.y, v1.x, v1.y};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int row = 4 * r + e;        // node 2r + e / 2, component e % 2
+            dst[row * kPB] = k == 0 ? v[e] : fmaf(P.wind_a, src[row * kPB], P.wind_b * v[e]);
+        }
+    }
+}
+
+// Wind of that field at a position (clamped into the box): with the trilinear
+// weights w_n of the corners, W = sum_n w_n sum_j Qhat[n][j] B_j = sum_j g_j B_j,
+// g_j = sum_(n >= j) w_n Qhat[n][j].  B holds row (node * 2 + component) at
+// B[row * Stride]: pw[k & 1] + lane with Stride kPB in the tile.
+template <int Stride = kPB>
+__device__ __forceinline__ float2 particle_wind_at(const ProblemC &P, const float *B, float x, float y,
+                                                   float z)
+{
+    const float tx = fminf(fmaxf((x - P.box_lo[0]) * P.inv_h[0], 0.0f), 1.0f);
+    const float ty = fminf(fmaxf((y - P.box_lo[1]) * P.inv_h[1], 0.0f), 1.0f);
+    const float tz = fminf(fmaxf((z - P.box_lo[2]) * P.inv_h[2], 0.0f), 1.0f);
+    float wn[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+        wn[n] = ((n & 4) ? tx : 1.0f - tx) * ((n & 2) ? ty : 1.0f - ty) * ((n & 1) ? tz : 1.0f - tz);
+    float2 w = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int jn = 0; jn < 8; ++jn) {
+        float g = 0.0f;
+#pragma unroll
+        for (int n = jn; n < 8; ++n) g = fmaf(wn[n], P.wchol[n * (n + 1) / 2 + jn], g);
+        w.x = fmaf(g, B[(2 * jn) * Stride], w.x);
+        w.y = fmaf(g, B[(2 * jn + 1) * Stride], w.y);
+    }
+    return w;
+}
+
 __device__ __forceinline__ void tile_barrier(int id, int count)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -206,13 +256,14 @@ struct CostSums {
 // visit.arrival or visit.departure, then visit.noise when the noise cost is
 // on.  Returns false when the control limits failed (the aircraft did not
 // move); otherwise s.dead / s.landed tell whether it stopped at this step.
-// ul = this particle's controls of this aircraft [S][3].
+// ul = this particle's controls of this aircraft [S][3]; the wind is the
+// sample's shared field Wk, or the particle's own field when pwk is given.
 template <class Visit>
 __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, AcState &s,
                                         const float *__restrict__ ul,
                                         const float4 *__restrict__ Wk, float m0, uint32_t l,
                                         uint32_t i, uint32_t m, int k, int J, uint32_t mpc,
-                                        Visit &visit)
+                                        Visit &visit, const float *pwk = nullptr)
 {
     const float dt = P.dt;
     if (k >= s.knext) {
@@ -246,7 +297,8 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
         return false;
     }
     // disturbance: wind field of sample m plus white turbulence
-    float2 w = wind_interp(wind_fetch(P, Wk, s.x, s.y, s.z));
+    float2 w = pwk ? particle_wind_at(P, pwk, s.x, s.y, s.z)
+                   : wind_interp(wind_fetch(P, Wk, s.x, s.y, s.z));
     float2 n;
     if ((k & 1) == 0) {
         const uint4 r = draw(P.key0, P.key1, l, i | (m << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
@@ -338,20 +390,21 @@ __device__ __forceinline__ float total_objective(const ProblemC &P, const Aircra
 }
 
 // Shared memory of one tile (32-bit words): positions float4 [2][N][32]
-// (double-buffered by step), separation flags [N][32], and the received
-// separation penalties [2][N][floor((N-1)/2) + 1][32] of the soft form.
+// (double-buffered by step), separation flags [N][32], the received
+// separation penalties [2][N][floor((N-1)/2) + 1][32] of the soft form, and in
+// wind mode 1 the particles' wind state [2][16][32].
 __host__ __device__ constexpr int tile_pair_slots(int N) { return (N - 1) / 2 + 1; }
-__host__ __device__ constexpr int tile_smem_words(int N)
+__host__ __device__ constexpr int tile_smem_words(int N, int wind_mode)
 {
-    return (9 * N + 2 * N * tile_pair_slots(N)) * kTileParticles;
+    return (9 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) * kTileParticles;
 }
 
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
 // packed wind field Wm of sample m and returns its per-sample costs (the
 // softplus variant when soft_on); the caller stores them (store_tile), so
 // that no output pointer is live during the steps.  spos is the tile's
-// tile_smem_words(N) buffer; every warp of the tile must call this with the
-// same barrier (bar_id, bar_count threads).
+// tile_smem_words(N, P.wind_mode) buffer; every warp of the tile must call this
+// with the same barrier (bar_id, bar_count threads).
 //
 // Separation (Eq. (avoidance)) checks every unordered pair once: warp i takes
 // the partners i+d, d = 1 .. floor((N-1)/2) (mod N), and for even N also
@@ -366,12 +419,14 @@ struct TileResult {
     unsigned int live;  // aircraft-steps simulated by this thread
 };
 
-__device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
-                                                   const float *__restrict__ u,
-                                                   const float4 *__restrict__ Wm, long long L,
-                                                   long long l0, int i, int j, int m, int J,
-                                                   bool soft_on, float *spos, int bar_id,
-                                                   int bar_count)
+// OwnWind: wind mode 1 (compiled apart, so mode 0 keeps its register budget).
+template <bool OwnWind>
+__device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
+                                                        const float *__restrict__ u,
+                                                        const float4 *__restrict__ Wm, long long L,
+                                                        long long l0, int i, int j, int m, int J,
+                                                        bool soft_on, float *spos, int bar_id,
+                                                        int bar_count)
 {
     const int N = P.N;
     const long long l = l0 + j;
@@ -397,13 +452,21 @@ __device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynS
     const bool even = (N & 1) == 0;
     const int n_pairs = n_half + ((even && i < (N >> 1)) ? 1 : 0);
     const int n_recv = n_half + ((even && i >= (N >> 1)) ? 1 : 0);
+    constexpr bool own_wind = OwnWind;
+    float *pw = spos + (9 * N + 2 * N * slots) * kPB;      // mode 1: [2][16][32]
+    if constexpr (own_wind) {
+        particle_wind_step(P, pw, i, N, j, (uint32_t)l, m, 0, mpc);
+        tile_barrier(bar_id, bar_count);
+    }
 
     for (int k = 0; k < P.H; ++k) {
         if (!s.dead && !s.landed) {
             ++nlive;
             ac_step(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i, (uint32_t)m, k,
-                    J, mpc, cs);
+                    J, mpc, cs, own_wind ? pw + (k & 1) * 16 * kPB + j : nullptr);
         }
+        // the particles' wind state of the next step, read after this step's barrier
+        if (own_wind && k + 1 < P.H) particle_wind_step(P, pw, i, N, j, (uint32_t)l, m, k + 1, mpc);
         // binary separation constraints at step k+1 among flying aircraft: every
         // thread publishes its position (a far-away altitude when not flying)
         const bool act = !s.dead && !s.landed;
@@ -464,6 +527,18 @@ __device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynS
     r.cost_soft = s.dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
     r.live = exists ? nlive : 0u;
     return r;
+}
+
+__device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
+                                                   const float *__restrict__ u,
+                                                   const float4 *__restrict__ Wm, long long L,
+                                                   long long l0, int i, int j, int m, int J,
+                                                   bool soft_on, float *spos, int bar_id,
+                                                   int bar_count)
+{
+    if (P.wind_mode == 1)
+        return rollout_tile_mode<true>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos, bar_id, bar_count);
+    return rollout_tile_mode<false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos, bar_id, bar_count);
 }
 
 // Stores one thread's tile result: cost_ms[(m N + i) L + l] (and the soft

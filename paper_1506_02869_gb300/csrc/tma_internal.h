@@ -45,6 +45,9 @@ struct ProblemC {
     float pop_lo[2], pop_hi[2], pop_inv_h[2];
     const float *popdense; // device [pop_n0][pop_n1] or nullptr
     float P_runway, P_beta, P_chi, P_vs, beta_f;
+    int wind_mode;         // 1: a wind field per (particle, sample) on the box corners
+    float wind_a, wind_b;  // AR(1) coefficients a, sqrt(1 - a^2) of that field
+    float wchol[36];       // its Qhat: lower Cholesky factor of R_hat (8 x 8, packed rows)
     uint32_t key0, key1;   // Philox key (seed + scenario_id * golden)
     AircraftC ac[kMaxN];
 };
