@@ -233,7 +233,7 @@ def wind_ar_coefficient(p):
 
 
 def particle_wind(p, l, m):
-    """Mode-1 wind of particle l, sample m: [H][8][2] on the box corners (reading R18)."""
+    """Mode-1 wind of particle l, sample m: [H][8][2] on the box corners (reading R19)."""
     out = np.empty((p.H, 8, 2), np.float64)
     mm = _Marshalled(p)
     lib().orc_particle_wind(mm.ps, int(l), int(m), _ptr(out, C.c_double))

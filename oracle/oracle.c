@@ -68,6 +68,17 @@
  *      counter (c0, c1, q | stream<<24, J | mpc_step<<16); uniforms use the
  *      top 23 bits, ((x>>9)+0.5)/2^23 (an odd multiple of 2^-24, exact in FP32
  *      and FP64); normals by Box-Muller.
+ *  R15 Plant (Fig. 1): one step dt of the chosen first-segment controls
+ *      under the wind of sample 0 at step 0 plus turbulence (stream 7), with
+ *      |sin(gamma)| held at 0.999 and T held within [Tmin, Tmax].
+ *  R16 Gradient (an extension): reverse mode of the soft objective over the
+ *      discrete dynamics; every limit, landing, cell and min/|.| decision keeps
+ *      its forward value.
+ *  R17 Metropolis-Hastings moves (an extension): target exp(-kappa C(u)) per
+ *      particle, coordinates scaled by the move step of their kind.
+ *  R18 Held-out evaluation winds: the wind model drawn from stream 8.
+ *  R19 Wind mode 1: one field per (particle, sample) on the 2x2x2 grid of the
+ *      box corners, drawn from stream 9 (see orc_particle_wind).
  */
 #include <math.h>
 #include <stdint.h>
@@ -152,7 +163,7 @@ void orc_wind_normals(const orc_problem *P, int m0, int mc, double *out)
     }
 }
 
-/* Mode 1 (reading R18): a wind field per (particle, sample) on the 2x2x2 grid of
+/* Mode 1 (reading R19): a wind field per (particle, sample) on the 2x2x2 grid of
  * the box corners, as the paper draws it inside its GPU kernel (Sec. 6).  The
  * recursion W(0) = Qhat v(0), W(k+1) = a W(k) + Q v(k+1), Q = sqrt(1 - a^2) Qhat,
  * is written W(k) = Qhat B(k) with B(0) = v(0), B(k) = a B(k-1) + sqrt(1-a^2) v(k).
