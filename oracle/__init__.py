@@ -442,6 +442,22 @@ def kappa(J: int) -> int:
     return lib().orc_kappa(J)
 
 
+def samples(p, J: int) -> int:
+    """Wind samples of iteration J: all M (sample mode 0), or the paper's inner
+    loop of Algorithm 1, SampleSchedule(J) draws, at most M (sample mode 1;
+    reading R20)."""
+    return min(kappa(J), p.M) if getattr(p, "sample_mode", 0) == 1 else p.M
+
+
+def exponent(p, J: int) -> int:
+    """The factor of the mean cost in the log-weight l = -exponent * cbar: the
+    annealing exponent kappa_J with M fixed samples (reading R10); with the
+    inner loop of Algorithm 1 the weight is the product of J_T over the
+    iteration's draws (Sec. 3.6), l = -sum_m c_m = -samples(p, J) * cbar
+    (reading R20)."""
+    return samples(p, J) if getattr(p, "sample_mode", 0) == 1 else kappa(J)
+
+
 def lse(cbar, kappa_J):
     """w~ = exp(l - max l) with l = -kappa * cbar per segment (row); returns
     (wtilde[nseg][L], lmax[nseg], wsum[nseg])."""
@@ -512,12 +528,13 @@ def smc_solve(p, W=None, nthreads=1, history=False):
     hist = []
     r = None
     for J in range(p.J_max):
-        r = rollout(p, u, J, W=W, nthreads=nthreads, soft=(p.sep_mode != 0))
+        Mj = samples(p, J)      # the first Mj samples of the solve's field
+        r = rollout(p.copy(M=Mj), u, J, W=W[:Mj], nthreads=nthreads, soft=(p.sep_mode != 0))
         cb = r["cbar_soft"] if p.sep_mode == 1 else r["cbar"]
         if history:
             hist.append({"J": J, "cbar": cb.copy(), "u": u.copy()})
         if J < p.J_max - 1:
-            wt, _, _ = lse(cb, kappa(J))
+            wt, _, _ = lse(cb, exponent(p, J))
             rr = [resample_uniform(p, i, J) for i in range(p.N)]
             anc, _ = resample(wt, rr)
             u = move(p, u, anc, J)

@@ -79,6 +79,11 @@
  *  R18 Held-out evaluation winds: the wind model drawn from stream 8.
  *  R19 Wind mode 1: one field per (particle, sample) on the 2x2x2 grid of the
  *      box corners, drawn from stream 9 (see orc_particle_wind).
+ *  R20 Sample mode 1 (the inner loop of Algorithm 1): iteration J uses the
+ *      first M_J = min(SampleSchedule(J), M) samples and the log-weight is
+ *      the log of the product of J_T over them, -M_J * (mean cost).  The
+ *      driver of the solve (oracle/__init__.py) applies it; the rollout here
+ *      takes the sample count as P->M.
  */
 #include <math.h>
 #include <stdint.h>

@@ -96,6 +96,7 @@ class Problem:
     beta_f: float = 3 * DEG
     wind_stream: int = 3                         # 8: held-out evaluation wind samples
     wind_mode: int = 0                           # 1: a field per (particle, sample), 2x2x2 grid
+    sample_mode: int = 0                         # 1: iteration J draws min(kappa_J, M) samples
     aircraft: Optional[np.ndarray] = None        # AIRCRAFT_DTYPE[N]
 
     def copy(self, **kw) -> "Problem":
