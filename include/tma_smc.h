@@ -97,6 +97,13 @@ typedef struct {
                                  box corners (grid must be 2,2,2), drawn inside the rollout from
                                  random stream 9 -- the paper's scheme (Sec. 3.9.1, Sec. 6).
                                  tma_rollout_grad and the accepted moves need mode 0. */
+    int32_t sample_mode;      /* 0: every iteration rolls out all M wind samples and weights by
+                                 l = -kappa_J * cbar (kappa_J = SampleSchedule(J), Sec. 5.1);
+                                 1: the inner loop of Algorithm 1 -- iteration J rolls out samples
+                                 0 .. M_J-1, M_J = min(SampleSchedule(J), M), and the weight is the
+                                 product of J_T over those draws (Sec. 3.6): l = -M_J * cbar.
+                                 tma_rollout_cost, tma_rollout_grad and the moves of iteration J
+                                 use M_J samples in mode 1. */
 } tma_problem;
 
 typedef struct {

@@ -64,7 +64,7 @@ class TmaProblem(C.Structure):
         ("pop_n", C.c_int32 * 2), ("pop_lo", C.c_double * 2), ("pop_hi", C.c_double * 2),
         ("popdense", C.POINTER(C.c_double)), ("P_runway", C.c_double), ("P_beta", C.c_double),
         ("P_chi", C.c_double), ("P_vs", C.c_double), ("beta_f", C.c_double),
-        ("wind_mode", C.c_int32),
+        ("wind_mode", C.c_int32), ("sample_mode", C.c_int32),
     ]
 
 
@@ -217,6 +217,7 @@ def problem_struct(p):
         setattr(s, n, float(_get(p, n)))
     s.sep_mode = int(_get(p, "sep_mode"))
     s.wind_mode = int(_get(p, "wind_mode", 0))
+    s.sample_mode = int(_get(p, "sample_mode", 0))
     s.ctrl_lo[:] = [float(v) for v in _get(p, "ctrl_lo")]
     s.ctrl_hi[:] = [float(v) for v in _get(p, "ctrl_hi")]
     s.move_sigma[:] = [float(v) for v in _get(p, "move_sigma")]

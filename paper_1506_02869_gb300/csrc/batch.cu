@@ -41,9 +41,11 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fm
 __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
     const ProblemC *__restrict__ probs, const BatchScen *__restrict__ scen, int n_scen,
     const DynState *__restrict__ dyns, const float *__restrict__ u, const float4 *__restrict__ W,
-    long long L, int nLb, int J, float *__restrict__ cost_ms, float *__restrict__ cost_ms_soft,
+    long long L, int nLb, int J, int Mj, float *__restrict__ cost_ms, float *__restrict__ cost_ms_soft,
     unsigned long long *__restrict__ live, unsigned long long *__restrict__ claimed)
 {
+    // this iteration's tiles: wind samples 0 .. Mj-1 (the cost rows keep the stride M)
+    const long long items = (long long)Mj * nLb;
     __shared__ ProblemC Ps;
     __shared__ BatchScen Sc;
     __shared__ long long slot_item[15];
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
     for (int s = 0; s < n_scen; ++s) {
         if (threadIdx.x == 0)
             skip_sh = *reinterpret_cast<volatile unsigned long long *>(claimed + s) >=
-                      (unsigned long long)scen[s].items;
+                      (unsigned long long)items;
         __syncthreads();            // also: the previous scenario's slots are done with Ps
         if (skip_sh) continue;
         {
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
                 if (i == 0 && lane == 0) slot_item[q] = (long long)atomicAdd(claimed + s, 1ull);
                 tile_barrier(bar, cnt);
                 const long long it = slot_item[q];
-                if (it >= Sc.items) break;
+                if (it >= items) break;
                 const int m = (int)(it / nLb);
                 const long long l0 = (it - (long long)m * nLb) * kPB;
                 const TileResult r = rollout_tile(
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(256) batch_sample_mean(const float *__restrict
                                                          const BatchScen *__restrict__ scen,
                                                          const int *__restrict__ seg_scen,
                                                          long long nseg, long long L, int M,
-                                                         float *__restrict__ cbar)
+                                                         int Mj, float *__restrict__ cbar)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nseg * L) return;
@@ -110,12 +112,12 @@ __global__ void __launch_bounds__(256) batch_sample_mean(const float *__restrict
     const size_t stride = (size_t)sc.N * L;
     Kahan acc;
     bool inf = false;
-    for (int m = 0; m < M; ++m) {
+    for (int m = 0; m < Mj; ++m) {
         const float v = __ldg(c + (size_t)m * stride);
         if (isinf(v)) inf = true;
         else acc.add(v);
     }
-    cbar[t] = inf ? __int_as_float(0x7f800000) : acc.s / (float)M;
+    cbar[t] = inf ? __int_as_float(0x7f800000) : acc.s / (float)Mj;
 }
 
 // ----------------------------------------------------------- move and init
@@ -407,7 +409,7 @@ size_t batch_rollout_smem()
 
 cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
                                  const DynState *dyns, const float *u, const float *W, long long L,
-                                 int J, float *cost_ms, float *cost_ms_soft,
+                                 int J, int Mj, float *cost_ms, float *cost_ms_soft,
                                  unsigned long long *live, unsigned long long *claimed, int grid,
                                  cudaStream_t st)
 {
@@ -415,7 +417,7 @@ cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, i
     if (e != cudaSuccess) return e;
     const int nLb = (int)((L + kPB - 1) / kPB);
     rollout_batched_kernel<<<grid, 1024, batch_rollout_smem(), st>>>(
-        probs, scen, n_scen, dyns, u, reinterpret_cast<const float4 *>(W), L, nLb, J, cost_ms,
+        probs, scen, n_scen, dyns, u, reinterpret_cast<const float4 *>(W), L, nLb, J, Mj, cost_ms,
         cost_ms_soft, live, claimed);
     count_launch();
     return cudaGetLastError();
@@ -437,9 +439,10 @@ int batch_rollout_grid()
 
 cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen,
                                      const int *seg_scen, long long nseg, long long L, int M,
-                                     float *cbar, cudaStream_t st)
+                                     int Mj, float *cbar, cudaStream_t st)
 {
-    batch_sample_mean<<<blocks_for(nseg * L, 256), 256, 0, st>>>(cost_ms, scen, seg_scen, nseg, L, M, cbar);
+    batch_sample_mean<<<blocks_for(nseg * L, 256), 256, 0, st>>>(cost_ms, scen, seg_scen, nseg, L, M,
+                                                                 Mj, cbar);
     count_launch();
     return cudaGetLastError();
 }

@@ -165,6 +165,7 @@ static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
         if (p->grid[d] < 2 || !(p->box_hi[d] > p->box_lo[d])) return TMA_ERR_INVALID_ARG;
     if (p->grid[2] > TMA_MAX_GRID_Z) return TMA_ERR_INVALID_ARG;
     if (p->wind_mode != 0 && p->wind_mode != 1) return TMA_ERR_INVALID_ARG;
+    if (p->sample_mode != 0 && p->sample_mode != 1) return TMA_ERR_INVALID_ARG;
     if (p->wind_mode == 1 && (p->grid[0] != 2 || p->grid[1] != 2 || p->grid[2] != 2))
         return TMA_ERR_INVALID_ARG;
     if ((long long)p->grid[0] * p->grid[1] > 16384) return TMA_ERR_INVALID_ARG;
@@ -373,6 +374,28 @@ struct StageTimer {
 };
 
 static int kappa_of(int J) { return (int)std::floor(3.0 + 5.0 * std::exp(0.05 * J)); }
+
+// Wind samples of iteration J: all M, or in sample mode 1 the inner loop of
+// Algorithm 1, SampleSchedule(J) draws (at most M).
+static int samples_of(const tma_problem &p, int J)
+{
+    return p.sample_mode == 1 ? std::min(kappa_of(J), p.M) : p.M;
+}
+
+// Factor of the mean cost in the log-weight: kappa_J with M fixed samples; in
+// sample mode 1 the product of J_T over the iteration's M_J draws (Sec. 3.6).
+static double exponent_of(const tma_problem &p, int J)
+{
+    return p.sample_mode == 1 ? (double)samples_of(p, J) : (double)kappa_of(J);
+}
+
+// The problem as the kernels of iteration J see it (M = that iteration's samples).
+static ProblemC problem_at(const tma_solver *s, int J)
+{
+    ProblemC P = s->P;
+    P.M = samples_of(s->prob, J);
+    return P;
+}
 
 // device address of DynState::mpc_step (pointer arithmetic only)
 static const uint32_t *dyn_mpc(const tma_solver *s)
@@ -754,20 +777,22 @@ static tma_status rollout_into(tma_solver *s, const float *d_u, int64_t L, int32
         if (r != TMA_OK) return r;
     }
     const bool soft = cbar_soft != nullptr;
+    const ProblemC Pj = problem_at(s, J);
     if (reset_live) TMA_CUDA(cudaMemsetAsync(s->d_live, 0, 8, st));
     {
         StageTimer t(s, 2, st);
-        TMA_CUDA(launch_rollout(s->P, s->d_dyn, d_u, s->d_W, L, J, s->d_cost_ms,
+        TMA_CUDA(launch_rollout(Pj, s->d_dyn, d_u, s->d_W, L, J, s->d_cost_ms,
                                 soft ? s->d_cost_ms_soft : nullptr, s->d_live, st,
                                 s->rollout_variant));
     }
     {
         StageTimer t(s, 3, st);
-        TMA_CUDA(launch_sample_mean(s->d_cost_ms, L, s->prob.M, s->prob.N, cbar, st));
+        TMA_CUDA(launch_sample_mean(s->d_cost_ms, L, Pj.M, s->prob.N, cbar, st));
         if (soft)
-            TMA_CUDA(launch_sample_mean(s->d_cost_ms_soft, L, s->prob.M, s->prob.N, cbar_soft, st));
+            TMA_CUDA(launch_sample_mean(s->d_cost_ms_soft, L, Pj.M, s->prob.N, cbar_soft, st));
     }
     s->last_L = L;
+    s->last_M = Pj.M;
     return TMA_OK;
 }
 
@@ -786,9 +811,14 @@ tma_status tma_sample_costs(tma_solver *s, float *d_out, int64_t L, int soft, tm
     const float *src = soft ? s->d_cost_ms_soft : s->d_cost_ms;
     if (!src) return TMA_ERR_INVALID_ARG;
     // the buffer holds [M][N][last_L]; copy out the first L particles of each row
+    // of the last call's samples, and NaN for the samples it did not use
     TMA_CUDA(cudaMemcpy2DAsync(d_out, (size_t)L * 4, src, (size_t)s->last_L * 4, (size_t)L * 4,
-                               (size_t)s->prob.M * s->prob.N, cudaMemcpyDeviceToDevice,
+                               (size_t)s->last_M * s->prob.N, cudaMemcpyDeviceToDevice,
                                (cudaStream_t)stream));
+    if (s->last_M < s->prob.M)
+        TMA_CUDA(cudaMemsetAsync(d_out + (size_t)s->last_M * s->prob.N * L, 0xFF,
+                                 (size_t)(s->prob.M - s->last_M) * s->prob.N * L * 4,
+                                 (cudaStream_t)stream));
     return TMA_OK;
 }
 
@@ -827,7 +857,7 @@ tma_status tma_init_controls(tma_solver *s, float *d_u, int64_t L, tma_stream_t 
 
 // Ranges of wind samples per gradient block: enough blocks for about two
 // waves of the device, at most one range per sample.
-static int grad_chunks(tma_solver *s, int64_t L, int variant)
+static int grad_chunks(tma_solver *s, int64_t L, int variant, int M)
 {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -835,7 +865,7 @@ static int grad_chunks(tma_solver *s, int64_t L, int variant)
     const long long tiles = (L + kTileParticles - 1) / kTileParticles;
     const long long want = 2LL * std::max(sms, 1) * per_sm;
     long long c = (want + tiles - 1) / std::max(tiles, 1LL);
-    return (int)std::max(1LL, std::min<long long>(c, s->prob.M));
+    return (int)std::max(1LL, std::min<long long>(c, M));
 }
 
 static tma_status ensure_grad_scratch(tma_solver *s, int64_t L, int nchunk)
@@ -881,7 +911,7 @@ static tma_status autotune_grad(tma_solver *s)
     const int64_t Lp = std::min<int64_t>(s->prob.L, 4096);
     const size_t nu = (size_t)Lp * s->prob.N * s->prob.S * 3;
     int max_chunks = 1;
-    for (int c = 0; c < nc; ++c) max_chunks = std::max(max_chunks, grad_chunks(s, Lp, cand[c]));
+    for (int c = 0; c < nc; ++c) max_chunks = std::max(max_chunks, grad_chunks(s, Lp, cand[c], s->prob.M));
     tma_status r = ensure_grad_scratch(s, Lp, max_chunks);
     if (r != TMA_OK) return r;
     cudaStream_t st = nullptr;
@@ -900,7 +930,7 @@ static tma_status autotune_grad(tma_solver *s)
     if (e == cudaSuccess) e = launch_init_controls(s->P, s->d_dyn, lo, hi, d_u, Lp, st);
     float best = 1e30f;
     for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-        const int nch = grad_chunks(s, Lp, cand[c]);
+        const int nch = grad_chunks(s, Lp, cand[c], s->prob.M);
         // one untimed launch, then two timed
         e = launch_rollout_grad(s->P, s->d_dyn, d_u, s->d_W, Lp, 0, nch, s->d_gcost_ms, s->d_gpart,
                                 nullptr, nullptr, nullptr, st, cand[c]);
@@ -941,11 +971,12 @@ static tma_status grad_into(tma_solver *s, const float *d_u, int64_t L, int32_t 
     }
     tma_status r = autotune_grad(s);
     if (r != TMA_OK) return r;
-    const int nchunk = grad_chunks(s, L, s->grad_variant);
+    const ProblemC Pj = problem_at(s, J);
+    const int nchunk = grad_chunks(s, L, s->grad_variant, Pj.M);
     r = ensure_grad_scratch(s, L, nchunk);
     if (r != TMA_OK) return r;
     StageTimer t(s, 8, st);
-    TMA_CUDA(launch_rollout_grad(s->P, s->d_dyn, d_u, s->d_W, L, J, nchunk, s->d_gcost_ms,
+    TMA_CUDA(launch_rollout_grad(Pj, s->d_dyn, d_u, s->d_W, L, J, nchunk, s->d_gcost_ms,
                                  s->d_gpart, cost, grad, cbar, st, s->grad_variant));
     return TMA_OK;
 }
@@ -1027,7 +1058,7 @@ extern "C" tma_status tma_set_move(tma_solver *s, int32_t kind, double eps0)
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : record_cuda_error(e);
     if (kind == TMA_MOVE_MALA) {
         r = autotune_grad(s);
-        if (r == TMA_OK) r = ensure_grad_scratch(s, p.L, grad_chunks(s, p.L, s->grad_variant));
+        if (r == TMA_OK) r = ensure_grad_scratch(s, p.L, grad_chunks(s, p.L, s->grad_variant, p.M));
         if (r != TMA_OK) return r;
     }
     s->move_kind = kind;
@@ -1103,7 +1134,7 @@ static tma_status mh_move(tma_solver *s, float *u_cur, int J, cudaStream_t st)
 {
     const tma_problem &p = s->prob;
     const int kind = s->move_kind;
-    const float kappa = (float)kappa_of(J);
+    const float kappa = (float)exponent_of(p, J);
     const MhParams h = mh_params(s, kind);
     if (kind == TMA_MOVE_MALA) {
         tma_status r = grad_into(s, u_cur, p.L, J, s->d_cost0, s->d_grad0, s->d_cbar0, st);
@@ -1161,7 +1192,7 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
         if (J < p.J_max - 1) {
             {
                 StageTimer t(s, 4, st);
-                TMA_CUDA(launch_lse(cb, p.N, p.L, (double)kappa_of(J), s->d_wtilde, nullptr, nullptr,
+                TMA_CUDA(launch_lse(cb, p.N, p.L, exponent_of(p, J), s->d_wtilde, nullptr, nullptr,
                                     s->d_work, st));
             }
             {
@@ -1443,7 +1474,8 @@ static bool same_shape(const tma_problem &a, const tma_problem &b)
 {
     bool ok = a.L == b.L && a.M == b.M && a.H == b.H && a.S == b.S && a.J_max == b.J_max &&
               a.dt == b.dt && a.beta_xy == b.beta_xy && a.gam_z == b.gam_z && a.lam_t == b.lam_t &&
-              a.wind_sigma == b.wind_sigma && a.sep_mode == b.sep_mode && a.wind_mode == b.wind_mode;
+              a.wind_sigma == b.wind_sigma && a.sep_mode == b.sep_mode && a.wind_mode == b.wind_mode &&
+              a.sample_mode == b.sample_mode;
     for (int d = 0; d < 3; ++d)
         ok = ok && a.grid[d] == b.grid[d] && a.box_lo[d] == b.box_lo[d] && a.box_hi[d] == b.box_hi[d];
     return ok;
@@ -1469,17 +1501,18 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
     const bool soft = b->sep_mode != 0;
     float *cb = b->sep_mode == 1 ? b->d_cbar_soft : b->d_cbar;
     for (int J = 0; J < b->J_max; ++J) {
+        const int Mj = samples_of(b->probs[0], J);
         TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, b->d_u[cur],
-                                      b->d_W, L, J, b->d_cost_ms,
+                                      b->d_W, L, J, Mj, b->d_cost_ms,
                                       soft ? b->d_cost_ms_soft : nullptr, b->d_live, b->d_queue,
                                       b->grid, st));
         TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms, b->d_scen, b->d_seg_scen, b->nseg, L, b->M,
-                                          b->d_cbar, st));
+                                          Mj, b->d_cbar, st));
         if (soft)
             TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms_soft, b->d_scen, b->d_seg_scen, b->nseg, L,
-                                              b->M, b->d_cbar_soft, st));
+                                              b->M, Mj, b->d_cbar_soft, st));
         if (J < b->J_max - 1) {
-            TMA_CUDA(launch_lse(cb, (int)b->nseg, L, (double)kappa_of(J), b->d_wtilde, nullptr,
+            TMA_CUDA(launch_lse(cb, (int)b->nseg, L, exponent_of(b->probs[0], J), b->d_wtilde, nullptr,
                                 nullptr, b->d_work, st));
             TMA_CUDA(launch_resample(b->d_wtilde, (int)b->nseg, L, 0u, 0u, (uint32_t)J, nullptr, 0u,
                                      b->d_anc, b->d_work, b->d_flags, st, b->d_segkeys, b->d_dyns));

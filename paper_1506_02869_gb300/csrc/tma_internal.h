@@ -160,12 +160,12 @@ int batch_rollout_grid();
 // claimed: one tile counter per scenario (zeroed by the launcher)
 cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, int n_scen,
                                  const DynState *dyns, const float *u, const float *W, long long L,
-                                 int J, float *cost_ms, float *cost_ms_soft,
+                                 int J, int Mj, float *cost_ms, float *cost_ms_soft,
                                  unsigned long long *live, unsigned long long *claimed, int grid,
                                  cudaStream_t st);
 cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen,
                                      const int *seg_scen, long long nseg, long long L, int M,
-                                     float *cbar, cudaStream_t st);
+                                     int Mj, float *cbar, cudaStream_t st);
 cudaError_t launch_batch_move(const BatchScen *scen, const int *seg_scen, const DynState *dyns,
                               long long nseg, long long L, int S, const float *u,
                               const int32_t *anc, int J, float *u_out, cudaStream_t st);
@@ -222,6 +222,7 @@ struct tma_solver {
     float *d_best_u = nullptr;
     int cur_u = 0;
     int64_t last_L = 0;
+    int last_M = 0;             // wind samples of the last rollout (M_J in sample mode 1)
     uint32_t mpc_step = 0;
     bool wind_ready = false;
     // stage profiling (CUDA events)

@@ -48,7 +48,8 @@ def test_struct_layout_matches_header(tmp_path):
     fields = {"tma_problem": (pkg.TmaProblem, ["N", "dt", "seed", "scenario_id", "box_lo", "grid",
                                                "wind_sigma", "sep_mode", "sp_beta", "ctrl_lo",
                                                "alpha_dep", "w_noise", "pop_n", "pop_lo",
-                                               "popdense", "P_runway", "beta_f", "wind_mode"]),
+                                               "popdense", "P_runway", "beta_f", "wind_mode",
+                                               "sample_mode"]),
               "tma_aircraft": (pkg.TmaAircraft, ["type", "x0", "theta_F", "m_empty", "Tmax"]),
               "tma_state": (pkg.TmaState, ["x", "m"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(){"]
@@ -86,7 +87,8 @@ def _create(p):
                                     dict(grid=(4, 4, 17)), dict(sep_mode=3), dict(dt=0.0),
                                     dict(J_max=0), dict(mpc_step=1 << 16), dict(sep_h=0.0),
                                     dict(v_min=300.0), dict(wind_mode=2), dict(wind_mode=-1),
-                                    dict(wind_mode=1, grid=(2, 2, 3)), dict(wind_mode=1, grid=(4, 4, 4))])
+                                    dict(wind_mode=1, grid=(2, 2, 3)), dict(wind_mode=1, grid=(4, 4, 4)),
+                                    dict(sample_mode=2), dict(sample_mode=-1)])
 def test_create_rejects_invalid_problems(lib, change):
     p = S.config1().copy(**change)
     if "N" in change and change["N"] > 2:
