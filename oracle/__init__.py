@@ -107,6 +107,8 @@ def lib():
             _lib.orc_resample_uniform.restype = u32
             _lib.orc_resample.argtypes = [P(d), i32, i32, P(u32), P(C.c_int32)]
             _lib.orc_resample.restype = i32
+            _lib.orc_resample_to.argtypes = [P(d), i32, i32, i32, P(u32), P(C.c_int32)]
+            _lib.orc_resample_to.restype = i32
             _lib.orc_move.argtypes = [P(OrcProblem), P(d), P(C.c_int32), i32, i32, P(d)]
             _lib.orc_init_controls.argtypes = [P(OrcProblem), i32, P(d)]
             _lib.orc_select.argtypes = [P(d), i32, i32, P(d), P(i32)]
@@ -476,24 +478,28 @@ def resample_uniform(p, seg: int, J: int) -> int:
     return lib().orc_resample_uniform(m.ps, seg, J)
 
 
-def resample(wtilde, r):
-    """Ancestors anc[nseg][L] of systematic resampling (reading R12); returns
-    (anc, number of degenerate segments)."""
+def resample(wtilde, r, L_out=None):
+    """Ancestors anc[nseg][L_out] of systematic resampling (reading R12; L_out
+    thresholds over the L weighted particles, reading R21; L_out = L by
+    default); returns (anc, number of degenerate segments)."""
     w = np.ascontiguousarray(wtilde, np.float64)
     nseg, L = w.shape
+    Lo = L if L_out is None else int(L_out)
     rr = np.ascontiguousarray(np.asarray(r, np.uint64).astype(np.uint32))
-    anc = np.empty((nseg, L), np.int32)
-    nd = lib().orc_resample(_ptr(w, C.c_double), nseg, L, _ptr(rr, C.c_uint32),
-                            _ptr(anc, C.c_int32))
+    anc = np.empty((nseg, Lo), np.int32)
+    nd = lib().orc_resample_to(_ptr(w, C.c_double), nseg, L, Lo, _ptr(rr, C.c_uint32),
+                               _ptr(anc, C.c_int32))
     return anc, nd
 
 
 def move(p, u, anc, J):
-    """u'[l][i] = clip(u[anc[i][l]][i] + sigma * xi) (Algorithm 1, perturbation)."""
+    """u'[l][i] = clip(u[anc[i][l]][i] + sigma * xi) (Algorithm 1, perturbation);
+    one child per ancestor entry, l < anc.shape[1]."""
     u = np.ascontiguousarray(u, np.float64).reshape(-1, p.N, p.S, 3)
-    L = u.shape[0]
-    a = np.ascontiguousarray(anc, np.int32)
-    out = np.empty_like(u)
+    a = np.ascontiguousarray(anc, np.int32).reshape(p.N, -1)
+    L = a.shape[1]
+    assert a.size == 0 or (a.min() >= 0 and a.max() < u.shape[0])
+    out = np.empty((L, p.N, p.S, 3))
     m = _Marshalled(p)
     lib().orc_move(m.ps, _ptr(u, C.c_double), _ptr(a, C.c_int32), L, J, _ptr(out, C.c_double))
     return out
@@ -518,13 +524,20 @@ def select(cbar):
     return int(best), bs.value, ni.value
 
 
+def particles(p, J: int) -> int:
+    """Particles evaluated in iteration J: L, or the particle schedule's entry
+    (reading R21)."""
+    sched = getattr(p, "L_sched", None)
+    return int(sched[J]) if sched is not None else p.L
+
+
 def smc_solve(p, W=None, nthreads=1, history=False):
     """One SMC optimisation (Algorithm 1) with the readings of oracle.c:
     J_max evaluations; between them per-aircraft resampling and perturbation;
     final selection from the last evaluation."""
     if W is None:
         W = wind_field(p)
-    u = init_controls(p)
+    u = init_controls(p, particles(p, 0))
     hist = []
     r = None
     for J in range(p.J_max):
@@ -536,7 +549,7 @@ def smc_solve(p, W=None, nthreads=1, history=False):
         if J < p.J_max - 1:
             wt, _, _ = lse(cb, exponent(p, J))
             rr = [resample_uniform(p, i, J) for i in range(p.N)]
-            anc, _ = resample(wt, rr)
+            anc, _ = resample(wt, rr, particles(p, J + 1))
             u = move(p, u, anc, J)
     cb = r["cbar_soft"] if p.sep_mode == 1 else r["cbar"]
     best, bsum, ninf = select(cb)

@@ -84,6 +84,9 @@
  *      the log of the product of J_T over them, -M_J * (mean cost).  The
  *      driver of the solve (oracle/__init__.py) applies it; the rollout here
  *      takes the sample count as P->M.
+ *  R21 Particle schedule: iteration J evaluates L_J particles; the systematic
+ *      resampling after it draws L_{J+1} ancestors from the L_J weighted ones
+ *      (orc_resample_to); the perturbation makes L_{J+1} children.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1129,29 +1132,33 @@ uint32_t orc_resample_uniform(const orc_problem *P, int seg, int J)
     return w[0];
 }
 
-int orc_resample(const double *wtilde, int nseg, int L, const uint32_t *r, int32_t *anc)
+/* Systematic resampling of Lout ancestors from Lin weighted particles (reading
+ * R12 with L_out thresholds t_l = floor((l 2^32 + r) Q / (Lout 2^32)),
+ * l < Lout; reading R21).  A segment with Q = 0 gets the evenly spread
+ * ancestors floor(l Lin / Lout) (the identity when Lout = Lin). */
+int orc_resample_to(const double *wtilde, int nseg, int Lin, int Lout, const uint32_t *r, int32_t *anc)
 {
     int ndeg = 0;
-    uint64_t *S = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(L > 0 ? L : 1));
+    uint64_t *S = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(Lin > 0 ? Lin : 1));
     for (int s = 0; s < nseg; s++) {
-        const double *w = wtilde + (int64_t)s * L;
+        const double *w = wtilde + (int64_t)s * Lin;
         uint64_t acc = 0;
-        for (int j = 0; j < L; j++) {
+        for (int j = 0; j < Lin; j++) {
             uint64_t q = 0;
             if (w[j] >= 1.0) q = 1ull << 40;
             else if (w[j] > 0.0) q = (uint64_t)(w[j] * 1099511627776.0);
             acc += q;
             S[j] = acc;
         }
-        int32_t *a = anc + (int64_t)s * L;
+        int32_t *a = anc + (int64_t)s * Lout;
         if (acc == 0) {
-            for (int l = 0; l < L; l++) a[l] = l;
+            for (int l = 0; l < Lout; l++) a[l] = (int32_t)((int64_t)l * Lin / Lout);
             ndeg++;
             continue;
         }
-        const unsigned __int128 den = (unsigned __int128)(uint64_t)L << 32;
+        const unsigned __int128 den = (unsigned __int128)(uint64_t)Lout << 32;
         int j = 0;
-        for (int l = 0; l < L; l++) {
+        for (int l = 0; l < Lout; l++) {
             unsigned __int128 num = (unsigned __int128)((((uint64_t)l) << 32) + r[s]) * acc;
             uint64_t t = (uint64_t)(num / den);
             while (S[j] <= t) j++;
@@ -1162,10 +1169,16 @@ int orc_resample(const double *wtilde, int nseg, int L, const uint32_t *r, int32
     return ndeg;
 }
 
+int orc_resample(const double *wtilde, int nseg, int L, const uint32_t *r, int32_t *anc)
+{
+    return orc_resample_to(wtilde, nseg, L, L, r, anc);
+}
+
 /* ------------------------------------------------------------------ */
 /* perturbation (Algorithm 1) and initialisation (Sec. 3.2)              */
 /* ------------------------------------------------------------------ */
 
+/* L = the number of children (anc[N][L]); ancestors index the parents in u. */
 void orc_move(const orc_problem *P, const double *u, const int32_t *anc, int L, int J,
               double *u_out)
 {

@@ -133,6 +133,7 @@ void orc_lse(const double *cbar, int nseg, int L, double kappa, double *wtilde, 
 /* Systematic resampling on a fixed-point CDF (bit-exact definition). */
 uint32_t orc_resample_uniform(const orc_problem *P, int seg, int J);
 int orc_resample(const double *wtilde, int nseg, int L, const uint32_t *r, int32_t *anc);
+int orc_resample_to(const double *wtilde, int nseg, int Lin, int Lout, const uint32_t *r, int32_t *anc);
 /* Perturbation of the resampled controls. */
 void orc_move(const orc_problem *P, const double *u, const int32_t *anc, int L, int J,
               double *u_out);

@@ -97,6 +97,7 @@ class Problem:
     wind_stream: int = 3                         # 8: held-out evaluation wind samples
     wind_mode: int = 0                           # 1: a field per (particle, sample), 2x2x2 grid
     sample_mode: int = 0                         # 1: iteration J draws min(kappa_J, M) samples
+    L_sched: Optional[tuple] = None              # particles per iteration (J_max entries, <= L)
     aircraft: Optional[np.ndarray] = None        # AIRCRAFT_DTYPE[N]
 
     def copy(self, **kw) -> "Problem":
@@ -301,6 +302,19 @@ CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
 
 def make_config(k: int, **kw):
     return CONFIGS[k](**kw)
+
+
+def particle_schedule(L: int, J_max: int, final_frac: float, multiple: int = 32) -> tuple:
+    """A decreasing particle count: geometric from L at J = 0 to final_frac * L
+    at J = J_max - 1, each rounded down to a multiple of `multiple` (at least
+    one multiple), never increasing."""
+    out, prev = [], L
+    for J in range(J_max):
+        x = L * final_frac ** (J / max(J_max - 1, 1))
+        n = max(multiple, int(x) // multiple * multiple) if J else L
+        prev = min(prev, n)
+        out.append(prev)
+    return tuple(out)
 
 
 def shrink(p: Problem, *, L=None, M=None, H=None, J_max=None, grid=None) -> Problem:
