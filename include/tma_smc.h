@@ -104,6 +104,12 @@ typedef struct {
                                  product of J_T over those draws (Sec. 3.6): l = -M_J * cbar.
                                  tma_rollout_cost, tma_rollout_grad and the moves of iteration J
                                  use M_J samples in mode 1. */
+    const int64_t *L_sched;   /* NULL: every iteration evaluates L particles.  Otherwise host
+                                 [J_max], 1 <= L_sched[J] <= L: iteration J evaluates L_sched[J]
+                                 particles and the resampling after it draws L_sched[J+1]
+                                 ancestors (tma_resample_to) -- the varying particle count the
+                                 paper proposes (Sec. 9).  Copied by tma_create; single solvers
+                                 only (tma_batch_create rejects it). */
 } tma_problem;
 
 typedef struct {
@@ -180,6 +186,14 @@ tma_status tma_live_steps(tma_solver *s, uint64_t *h_live, tma_stream_t stream);
  * Ancestors must lie in [0, L); an out-of-range ancestor is replaced by l. */
 tma_status tma_move(tma_solver *s, const float *d_u, const int32_t *d_anc, int64_t L, int32_t J,
                     float *d_u_out, tma_stream_t stream);
+
+/* The perturbation with another number of parents (varying particle count,
+ * Sec. 9): L children d_u_out[L][N][S][3] from the L_in parents d_u[L_in],
+ * d_anc[N][L] in [0, L_in) (tma_resample_to's output); an out-of-range
+ * ancestor is replaced by min(l, L_in - 1).  L, L_in <= the solver's L;
+ * tma_move is this call with L_in = L. */
+tma_status tma_move_to(tma_solver *s, const float *d_u, int64_t L_in, const int32_t *d_anc, int64_t L,
+                       int32_t J, float *d_u_out, tma_stream_t stream);
 
 /* Uniform initial controls (Sec. 3.2) from random stream 4: d_u[L][N][S][3]. */
 tma_status tma_init_controls(tma_solver *s, float *d_u, int64_t L, tma_stream_t stream);
@@ -388,6 +402,18 @@ size_t tma_resample_workspace(int32_t nseg, int64_t L);
 tma_status tma_resample(const double *d_wtilde, int32_t nseg, int64_t L, uint64_t seed,
                         uint32_t scenario_id, uint32_t J, uint32_t mpc_step, int32_t *d_anc,
                         void *d_work, size_t work_bytes, tma_stream_t stream);
+
+/* Systematic resampling to another particle count (the varying particle count
+ * the paper proposes as a speed-up, Sec. 9): L_out ancestors per segment from
+ * the L weighted particles, t_l = floor((l 2^32 + r) Q / (L_out 2^32)) for
+ * l < L_out, d_anc[s][l] = min{j : S_j > t_l} in [0, L); d_anc is
+ * [nseg][L_out].  A segment with Q = 0 gets ancestors floor(l L / L_out) and
+ * the call returns TMA_WARN_DEGENERATE.  L and L_out are both zero or both in
+ * [1, TMA_MAX_PARTICLES].  Uniform r, weights and workspace as tma_resample
+ * (workspace sized by L); tma_resample is this call with L_out = L. */
+tma_status tma_resample_to(const double *d_wtilde, int32_t nseg, int64_t L, int64_t L_out,
+                           uint64_t seed, uint32_t scenario_id, uint32_t J, uint32_t mpc_step,
+                           int32_t *d_anc, void *d_work, size_t work_bytes, tma_stream_t stream);
 
 /* Final selection (Sec. 3.8): over particles l < L, the fewest aircraft with
  * infinite cost, then the smallest sum_i (double)cbar[i][l] summed in order

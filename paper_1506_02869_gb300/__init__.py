@@ -38,6 +38,7 @@ EXPORTS = [
     "tma_batch_mpc", "tma_batch_results", "tma_batch_latency", "tma_batch_live_steps",
     "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
     "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
+    "tma_resample_to", "tma_move_to",
 ]
 
 
@@ -65,6 +66,7 @@ class TmaProblem(C.Structure):
         ("popdense", C.POINTER(C.c_double)), ("P_runway", C.c_double), ("P_beta", C.c_double),
         ("P_chi", C.c_double), ("P_vs", C.c_double), ("beta_f", C.c_double),
         ("wind_mode", C.c_int32), ("sample_mode", C.c_int32),
+        ("L_sched", C.POINTER(C.c_int64)),
     ]
 
 
@@ -118,6 +120,7 @@ def lib():
                 "tma_sample_costs": ([vp, vp, i64, C.c_int, st], C.c_int),
                 "tma_live_steps": ([vp, P(u64), st], C.c_int),
                 "tma_move": ([vp, vp, vp, i64, i32, vp, st], C.c_int),
+                "tma_move_to": ([vp, vp, i64, vp, i64, i32, vp, st], C.c_int),
                 "tma_init_controls": ([vp, vp, i64, st], C.c_int),
                 "tma_solve": ([vp, vp, P(d), st], C.c_int),
                 "tma_solve_host": ([vp, P(TmaState), u32, vp, P(d), st], C.c_int),
@@ -127,6 +130,7 @@ def lib():
                 "tma_lse": ([vp, i32, i64, d, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_resample_workspace": ([i32, i64], sz),
                 "tma_resample": ([vp, i32, i64, u64, u32, u32, u32, vp, vp, sz, st], C.c_int),
+                "tma_resample_to": ([vp, i32, i64, i64, u64, u32, u32, u32, vp, vp, sz, st], C.c_int),
                 "tma_select_workspace": ([i64], sz),
                 "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_profile_enable": ([vp, C.c_int], C.c_int),
@@ -232,6 +236,11 @@ def problem_struct(p):
         s.pop_lo[:] = [float(v) for v in _get(p, "pop_lo")]
         s.pop_hi[:] = [float(v) for v in _get(p, "pop_hi")]
         s.popdense = pd.ctypes.data_as(C.POINTER(C.c_double))
+    ls = _get(p, "L_sched", None)
+    if ls is not None:
+        ls = np.ascontiguousarray(ls, np.int64)
+        keep.append(ls)
+        s.L_sched = ls.ctypes.data_as(C.POINTER(C.c_int64))
     ac = _get(p, "aircraft")
     arr = (TmaAircraft * s.N)()
     for i in range(s.N):
@@ -305,6 +314,12 @@ def tma_live_steps(h, stream=None):
 def tma_move(h, u, anc, J, u_out, stream=None):
     _check(lib().tma_move(h, _dptr(u), _dptr(anc), u.shape[0], int(J), _dptr(u_out),
                           _stream(stream)), "tma_move")
+
+
+def tma_move_to(h, u, anc, J, u_out, stream=None):
+    """u: parents [L_in][N][S][3], anc: int32 [N][L] -> u_out: children [L][N][S][3]."""
+    _check(lib().tma_move_to(h, _dptr(u), u.shape[0], _dptr(anc), anc.shape[1], int(J), _dptr(u_out),
+                             _stream(stream)), "tma_move_to")
 
 
 def tma_init_controls(h, u, stream=None):
@@ -566,6 +581,20 @@ def tma_resample(wtilde, seed, scenario_id, J, mpc_step, anc, work=None, stream=
                   "tma_resample", allow=(TMA_OK, TMA_WARN_DEGENERATE))
 
 
+def tma_resample_to(wtilde, seed, scenario_id, J, mpc_step, anc, work=None, stream=None):
+    """wtilde: cuda float64 [nseg][L] -> anc int32 [nseg][L_out] (L_out = anc.shape[1]);
+    returns the status."""
+    nseg, L = wtilde.shape
+    need = lib().tma_resample_workspace(nseg, L)
+    if work is None:
+        work = _workspace(need, wtilde.device)
+    return _check(lib().tma_resample_to(_dptr(wtilde), nseg, L, anc.shape[1],
+                                        int(seed) & 0xFFFFFFFFFFFFFFFF, int(scenario_id), int(J),
+                                        int(mpc_step), _dptr(anc), _dptr(work), work.numel(),
+                                        _stream(stream)),
+                  "tma_resample_to", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+
+
 def tma_resample_noalloc(wtilde, seed, scenario_id, J, mpc_step, anc, stream=None):
     """tma_resample without a workspace (library-owned fixed scratch; see the
     header for its size limit and the serialisation rule); returns the status."""
@@ -596,6 +625,9 @@ class Solver:
         self.problem = problem
         self.N, self.S, self.L, self.M, self.H = (int(_get(problem, n)) for n in ("N", "S", "L", "M", "H"))
         self.J_max = int(_get(problem, "J_max"))
+        ls = _get(problem, "L_sched", None)
+        # particles after the last iteration (the set the selection chooses from)
+        self.L_final = int(ls[self.J_max - 1]) if ls is not None else self.L
         self.sep_mode = int(_get(problem, "sep_mode"))
         self.grid = tuple(int(v) for v in _get(problem, "grid"))
         self.device = torch.device(device if device is not None else "cuda")
@@ -660,7 +692,7 @@ class Solver:
 
     def particles(self, L=None):
         torch = _torch()
-        L = self.L if L is None else L
+        L = self.L_final if L is None else L
         out = torch.empty((L, self.N, self.S, 3), dtype=torch.float32, device=self.device)
         return tma_get_particles(self.h, out)
 

@@ -166,6 +166,9 @@ static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
     if (p->grid[2] > TMA_MAX_GRID_Z) return TMA_ERR_INVALID_ARG;
     if (p->wind_mode != 0 && p->wind_mode != 1) return TMA_ERR_INVALID_ARG;
     if (p->sample_mode != 0 && p->sample_mode != 1) return TMA_ERR_INVALID_ARG;
+    if (p->L_sched)
+        for (int J = 0; J < p->J_max; ++J)
+            if (p->L_sched[J] < 1 || p->L_sched[J] > p->L) return TMA_ERR_INVALID_ARG;
     if (p->wind_mode == 1 && (p->grid[0] != 2 || p->grid[1] != 2 || p->grid[2] != 2))
         return TMA_ERR_INVALID_ARG;
     if ((long long)p->grid[0] * p->grid[1] > 16384) return TMA_ERR_INVALID_ARG;
@@ -389,6 +392,12 @@ static double exponent_of(const tma_problem &p, int J)
     return p.sample_mode == 1 ? (double)samples_of(p, J) : (double)kappa_of(J);
 }
 
+// Particles evaluated in iteration J (the particle schedule, else L).
+static int64_t particles_of(const tma_solver *s, int J)
+{
+    return s->L_sched.empty() ? s->prob.L : s->L_sched[(size_t)J];
+}
+
 // The problem as the kernels of iteration J see it (M = that iteration's samples).
 static ProblemC problem_at(const tma_solver *s, int J)
 {
@@ -462,6 +471,8 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
                                     prob->popdense + (size_t)prob->pop_n[0] * prob->pop_n[1]);
         }
         s->prob.popdense = nullptr;
+        if (prob->L_sched) s->L_sched.assign(prob->L_sched, prob->L_sched + prob->J_max);
+        s->prob.L_sched = nullptr;
         s->mpc_step = prob->mpc_step;
         cudaGetDevice(&s->device);
         const tma_problem &p = s->prob;
@@ -835,12 +846,19 @@ tma_status tma_live_steps(tma_solver *s, uint64_t *h_live, tma_stream_t stream)
 tma_status tma_move(tma_solver *s, const float *d_u, const int32_t *d_anc, int64_t L, int32_t J,
                     float *d_u_out, tma_stream_t stream)
 {
-    if (!s || !d_u || !d_anc || !d_u_out || d_u == d_u_out || L < 0 || L > s->prob.L || J < 0 ||
-        J > 0xFFFF)
+    return tma_move_to(s, d_u, L, d_anc, L, J, d_u_out, stream);
+}
+
+tma_status tma_move_to(tma_solver *s, const float *d_u, int64_t L_in, const int32_t *d_anc, int64_t L,
+                       int32_t J, float *d_u_out, tma_stream_t stream)
+{
+    if (!s || !d_u || !d_anc || !d_u_out || d_u == d_u_out || L < 0 || L > s->prob.L || L_in < 0 ||
+        L_in > s->prob.L || (L > 0 && L_in == 0) || J < 0 || J > 0xFFFF)
         return TMA_ERR_INVALID_ARG;
     float lo[3], hi[3], sg[3];
     ctrl_f(s->prob, lo, hi, sg);
-    TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, sg, d_u, d_anc, L, J, d_u_out, (cudaStream_t)stream));
+    TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, sg, d_u, d_anc, L, L_in, J, d_u_out,
+                         (cudaStream_t)stream));
     return TMA_OK;
 }
 
@@ -1130,37 +1148,37 @@ extern "C" tma_status tma_mh_stats(tma_solver *s, uint32_t *h_accepts, double *h
 
 // One accepted move of all particles at iteration J: u_cur holds the resampled
 // particles on entry and the moved ones on exit.
-static tma_status mh_move(tma_solver *s, float *u_cur, int J, cudaStream_t st)
+static tma_status mh_move(tma_solver *s, float *u_cur, int J, int64_t L, cudaStream_t st)
 {
     const tma_problem &p = s->prob;
     const int kind = s->move_kind;
     const float kappa = (float)exponent_of(p, J);
     const MhParams h = mh_params(s, kind);
     if (kind == TMA_MOVE_MALA) {
-        tma_status r = grad_into(s, u_cur, p.L, J, s->d_cost0, s->d_grad0, s->d_cbar0, st);
+        tma_status r = grad_into(s, u_cur, L, J, s->d_cost0, s->d_grad0, s->d_cbar0, st);
         if (r != TMA_OK) return r;
     } else {
-        tma_status r = rollout_into(s, u_cur, p.L, J, s->d_cbar, s->d_cbar0, st, false);
+        tma_status r = rollout_into(s, u_cur, L, J, s->d_cbar, s->d_cbar0, st, false);
         if (r != TMA_OK) return r;
     }
     {
         StageTimer t(s, 9, st);
-        TMA_CUDA(launch_mh_propose(h, s->d_dyn, u_cur, s->d_grad0, p.L, J, kappa, s->d_eps,
+        TMA_CUDA(launch_mh_propose(h, s->d_dyn, u_cur, s->d_grad0, L, J, kappa, s->d_eps,
                                    s->d_u_prop, s->d_inbox, st));
     }
     if (kind == TMA_MOVE_MALA) {
-        tma_status r = grad_into(s, s->d_u_prop, p.L, J, s->d_cost1, s->d_grad1, s->d_cbar1, st);
+        tma_status r = grad_into(s, s->d_u_prop, L, J, s->d_cost1, s->d_grad1, s->d_cbar1, st);
         if (r != TMA_OK) return r;
     } else {
-        tma_status r = rollout_into(s, s->d_u_prop, p.L, J, s->d_cbar, s->d_cbar1, st, false);
+        tma_status r = rollout_into(s, s->d_u_prop, L, J, s->d_cbar, s->d_cbar1, st, false);
         if (r != TMA_OK) return r;
     }
     {
         StageTimer t(s, 9, st);
         TMA_CUDA(launch_mh_accept(h, s->d_dyn, u_cur, s->d_u_prop, s->d_cbar0, s->d_cbar1,
-                                  s->d_grad0, s->d_grad1, s->d_inbox, p.L, J, kappa, s->d_eps,
+                                  s->d_grad0, s->d_grad1, s->d_inbox, L, J, kappa, s->d_eps,
                                   u_cur, nullptr, nullptr, s->d_nacc, st));
-        TMA_CUDA(launch_mh_adapt(s->d_eps, s->d_nacc, s->d_acc_hist, s->d_eps_hist, J, p.L, st));
+        TMA_CUDA(launch_mh_adapt(s->d_eps, s->d_nacc, s->d_acc_hist, s->d_eps_hist, J, L, st));
     }
     return TMA_OK;
 }
@@ -1180,24 +1198,27 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
     }
     {
         StageTimer t(s, 1, st);
-        TMA_CUDA(launch_init_controls(s->P, s->d_dyn, lo, hi, s->d_u[0], p.L, st));
+        TMA_CUDA(launch_init_controls(s->P, s->d_dyn, lo, hi, s->d_u[0], particles_of(s, 0), st));
     }
     int cur = 0;
     const bool use_soft = p.sep_mode == 1;
     float *cb = use_soft ? s->d_cbar_soft : s->d_cbar;
     for (int J = 0; J < p.J_max; ++J) {
-        r = rollout_into(s, s->d_u[cur], p.L, J, s->d_cbar, p.sep_mode != 0 ? s->d_cbar_soft : nullptr,
+        // every stage of iteration J sees its particles packed: [L_J] or [N][L_J]
+        const int64_t Lj = particles_of(s, J);
+        r = rollout_into(s, s->d_u[cur], Lj, J, s->d_cbar, p.sep_mode != 0 ? s->d_cbar_soft : nullptr,
                          st, false);
         if (r != TMA_OK) return r;
         if (J < p.J_max - 1) {
+            const int64_t Ln = particles_of(s, J + 1);
             {
                 StageTimer t(s, 4, st);
-                TMA_CUDA(launch_lse(cb, p.N, p.L, exponent_of(p, J), s->d_wtilde, nullptr, nullptr,
+                TMA_CUDA(launch_lse(cb, p.N, Lj, exponent_of(p, J), s->d_wtilde, nullptr, nullptr,
                                     s->d_work, st));
             }
             {
                 StageTimer t(s, 5, st);
-                TMA_CUDA(launch_resample(s->d_wtilde, p.N, p.L, s->P.key0, s->P.key1, (uint32_t)J,
+                TMA_CUDA(launch_resample(s->d_wtilde, p.N, Lj, Ln, s->P.key0, s->P.key1, (uint32_t)J,
                                          dyn_mpc(s), 0u, s->d_anc, s->d_work, s->d_flags, st));
             }
             {
@@ -1205,11 +1226,11 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
                 // the accepted moves start from the resampled particles themselves
                 const float zero[3] = {0.0f, 0.0f, 0.0f};
                 TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, s->move_kind == TMA_MOVE_PAPER ? sg : zero,
-                                     s->d_u[cur], s->d_anc, p.L, J, s->d_u[cur ^ 1], st));
+                                     s->d_u[cur], s->d_anc, Ln, Lj, J, s->d_u[cur ^ 1], st));
             }
             cur ^= 1;
             if (s->move_kind != TMA_MOVE_PAPER) {
-                r = mh_move(s, s->d_u[cur], J, st);
+                r = mh_move(s, s->d_u[cur], J, Ln, st);
                 if (r != TMA_OK) return r;
             }
         }
@@ -1217,7 +1238,8 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
     s->cur_u = cur;
     {
         StageTimer t(s, 7, st);
-        TMA_CUDA(launch_select(cb, p.N, p.L, s->d_best, s->d_best_sum, s->d_ninf, s->d_work, st));
+        const int64_t Lf = particles_of(s, p.J_max - 1);
+        TMA_CUDA(launch_select(cb, p.N, Lf, s->d_best, s->d_best_sum, s->d_ninf, s->d_work, st));
         TMA_CUDA(launch_gather_best(s->d_u[cur], s->d_best, p.N * p.S * 3, s->d_best_u, st,
                                     s->d_flags, s->d_ninf, s->d_err));
     }
@@ -1268,7 +1290,7 @@ tma_status tma_solve_host(tma_solver *s, const tma_state *h_x0, uint32_t mpc_ste
 
 tma_status tma_get_particles(tma_solver *s, float *d_u_out, int64_t L, tma_stream_t stream)
 {
-    if (!s || !d_u_out || L < 0 || L > s->prob.L) return TMA_ERR_INVALID_ARG;
+    if (!s || !d_u_out || L < 0 || L > particles_of(s, s->prob.J_max - 1)) return TMA_ERR_INVALID_ARG;
     const size_t bytes = (size_t)L * s->prob.N * s->prob.S * 3 * sizeof(float);
     TMA_CUDA(cudaMemcpyAsync(d_u_out, s->d_u[s->cur_u], bytes, cudaMemcpyDeviceToDevice,
                              (cudaStream_t)stream));
@@ -1316,7 +1338,16 @@ tma_status tma_resample(const double *d_wtilde, int32_t nseg, int64_t L, uint64_
                         uint32_t scenario_id, uint32_t J, uint32_t mpc_step, int32_t *d_anc,
                         void *d_work, size_t work_bytes, tma_stream_t stream)
 {
-    if (nseg < 0 || L < 0 || L > TMA_MAX_PARTICLES || J > 0xFFFF || mpc_step > 0xFFFF)
+    return tma_resample_to(d_wtilde, nseg, L, L, seed, scenario_id, J, mpc_step, d_anc, d_work,
+                           work_bytes, stream);
+}
+
+tma_status tma_resample_to(const double *d_wtilde, int32_t nseg, int64_t L, int64_t L_out,
+                           uint64_t seed, uint32_t scenario_id, uint32_t J, uint32_t mpc_step,
+                           int32_t *d_anc, void *d_work, size_t work_bytes, tma_stream_t stream)
+{
+    if (nseg < 0 || L < 0 || L > TMA_MAX_PARTICLES || L_out < 0 || L_out > TMA_MAX_PARTICLES ||
+        J > 0xFFFF || mpc_step > 0xFFFF || (L == 0) != (L_out == 0))
         return TMA_ERR_INVALID_ARG;
     if (nseg == 0 || L == 0) return TMA_OK;
     if (!d_wtilde || !d_anc || !d_work || work_bytes < tma_resample_workspace(nseg, L))
@@ -1329,8 +1360,8 @@ tma_status tma_resample(const double *d_wtilde, int32_t nseg, int64_t L, uint64_
     unsigned int *flags = reinterpret_cast<unsigned int *>(
         (reinterpret_cast<uintptr_t>(base + rw) + 3) & ~uintptr_t(3));
     TMA_CUDA(cudaMemsetAsync(flags, 0, 4, st));
-    TMA_CUDA(launch_resample(d_wtilde, nseg, L, (uint32_t)key, (uint32_t)(key >> 32), J, nullptr,
-                             mpc_step, d_anc, d_work, flags, st));
+    TMA_CUDA(launch_resample(d_wtilde, nseg, L, L_out, (uint32_t)key, (uint32_t)(key >> 32), J,
+                             nullptr, mpc_step, d_anc, d_work, flags, st));
     unsigned int h = 0;
     TMA_CUDA(cudaMemcpyAsync(&h, flags, 4, cudaMemcpyDeviceToHost, st));
     TMA_CUDA(cudaStreamSynchronize(st));
@@ -1514,7 +1545,7 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
         if (J < b->J_max - 1) {
             TMA_CUDA(launch_lse(cb, (int)b->nseg, L, exponent_of(b->probs[0], J), b->d_wtilde, nullptr,
                                 nullptr, b->d_work, st));
-            TMA_CUDA(launch_resample(b->d_wtilde, (int)b->nseg, L, 0u, 0u, (uint32_t)J, nullptr, 0u,
+            TMA_CUDA(launch_resample(b->d_wtilde, (int)b->nseg, L, L, 0u, 0u, (uint32_t)J, nullptr, 0u,
                                      b->d_anc, b->d_work, b->d_flags, st, b->d_segkeys, b->d_dyns));
             TMA_CUDA(launch_batch_move(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, L, b->S,
                                        b->d_u[cur], b->d_anc, J, b->d_u[cur ^ 1], st));
@@ -1547,6 +1578,7 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
         tma_status v = validate(&probs[s], aircraft[s]);
         if (v != TMA_OK) return v;
         if (!same_shape(probs[0], probs[s])) return TMA_ERR_INVALID_ARG;
+        if (probs[s].L_sched) return TMA_ERR_UNSUPPORTED;    // fixed particle count per batch
     }
     tma_batch *b = nullptr;
     try {

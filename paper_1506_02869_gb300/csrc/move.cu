@@ -24,14 +24,16 @@ template <bool kVec>
 __global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState *__restrict__ dyn,
                                                    const float *__restrict__ u,
                                                    const int32_t *__restrict__ anc, long long L,
-                                                   int J, float *__restrict__ u_out)
+                                                   long long Lin, int J, float *__restrict__ u_out)
 {
+    // L children from Lin parents
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L * C.N) return;
     const long long l = t / C.N;
     const int i = (int)(t - l * C.N);
     int a = __ldg(anc + (size_t)i * L + l);
-    if ((unsigned long long)a >= (unsigned long long)L) a = (int)l;   // out-of-range ancestor: keep own record
+    if ((unsigned long long)a >= (unsigned long long)Lin)   // out-of-range ancestor: own index (clamped)
+        a = (int)(l < Lin ? l : Lin - 1);
     const uint32_t mpc = dyn ? dyn->mpc_step : 0u;
     const float *src = u + ((size_t)a * C.N + i) * C.nc;
     float *dst = u_out + ((size_t)l * C.N + i) * C.nc;
@@ -106,14 +108,14 @@ MoveC make_move(const ProblemC &P, const float lo[3], const float hi[3], const f
 
 cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                         const float ctrl_hi[3], const float sigma[3], const float *u,
-                        const int32_t *anc, int64_t L, int J, float *u_out, cudaStream_t st)
+                        const int32_t *anc, int64_t L, int64_t Lin, int J, float *u_out, cudaStream_t st)
 {
-    if (L <= 0) return cudaSuccess;
+    if (L <= 0 || Lin <= 0) return cudaSuccess;
     const MoveC C = make_move(P, ctrl_lo, ctrl_hi, sigma);
     const long long n = (long long)L * P.N;
     const unsigned grid = (unsigned)((n + 255) / 256);
-    if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, J, u_out);
-    else move_kernel<false><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, J, u_out);
+    if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
+    else move_kernel<false><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
     count_launch();
     return cudaGetLastError();
 }

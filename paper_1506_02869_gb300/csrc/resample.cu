@@ -12,12 +12,13 @@
 //   Resample: (1) chunk sums of q = floor(wtilde 2^40) (uint64, exact);
 //             (2) every block forms its chunk's inclusive prefix S_j in shared
 //             memory, finds the range of particles l whose threshold
-//             t_l = floor((l 2^32 + r) Q / (L 2^32)) falls in the chunk, and
+//             t_l = floor((l 2^32 + r) Q / (Lout 2^32)) falls in the chunk, and
 //             assigns a_l = min{j : S_j > t_l} by binary search.  Because
 //             S_j > floor(y) <=> S_j > y for integer S_j, both searches compare
-//             128-bit products S_j * L 2^32 against (l 2^32 + r) * Q and need no
-//             division.  Integer arithmetic makes the result independent of the
-//             summation order.
+//             128-bit products S_j * Lout 2^32 against (l 2^32 + r) * Q and need
+//             no division.  Integer arithmetic makes the result independent of
+//             the summation order.  Lout ancestors are drawn from the Lin weighted
+//             particles of the segment (Lout = Lin for a fixed particle count).
 #include <cfloat>
 #include <mutex>
 
@@ -202,7 +203,7 @@ __device__ long long count_below(unsigned long long X, unsigned long long Q, uns
 }
 
 __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict__ wtilde, long long L,
-                                                       int nchunk,
+                                                       long long Lout, int nchunk,
                                                        const unsigned long long *__restrict__ cq,
                                                        uint32_t key0, uint32_t key1, uint32_t J,
                                                        const uint32_t *__restrict__ d_mpc,
@@ -230,11 +231,13 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
     }
     before = block_reduce(before, AddU64(), sh, 0ull);
     total = block_reduce(total, AddU64(), sh, 0ull);
-    int32_t *a = anc + (size_t)s * L;
+    int32_t *a = anc + (size_t)s * Lout;
 
     if (total == 0) {
-        // degenerate segment: identity ancestors
-        for (int j = threadIdx.x; j < len; j += kThreads) a[base + j] = (int32_t)(base + j);
+        // degenerate segment: ancestors floor(l L / Lout) spread evenly (the
+        // identity when Lout = L); this chunk writes the l that map into it
+        const long long l0 = (base * Lout + L - 1) / L, l1 = ((base + len) * Lout + L - 1) / L;
+        for (long long l = l0 + threadIdx.x; l < l1; l += kThreads) a[l] = (int32_t)(l * L / Lout);
         if (c == 0 && threadIdx.x == 0 && flags) atomicOr(flags, 1u);
         return;
     }
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
     for (int w = 0; w < wid; ++w) woff += wtot[w];
     const unsigned long long add = before + woff + (incl - run);
     // the searches compare thresholds against S_j * D: form the products once
-    const unsigned long long D = (unsigned long long)L << 32;
+    const unsigned long long D = (unsigned long long)Lout << 32;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const unsigned long long S = qv[j] + add;
@@ -298,8 +301,8 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
         r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
     }
-    if (threadIdx.x == 0) range[0] = count_below(before, total, D, r, L);
-    if (threadIdx.x == 32) range[1] = count_below(s_last, total, D, r, L);
+    if (threadIdx.x == 0) range[0] = count_below(before, total, D, r, Lout);
+    if (threadIdx.x == 32) range[1] = count_below(s_last, total, D, r, Lout);
     __syncthreads();
     const long long lo = range[0], hi = range[1];
     for (long long l = lo + threadIdx.x; l < hi; l += kThreads) {
@@ -385,19 +388,19 @@ cudaError_t scratch_address(void **out)
 }
 }  // namespace
 
-cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t key0,
+cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, int64_t Lout, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
                             int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st,
                             const SegKey *seg_keys, const DynState *dyns)
 {
-    if (nseg <= 0 || L <= 0) return cudaSuccess;
+    if (nseg <= 0 || L <= 0 || Lout <= 0) return cudaSuccess;
     const int nc = n_chunks(L);
     auto *cq = reinterpret_cast<unsigned long long *>(
         (reinterpret_cast<uintptr_t>(work) + 15) & ~uintptr_t(15));
     dim3 grid(nc, nseg);
     res_chunk_sum<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq);
-    res_expand<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq, key0, key1, J, d_mpc, mpc_host, anc,
-                                          d_flags, seg_keys, dyns);
+    res_expand<<<grid, kThreads, 0, st>>>(wtilde, L, Lout, nc, cq, key0, key1, J, d_mpc, mpc_host,
+                                          anc, d_flags, seg_keys, dyns);
     count_launch(2);
     return cudaGetLastError();
 }
@@ -422,7 +425,7 @@ extern "C" tma_status tma_resample_noalloc(const double *d_wtilde, int32_t nseg,
     if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned int), st)) != cudaSuccess)
         return record_cuda_error(e);
     const uint64_t key = seed + (uint64_t)scenario_id * 0x9E3779B97F4A7C15ull;
-    if ((e = launch_resample(d_wtilde, nseg, L, (uint32_t)key, (uint32_t)(key >> 32), J, nullptr,
+    if ((e = launch_resample(d_wtilde, nseg, L, L, (uint32_t)key, (uint32_t)(key >> 32), J, nullptr,
                              mpc_step, d_anc, scratch, flags, st)) != cudaSuccess)
         return record_cuda_error(e);
     unsigned int h = 0;

@@ -112,7 +112,7 @@ cudaError_t launch_sample_mean(const float *cost_ms, int64_t L, int M, int N, fl
 cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, double *wtilde,
                        double *lmax, double *wsum, void *work, cudaStream_t st);
 size_t lse_workspace(int nseg, int64_t L);
-cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, uint32_t key0,
+cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, int64_t Lout, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
                             int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st,
                             const SegKey *seg_keys = nullptr, const DynState *dyns = nullptr);
@@ -120,7 +120,8 @@ size_t resample_workspace(int nseg, int64_t L);
 
 cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                         const float ctrl_hi[3], const float sigma[3], const float *u,
-                        const int32_t *anc, int64_t L, int J, float *u_out, cudaStream_t st);
+                        const int32_t *anc, int64_t L, int64_t Lin, int J, float *u_out,
+                        cudaStream_t st);
 cudaError_t launch_init_controls(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                                  const float ctrl_hi[3], float *u, int64_t L, cudaStream_t st);
 
@@ -196,6 +197,7 @@ struct tma_solver {
     tma_problem prob;
     std::vector<tma_aircraft> aircraft;
     std::vector<double> popdense_host;
+    std::vector<int64_t> L_sched;   // particles per iteration (empty: L every iteration)
     tma::ProblemC P;
     tma::WindC wind;
     int device;

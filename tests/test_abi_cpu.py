@@ -49,7 +49,7 @@ def test_struct_layout_matches_header(tmp_path):
                                                "wind_sigma", "sep_mode", "sp_beta", "ctrl_lo",
                                                "alpha_dep", "w_noise", "pop_n", "pop_lo",
                                                "popdense", "P_runway", "beta_f", "wind_mode",
-                                               "sample_mode"]),
+                                               "sample_mode", "L_sched"]),
               "tma_aircraft": (pkg.TmaAircraft, ["type", "x0", "theta_F", "m_empty", "Tmax"]),
               "tma_state": (pkg.TmaState, ["x", "m"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(){"]
@@ -88,7 +88,8 @@ def _create(p):
                                     dict(J_max=0), dict(mpc_step=1 << 16), dict(sep_h=0.0),
                                     dict(v_min=300.0), dict(wind_mode=2), dict(wind_mode=-1),
                                     dict(wind_mode=1, grid=(2, 2, 3)), dict(wind_mode=1, grid=(4, 4, 4)),
-                                    dict(sample_mode=2), dict(sample_mode=-1)])
+                                    dict(sample_mode=2), dict(sample_mode=-1),
+                                    dict(L_sched=(1024,) * 9 + (0,)), dict(L_sched=(2048,) + (1024,) * 9)])
 def test_create_rejects_invalid_problems(lib, change):
     p = S.config1().copy(**change)
     if "N" in change and change["N"] > 2:
@@ -110,6 +111,13 @@ def test_stage_calls_reject_invalid_arguments(lib):
     # empty inputs are valid no-ops
     assert L.tma_resample(null, 0, 10, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_OK
     assert L.tma_resample(null, 3, 0, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_OK
+    # resampling to another count: both counts empty or both positive
+    assert L.tma_resample_to(null, 2, 10, 0, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_resample_to(null, 2, 0, 5, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_resample_to(null, 2, 10, -1, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_resample_to(null, 2, 10, 7, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_resample_to(null, 0, 10, 7, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_OK
+    assert L.tma_move_to(null, null, 4, null, 4, 0, null, null) == pkg.TMA_ERR_INVALID_ARG
 
 
 def test_workspace_sizes(lib):
@@ -146,6 +154,9 @@ def test_batch_create_rejects_invalid_batches(lib):
     assert st == pkg.TMA_ERR_INVALID_ARG and not h.value
     bad_grid = pkg.problem_struct(ps[1].copy(grid=(8, 8, 4)))
     assert create([structs[0], bad_grid])[0] == pkg.TMA_ERR_INVALID_ARG
+    # a particle schedule is for single solvers only
+    sched = pkg.problem_struct(ps[1].copy(L_sched=(64, 32)))
+    assert create([structs[0], sched])[0] == pkg.TMA_ERR_UNSUPPORTED
     assert lib.tma_batch_mpc(None, 1, 1, None) == pkg.TMA_ERR_INVALID_ARG
     assert lib.tma_plant_step(None, None, None) == pkg.TMA_ERR_INVALID_ARG
 
