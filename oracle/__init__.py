@@ -62,11 +62,12 @@ class OrcProblem(C.Structure):
         ("P_runway", C.c_double), ("P_beta", C.c_double), ("P_chi", C.c_double),
         ("P_vs", C.c_double), ("beta_f", C.c_double), ("wind_stream", C.c_uint32),
         ("wind_mode", C.c_int), ("wind_chol", C.POINTER(C.c_double)),
+        ("rolling", C.c_int), ("finished", C.c_uint32),
     ]
 
 
 class OrcAircraft(C.Structure):
-    _fields_ = [("type", C.c_int32), ("pad_", C.c_int32)] + [
+    _fields_ = [("type", C.c_int32), ("t_enter", C.c_int32)] + [
         (n, C.c_double) for n in ("x", "y", "z", "v", "chi", "m", "theta_F", "Z", "v_D",
                                   "m_empty", "S", "CD0", "CD2", "Cf1", "Cf2", "Tmin", "Tmax")]
 
@@ -98,6 +99,8 @@ def lib():
                                            P(d)]
             _lib.orc_mh_accept.restype = None
             _lib.orc_plant_step.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), P(d), P(d), P(d)]
+            _lib.orc_plant_finished.argtypes = [P(OrcProblem), P(OrcAircraft), P(d)]
+            _lib.orc_plant_finished.restype = u32
             _lib.orc_particle_wind.argtypes = [P(OrcProblem), i64, i32, P(d)]
             _lib.orc_particle_wind.restype = None
             _lib.orc_kappa.argtypes = [i32]
@@ -137,6 +140,8 @@ class _Marshalled:
             setattr(s, n, float(getattr(p, n)))
         s.sep_mode = p.sep_mode
         s.wind_stream = int(getattr(p, "wind_stream", 3))
+        s.rolling = int(getattr(p, "rolling", 0))
+        s.finished = int(getattr(p, "finished", 0)) & 0xFFFFFFFF
         s.wind_mode = int(getattr(p, "wind_mode", 0))
         if s.wind_mode == 1:
             # Qhat: lower Cholesky factor of R_hat on the 2x2x2 corner grid (a library step)
@@ -160,6 +165,7 @@ class _Marshalled:
         for i in range(p.N):
             r = ac[i]
             self.ac[i].type = int(r["type"])
+            self.ac[i].t_enter = int(r["t_enter"]) if "t_enter" in r.dtype.names else 0
             for n in ("x", "y", "z", "v", "chi", "m", "theta_F", "Z", "v_D", "m_empty", "S",
                       "CD0", "CD2", "Cf1", "Cf2", "Tmin", "Tmax"):
                 setattr(self.ac[i], n, float(r[n]))
@@ -420,10 +426,20 @@ def mh_accept(p, u, up, cbar, cbarp, g, gp, inbox, J, kappa, eps, kind):
     return out, acc.astype(bool), la
 
 
+def plant_finished(p, x):
+    """Rolling window (reading R22): the finished mask after a plant step that
+    produced the states x[N][6]: p.finished plus every active arrival inside
+    the landing sector."""
+    xi = np.ascontiguousarray(x, np.float64).reshape(p.N, 6)
+    mm = _Marshalled(p)
+    return int(lib().orc_plant_finished(mm.ps, mm.ac, _ptr(xi, C.c_double)))
+
+
 def plant_step(p, x, W0, u0):
     """One step of the true system (Sec. 2, Fig. 1): states x[N][6] (x, y, z,
     v, chi, m), wind field W0[P][2] of sample 0 at step 0, first-segment
-    controls u0[N][3]; returns the new states."""
+    controls u0[N][3]; returns the new states.  With a rolling window, aircraft
+    that have not entered (t_enter > mpc_step) or have finished keep theirs."""
     xi = np.ascontiguousarray(x, np.float64).reshape(p.N, 6)
     W = np.ascontiguousarray(W0, np.float64).reshape(p.n_grid, 2)
     uu = np.ascontiguousarray(u0, np.float64).reshape(p.N, 3)

@@ -84,6 +84,15 @@
  *      the log of the product of J_T over them, -M_J * (mean cost).  The
  *      driver of the solve (oracle/__init__.py) applies it; the rollout here
  *      takes the sample count as P->M.
+ *  R22 Rolling window (the paper's rolling-window section): aircraft i enters
+ *      at MPC step t_enter and, at MPC step t, flies the horizon steps
+ *      k >= k_in = max(0, t_enter - t) from its entry state; its objective
+ *      is the mean of its per-step terms over its H - k_in active steps
+ *      (the fuel bound and the departure altitude bounds over those steps).
+ *      An aircraft with k_in >= H, or one that has finished, is not in the
+ *      problem: cost 0 (J_T = 1), no simulation, no separation checks.  The
+ *      plant moves only active aircraft and marks an arrival finished once
+ *      it is in the landing sector of Eq. (TO_init).
  *  R21 Particle schedule: iteration J evaluates L_J particles; the systematic
  *      resampling after it draws L_{J+1} ancestors from the L_J weighted ones
  *      (orc_resample_to); the perturbation makes L_{J+1} children.
@@ -332,6 +341,18 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
         Wm = own;
     }
 
+    /* rolling window (reading R22): first active step, and whether the
+     * aircraft is in the problem at all during this horizon */
+    int kin[256], out[256];
+    for (int i = 0; i < N; i++) {
+        kin[i] = 0;
+        out[i] = 0;
+        if (P->rolling) {
+            const int64_t d = (int64_t)A[i].t_enter - (int64_t)P->mpc_step;
+            kin[i] = d > 0 ? (d < H ? (int)d : H) : 0;
+            out[i] = ((P->finished >> i) & 1u) || kin[i] >= H;
+        }
+    }
     for (int i = 0; i < N; i++) {
         acst *s = &st[i];
         memset(s, 0, sizeof(*s));
@@ -347,7 +368,7 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
         for (int i = 0; i < N; i++) {
             acst *s = &st[i];
             const orc_aircraft *a = &A[i];
-            if (s->dead || s->landed) continue;
+            if (s->dead || s->landed || out[i] || k < kin[i]) continue;
             nlive++;
             const int seg = (int)(((int64_t)k * S) / H);
             const double *uu = ul + ((int64_t)i * S + seg) * 3;
@@ -466,9 +487,9 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
 
         /* binary separation constraints at step k+1, Eq. (avoidance) */
         for (int i = 0; i < N; i++) {
-            if (st[i].dead || st[i].landed) continue;
+            if (st[i].dead || st[i].landed || out[i] || k < kin[i]) continue;
             for (int j = i + 1; j < N; j++) {
-                if (st[j].dead || st[j].landed) continue;
+                if (st[j].dead || st[j].landed || out[j] || k < kin[j]) continue;
                 double dx = st[i].x - st[j].x, dy = st[i].y - st[j].y, dz = st[i].z - st[j].z;
                 double dh2 = dx * dx + dy * dy, adz = fabs(dz);
                 conj_t cp;
@@ -495,31 +516,38 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
     for (int i = 0; i < N; i++) {
         const acst *s = &st[i];
         const orc_aircraft *a = &A[i];
+        if (out[i]) {                 /* not in the problem this horizon: J_T = 1 */
+            if (ch) ch[i] = 0.0;
+            if (cs) cs[i] = 0.0;
+            if (mg) mg[i] = s->margin;
+            continue;
+        }
+        const int Ha = H - kin[i];    /* active steps (H without a rolling window) */
         const double eta_max = a->Cf1 * (1.0 + P->v_max / a->Cf2);
-        const double Fmax = H * dt * a->Tmax * eta_max;
+        const double Fmax = Ha * dt * a->Tmax * eta_max;
         const double Jf = 1.0 - s->F / Fmax;
         double Jsum;
         if (a->type == 1) {
             double d0 = fabs(a->Z - a->z), c = P->v_max * sgmax * dt;
             double supB = 0.0, infB = 0.0;
-            for (int k = 1; k <= H; k++) {
+            for (int k = 1; k <= Ha; k++) {
                 supB += d0 + k * c;
                 infB += (d0 - k * c) > 0.0 ? d0 - k * c : 0.0;
             }
-            supB /= H;
-            infB /= H;
-            double J1 = 1.0 - (s->sA / H) / M_PI;
-            double J3 = (supB - s->sB / H) / (supB - infB);
+            supB /= Ha;
+            infB /= Ha;
+            double J1 = 1.0 - (s->sA / Ha) / M_PI;
+            double J3 = (supB - s->sB / Ha) / (supB - infB);
             double Cmax = fmax(P->v_max - a->v_D, a->v_D - P->v_min);
-            double J4 = 1.0 - (s->sC / H) / Cmax;
+            double J4 = 1.0 - (s->sC / Ha) / Cmax;
             Jsum = P->alpha_dep[0] * J1 + P->alpha_dep[1] * Jf + P->alpha_dep[2] * J3 +
                    P->alpha_dep[3] * J4;
         } else {
-            double J1 = 1.0 - (s->sA / H) / M_PI;
-            double J3 = 1.0 - (s->sB / H) / (0.5 * M_PI);
+            double J1 = 1.0 - (s->sA / Ha) / M_PI;
+            double J3 = 1.0 - (s->sB / Ha) / (0.5 * M_PI);
             Jsum = P->alpha_arr[0] * J1 + P->alpha_arr[1] * J3 + P->alpha_arr[2] * Jf;
         }
-        double JT = (1.0 - P->w_noise) * Jsum + P->w_noise * (1.0 - s->sN / H);
+        double JT = (1.0 - P->w_noise) * Jsum + P->w_noise * (1.0 - s->sN / Ha);
         double base = -log(JT > 1e-30 ? JT : 1e-30);
         if (ch) ch[i] = (s->dead || s->sepv) ? INFINITY : base;
         if (cs) cs[i] = s->dead ? INFINITY : base + P->mu_sep * s->soft;
@@ -674,7 +702,7 @@ double orc_rollout_grad(const orc_problem *P, const orc_aircraft *A, const doubl
     const double dt = P->dt, sgmax = sin(P->gamma_max), tpmax = tan(P->phi_max);
     const double Sh = P->sep_h, Sv = P->sep_v, bet = P->sp_beta, mu = P->mu_sep;
     for (int n = 0; n < N * S * 3; n++) grad[n] = 0.0;
-    if (P->wind_mode != 0) return NAN;      /* the gradient uses the shared wind field */
+    if (P->wind_mode != 0 || P->rolling) return NAN;   /* shared wind field, fixed aircraft set */
     gstep *tr = (gstep *)malloc(sizeof(gstep) * (size_t)(H + 1) * N);
     double *gs = (double *)calloc((size_t)N * S * 3, sizeof(double));
     double total = 0.0;
@@ -1047,12 +1075,47 @@ void orc_mh_accept(const orc_problem *P, const double *u, const double *up, cons
  * Eq. (hor) with the climb angle kept below 90 degrees (|sin gamma| <= 0.999)
  * and the thrust held within [Tmin, Tmax]; disturbance = wind field W0[P][2]
  * (sample 0, step 0) plus white turbulence from random stream 7. */
+static int plant_active(const orc_problem *P, const orc_aircraft *A, int i)
+{
+    return !P->rolling ||
+           (!((P->finished >> i) & 1u) && (int64_t)A[i].t_enter <= (int64_t)P->mpc_step);
+}
+
+/* Rolling window (reading R22): the finished mask after a plant step that
+ * produced the states x[N][6] -- the previous mask plus every active arrival
+ * inside the landing sector of Eq. (TO_init) (range, glide angle, bearing cone
+ * with x > 0, heading, speed). */
+uint32_t orc_plant_finished(const orc_problem *P, const orc_aircraft *A, const double *x)
+{
+    uint32_t f = P->finished;
+    if (!P->rolling) return f;
+    for (int i = 0; i < P->N; i++) {
+        if (A[i].type != 0 || !plant_active(P, A, i)) continue;
+        const double *s = x + 6 * i;
+        const double r = sqrt(s[0] * s[0] + s[1] * s[1]);
+        const double th = atan2(s[1], s[0]), ath = fabs(th);
+        const double ratio = ath < 1e-3 ? 1.0 + th * th / 6.0 : ath / fmax(sin(ath), 0.25 * ath);
+        const double beta = atan2(s[2], r * ratio);
+        const double hdg = angdist(s[4] - M_PI);
+        if (r <= P->P_runway && beta <= P->P_beta && s[0] > 0.0 && ath <= P->P_chi &&
+            hdg <= P->P_chi && s[3] <= P->P_vs)
+            f |= 1u << i;
+    }
+    return f;
+}
+
+/* Rolling window: an aircraft that has not entered or has finished keeps its
+ * state. */
 void orc_plant_step(const orc_problem *P, const orc_aircraft *A, const double *x_in,
                     const double *W0, const double *u0, double *x_out)
 {
     for (int i = 0; i < P->N; i++) {
         const orc_aircraft *a = &A[i];
         const double *s = x_in + 6 * i;
+        if (!plant_active(P, A, i)) {
+            for (int c = 0; c < 6; c++) x_out[6 * i + c] = s[c];
+            continue;
+        }
         double x = s[0], y = s[1], z = s[2], v = s[3], chi = s[4], m = s[5];
         double w = u0[3 * i], hd = u0[3 * i + 1], acc = u0[3 * i + 2];
         double sg = hd / v;

@@ -53,11 +53,14 @@ typedef struct {
                                      1 a field per (particle, sample) on the 2x2x2 grid of
                                      the box corners (the paper's scheme) */
     const double *wind_chol;      /* mode 1: lower Cholesky factor of R_hat, 8 x 8 row-major */
+    int rolling;                  /* 1: rolling window (aircraft enter at t_enter, finished
+                                     aircraft have left; reading R22) */
+    uint32_t finished;            /* rolling window: bit i = aircraft i has left the problem */
 } orc_problem;
 
 typedef struct {
     int32_t type;                 /* 0 arrival, 1 departure */
-    int32_t pad_;
+    int32_t t_enter;              /* rolling window: MPC step at which the aircraft enters */
     double x, y, z, v, chi, m;
     double theta_F, Z, v_D;
     double m_empty, S, CD0, CD2, Cf1, Cf2, Tmin, Tmax;
@@ -123,6 +126,7 @@ void orc_mh_accept(const orc_problem *P, const double *u, const double *up, cons
 
 /* One step of the true system (plant of the MPC loop): x_in/x_out[N][6]
  * (x, y, z, v, chi, m), W0 = wind field of sample 0 at step 0, u0[N][3]. */
+uint32_t orc_plant_finished(const orc_problem *P, const orc_aircraft *A, const double *x);
 void orc_plant_step(const orc_problem *P, const orc_aircraft *A, const double *x_in,
                     const double *W0, const double *u0, double *x_out);
 

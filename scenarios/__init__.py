@@ -39,6 +39,7 @@ AIRCRAFT_DTYPE = np.dtype([
     ("S", np.float64), ("CD0", np.float64), ("CD2", np.float64),
     ("Cf1", np.float64), ("Cf2", np.float64),
     ("Tmin", np.float64), ("Tmax", np.float64),
+    ("t_enter", np.int32),       # rolling window: MPC step at which the aircraft enters
 ])
 
 NM = 1852.0
@@ -98,6 +99,8 @@ class Problem:
     wind_mode: int = 0                           # 1: a field per (particle, sample), 2x2x2 grid
     sample_mode: int = 0                         # 1: iteration J draws min(kappa_J, M) samples
     L_sched: Optional[tuple] = None              # particles per iteration (J_max entries, <= L)
+    rolling: int = 0                             # 1: rolling window (t_enter, finished aircraft)
+    finished: int = 0                            # rolling window: bit i = aircraft i has left
     aircraft: Optional[np.ndarray] = None        # AIRCRAFT_DTYPE[N]
 
     def copy(self, **kw) -> "Problem":
