@@ -725,8 +725,11 @@ def run_schedule(args, local):
     def particles_of(p, J):
         return p.L_sched[J] if p.L_sched is not None else p.L
 
+    tuned = {}
+
     def timed_solve(p):
         sol = pkg.Solver(p)
+        tuned[p.N] = pkg.tma_get_tuning(sol.h)[0]
         sol.solve()                       # warm (autotuning, allocation)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -738,11 +741,19 @@ def run_schedule(args, local):
         return bu, c, e0.elapsed_time(e1)
 
     res = {m: {"ms": [], "heldout": [], "units": []} for m in variants}
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except (AttributeError, RuntimeError):
+        uuid = None
+    sampler = ClockSampler(uuid) if uuid else None
+    if sampler:
+        sampler.start()
     for s in range(args.seeds):
         p0 = S.config2(seed=base.seed + 1000 * s)
         ev = pkg.Solver(p0.copy(M=256, L=32))
         ev.set_wind_stream(8)
         ev.wind_field()
+        torch.cuda.synchronize()
         for name, kw in variants.items():
             p = p0.copy(**kw)
             bu, c, ms = timed_solve(p)
@@ -755,7 +766,8 @@ def run_schedule(args, local):
     out = {"mode": "schedule", "workload": "tma-8ac-L65536-M32-H60-grid64x64x8-J30",
            "seeds": args.seeds, "heldout_samples": 256,
            "samples_per_iteration": [samples_of(base.copy(sample_mode=1), J) for J in range(base.J_max)],
-           "particles_per_iteration": list(lsched)}
+           "particles_per_iteration": list(lsched),
+           "clocks": sampler.stop() if sampler else None, "rollout_variant": tuned}
     for name, r in res.items():
         ms = np.array(r["ms"])
         H = np.array(r["heldout"])

@@ -110,6 +110,15 @@ typedef struct {
                                  ancestors (tma_resample_to) -- the varying particle count the
                                  paper proposes (Sec. 9).  Copied by tma_create; single solvers
                                  only (tma_batch_create rejects it). */
+    int32_t rolling;          /* 1: rolling window (the paper's rolling-window section).  At MPC
+                                 step t aircraft i flies the horizon steps k >= max(0, t_enter - t)
+                                 from its entry state, its objective is the mean of its per-step
+                                 terms over those steps, and an aircraft that enters after the
+                                 horizon, or has finished, is out of the problem (cost 0, not
+                                 simulated, not in separation checks).  The plant moves only
+                                 active aircraft and marks an arrival finished once it is in the
+                                 landing sector of Eq. (TO_init).  tma_rollout_grad and the
+                                 Langevin move need rolling = 0. */
 } tma_problem;
 
 typedef struct {
@@ -118,8 +127,9 @@ typedef struct {
 
 typedef struct {
     int32_t type;             /* 0 arrival, 1 departure */
-    int32_t pad_;
-    tma_state x0;             /* initial state */
+    int32_t t_enter;          /* rolling window (tma_problem.rolling = 1): the MPC step at which
+                                 the aircraft enters the problem; ignored otherwise */
+    tma_state x0;             /* initial state (the entry state of a late entrant) */
     double theta_F, Z, v_D;   /* departure targets: bearing, altitude, airspeed (Sec. 3.5) */
     double m_empty;           /* minimum mass m_Aircraft (Sec. 3.4) */
     double S, CD0, CD2;       /* wing area and drag polar */
@@ -337,6 +347,17 @@ tma_status tma_mpc_run(tma_solver *s, int32_t n_steps, tma_state *h_traj, double
  * particle had an infeasible aircraft (no particle satisfied every limit).
  * Clears the word; syncs. */
 tma_status tma_get_error(tma_solver *s, uint32_t *h_err, tma_stream_t stream);
+
+/* Rolling window: set the mask of aircraft that have left the problem (bit i =
+ * aircraft i; bits at or above N must be zero); tma_set_state with states
+ * clears it, the plant step sets bits of arrivals that landed.  Syncs. */
+tma_status tma_set_finished(tma_solver *s, uint32_t mask, tma_stream_t stream);
+
+/* Rolling window: per aircraft h_status[N] (may be NULL) at the current MPC
+ * step -- 0 not yet entered (t_enter > MPC step), 1 active, 2 finished -- and
+ * the finished mask (may be NULL).  Without a rolling window every aircraft is
+ * 1.  Syncs. */
+tma_status tma_get_status(tma_solver *s, int32_t *h_status, uint32_t *h_finished, tma_stream_t stream);
 
 /* The solver's current state h_x[N] (host) and MPC step; syncs. */
 tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream);

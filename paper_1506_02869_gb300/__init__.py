@@ -38,7 +38,7 @@ EXPORTS = [
     "tma_batch_mpc", "tma_batch_results", "tma_batch_latency", "tma_batch_live_steps",
     "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
     "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
-    "tma_resample_to", "tma_move_to",
+    "tma_resample_to", "tma_move_to", "tma_set_finished", "tma_get_status",
 ]
 
 
@@ -66,7 +66,7 @@ class TmaProblem(C.Structure):
         ("popdense", C.POINTER(C.c_double)), ("P_runway", C.c_double), ("P_beta", C.c_double),
         ("P_chi", C.c_double), ("P_vs", C.c_double), ("beta_f", C.c_double),
         ("wind_mode", C.c_int32), ("sample_mode", C.c_int32),
-        ("L_sched", C.POINTER(C.c_int64)),
+        ("L_sched", C.POINTER(C.c_int64)), ("rolling", C.c_int32),
     ]
 
 
@@ -83,7 +83,7 @@ STAGES = ("wind", "init", "rollout", "sample_mean", "lse", "resample", "move", "
 
 
 class TmaAircraft(C.Structure):
-    _fields_ = [("type", C.c_int32), ("pad_", C.c_int32), ("x0", TmaState)] + [
+    _fields_ = [("type", C.c_int32), ("t_enter", C.c_int32), ("x0", TmaState)] + [
         (n, C.c_double) for n in ("theta_F", "Z", "v_D", "m_empty", "S", "CD0", "CD2", "Cf1",
                                   "Cf2", "Tmin", "Tmax")]
 
@@ -138,6 +138,8 @@ def lib():
                 "tma_get_grad_tuning": ([vp, P(i32), P(i32), P(i32), P(C.c_float)], C.c_int),
                 "tma_plant_step": ([vp, vp, st], C.c_int),
                 "tma_get_state": ([vp, P(TmaState), P(u32), st], C.c_int),
+                "tma_set_finished": ([vp, u32, st], C.c_int),
+                "tma_get_status": ([vp, P(i32), P(u32), st], C.c_int),
                 "tma_mpc_run": ([vp, i32, P(TmaState), P(d), st], C.c_int),
                 "tma_get_error": ([vp, P(u32), st], C.c_int),
                 "tma_batch_create": ([P(TmaProblem), P(P(TmaAircraft)), i32, P(vp)], C.c_int),
@@ -222,6 +224,7 @@ def problem_struct(p):
     s.sep_mode = int(_get(p, "sep_mode"))
     s.wind_mode = int(_get(p, "wind_mode", 0))
     s.sample_mode = int(_get(p, "sample_mode", 0))
+    s.rolling = int(_get(p, "rolling", 0))
     s.ctrl_lo[:] = [float(v) for v in _get(p, "ctrl_lo")]
     s.ctrl_hi[:] = [float(v) for v in _get(p, "ctrl_hi")]
     s.move_sigma[:] = [float(v) for v in _get(p, "move_sigma")]
@@ -247,6 +250,7 @@ def problem_struct(p):
         r = ac[i]
         a = arr[i]
         a.type = int(r["type"])
+        a.t_enter = int(r["t_enter"]) if "t_enter" in r.dtype.names else 0
         for n in ("x", "y", "z", "v", "chi", "m"):
             setattr(a.x0, n, float(r[n]))
         for n in ("theta_F", "Z", "v_D", "m_empty", "S", "CD0", "CD2", "Cf1", "Cf2", "Tmin", "Tmax"):
@@ -487,6 +491,18 @@ def tma_get_state(h, N, stream=None):
     return np.array([[a.x, a.y, a.z, a.v, a.chi, a.m] for a in arr]), mpc.value
 
 
+def tma_set_finished(h, mask, stream=None):
+    _check(lib().tma_set_finished(h, int(mask) & 0xFFFFFFFF, _stream(stream)), "tma_set_finished")
+
+
+def tma_get_status(h, N, stream=None):
+    """(per-aircraft status [N]: 0 not entered, 1 active, 2 finished; finished mask)."""
+    st = (C.c_int32 * N)()
+    fin = C.c_uint32()
+    _check(lib().tma_get_status(h, st, C.byref(fin), _stream(stream)), "tma_get_status")
+    return np.array(list(st), np.int32), fin.value
+
+
 # ----------------------------------------------------------------- batches
 
 def tma_batch_create(problems):
@@ -643,6 +659,12 @@ class Solver:
 
     def set_state(self, x0=None, mpc_step=0):
         tma_set_state(self.h, x0, mpc_step)
+
+    def set_finished(self, mask):
+        tma_set_finished(self.h, mask)
+
+    def status(self):
+        return tma_get_status(self.h, self.N)
 
     def wind_field(self):
         torch = _torch()

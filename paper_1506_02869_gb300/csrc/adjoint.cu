@@ -380,7 +380,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
         // checkpoints; J_T fixes the cost coefficients of the reverse sweep
         AcState s;
         ac_init(s, dyn, i, exists);
-        const AltBounds ab = alt_bounds(P, A, s.z);
+        const AltBounds ab = alt_bounds(P, A, s.z, P.H);
         CostSums cs;
         for (int k = 0; k < P.H; ++k) {
             if (k % kCkEvery == 0) ck[k / kCkEvery] = save(s);
@@ -388,7 +388,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
                 ac_step(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i,
                         (uint32_t)m, k, J, mpc, cs);
         }
-        const float JT = total_objective(P, A, cs, s.F.s, ab);
+        const float JT = total_objective(P, A, cs, s.F.s, ab, P.H);
         const float c = -logf(fmaxf(JT, 1e-30f));
         const bool dead = s.dead;
         const CostGrad cg = cost_grad(P, A, JT, ab, invM);

@@ -325,7 +325,9 @@ __global__ void stamp_start(unsigned long long *t0)
 // white turbulence from random stream 7; the climb angle is kept below 90 degrees and the thrust
 // within its limits (the plant cannot refuse a command), and the speed and
 // fuel follow from the applied thrust.  The state is written back for the
-// next MPC step.
+// next MPC step.  Rolling window: an aircraft that has not entered
+// (t_enter > MPC step) or has finished keeps its state; an arrival that ends
+// the step in the landing sector is marked finished.
 __global__ void __launch_bounds__(128) plant_step_kernel(const ProblemC *__restrict__ probs,
                                                          const BatchScen *__restrict__ scen,
                                                          const int *__restrict__ seg_scen,
@@ -341,6 +343,8 @@ __global__ void __launch_bounds__(128) plant_step_kernel(const ProblemC *__restr
     const int i = (int)(seg - sc.seg_off);
     const AircraftC &A = P.ac[i];
     DynState &d = dyns[s];
+    if (P.rolling && ((((d.finished >> i) & 1u) != 0u) || (long long)A.t_enter > (long long)d.mpc_step))
+        return;
     const float x = d.x0[i][0], y = d.x0[i][1], z = d.x0[i][2];
     const float v = d.x0[i][3], chi = d.x0[i][4], mass = d.x0[i][5];
     const float *uu = best_u + (size_t)seg * S * 3;   // segment 0 of this aircraft
@@ -385,6 +389,14 @@ __global__ void __launch_bounds__(128) plant_step_kernel(const ProblemC *__restr
     d.x0[i][3] = fmaf(dt, (T - D) / mass - kG0 * sg, v);
     d.x0[i][4] = fmaf(dt, uw, chi);
     d.x0[i][5] = mass - dt * eta * T;
+    if (P.rolling && A.type == 0) {
+        // only this thread sets bit i; the others read their own bits
+        const float x1 = d.x0[i][0], y1 = d.x0[i][1];
+        const float th = atan2_poly(y1, x1);
+        float r, ath;
+        const float beta = arc_glide(x1, y1, d.x0[i][2], th, r, ath);
+        if (in_landing_sector(P, x1, r, ath, beta, d.x0[i][4], d.x0[i][3])) atomicOr(&d.finished, 1u << i);
+    }
 }
 
 __global__ void advance_mpc_step(DynState *__restrict__ dyns, int n_scen)

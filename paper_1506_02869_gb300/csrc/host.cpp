@@ -166,6 +166,7 @@ static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
     if (p->grid[2] > TMA_MAX_GRID_Z) return TMA_ERR_INVALID_ARG;
     if (p->wind_mode != 0 && p->wind_mode != 1) return TMA_ERR_INVALID_ARG;
     if (p->sample_mode != 0 && p->sample_mode != 1) return TMA_ERR_INVALID_ARG;
+    if (p->rolling != 0 && p->rolling != 1) return TMA_ERR_INVALID_ARG;
     if (p->L_sched)
         for (int J = 0; J < p->J_max; ++J)
             if (p->L_sched[J] < 1 || p->L_sched[J] > p->L) return TMA_ERR_INVALID_ARG;
@@ -290,7 +291,9 @@ static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraf
         const double Fmax = p.H * p.dt * a.Tmax * a.Cf1 * (1.0 + p.v_max / a.Cf2);
         c.invFmax = (float)(1.0 / Fmax);
         c.invCmax = (float)(1.0 / std::max(p.v_max - a.v_D, a.v_D - p.v_min));
+        c.t_enter = a.t_enter;
     }
+    P.rolling = p.rolling;
     return P;
 }
 
@@ -706,6 +709,9 @@ static tma_status autotune_rollout(tma_solver *s)
     }
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // time on an idle device: work still running on other streams (the caller's
+    // own kernels) would make a slower variant look faster
+    TMA_CUDA(cudaDeviceSynchronize());
     TMA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     auto cleanup = [&]() {
         if (e0) cudaEventDestroy(e0);
@@ -935,6 +941,9 @@ static tma_status autotune_grad(tma_solver *s)
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float *d_u = nullptr;
+    // time on an idle device: work still running on other streams (the caller's
+    // own kernels) would make a slower variant look faster
+    TMA_CUDA(cudaDeviceSynchronize());
     TMA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -1013,7 +1022,8 @@ extern "C" tma_status tma_rollout_grad(tma_solver *s, const float *d_u, int64_t 
 {
     if (!s || !d_u || !d_cost || !d_grad || L < 0 || L > s->prob.L || J < 0 || J > 0xFFFF)
         return TMA_ERR_INVALID_ARG;
-    if (s->prob.H > TMA_MAX_GRAD_HORIZON || s->prob.wind_mode != 0) return TMA_ERR_UNSUPPORTED;
+    if (s->prob.H > TMA_MAX_GRAD_HORIZON || s->prob.wind_mode != 0 || s->prob.rolling != 0)
+        return TMA_ERR_UNSUPPORTED;
     if (L == 0) return TMA_OK;
     return grad_into(s, d_u, L, J, d_cost, d_grad, d_cbar_soft, (cudaStream_t)stream);
 }
@@ -1056,7 +1066,8 @@ extern "C" tma_status tma_set_move(tma_solver *s, int32_t kind, double eps0)
         return TMA_OK;
     }
     if (!(eps0 > 0.0) || !std::isfinite(eps0) || s->prob.sep_mode == 0) return TMA_ERR_INVALID_ARG;
-    if (kind == TMA_MOVE_MALA && (s->prob.H > TMA_MAX_GRAD_HORIZON || s->prob.wind_mode != 0))
+    if (kind == TMA_MOVE_MALA &&
+        (s->prob.H > TMA_MAX_GRAD_HORIZON || s->prob.wind_mode != 0 || s->prob.rolling != 0))
         return TMA_ERR_UNSUPPORTED;
     tma_status r = ensure_mh_scalars(s);
     if (r != TMA_OK) return r;
@@ -1484,6 +1495,30 @@ tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_str
     return TMA_OK;
 }
 
+tma_status tma_set_finished(tma_solver *s, uint32_t mask, tma_stream_t stream)
+{
+    if (!s || (s->prob.N < 32 && (mask >> s->prob.N) != 0u)) return TMA_ERR_INVALID_ARG;
+    TMA_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(s->d_dyn) + offsetof(DynState, finished), &mask,
+                             sizeof mask, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return TMA_OK;
+}
+
+tma_status tma_get_status(tma_solver *s, int32_t *h_status, uint32_t *h_finished, tma_stream_t stream)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    DynState d;
+    TMA_CUDA(cudaMemcpyAsync(&d, s->d_dyn, sizeof d, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int i = 0; h_status && i < s->prob.N; ++i) {
+        if ((d.finished >> i) & 1u) h_status[i] = 2;
+        else if (s->prob.rolling && (int64_t)s->aircraft[i].t_enter > (int64_t)d.mpc_step) h_status[i] = 0;
+        else h_status[i] = 1;
+    }
+    if (h_finished) *h_finished = d.finished;
+    return TMA_OK;
+}
+
 // ------------------------------------------------------------------ batches
 
 static void batch_free(tma_batch *b)
@@ -1776,6 +1811,7 @@ tma_status tma_batch_set_state(tma_batch *b, const tma_state *h_x0, const uint32
             d[4] = (float)x.chi;
             d[5] = (float)x.m;
         }
+        if (h_x0) b->dyn_h[s].finished = 0u;     // new states: every aircraft back in the problem
         if (h_mpc) {
             if (h_mpc[s] > 0xFFFF) return TMA_ERR_INVALID_ARG;
             b->dyn_h[s].mpc_step = h_mpc[s];

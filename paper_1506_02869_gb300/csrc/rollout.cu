@@ -20,9 +20,9 @@ namespace {
 // Launch-bound variants (block size cap, minimum resident blocks per SM): the
 // register budget per thread is 65536 / (cap * blocks); the autotuner picks
 // among the variants whose cap fits the block (32 * N threads).  OwnWind is
-// wind mode 1 (per-particle fields), a kernel of its own so that mode 0 keeps
-// its register allocation.
-template <int kMaxThreads, int kMinBlocks, bool OwnWind>
+// wind mode 1 (per-particle fields) and Rolling the rolling window, each a
+// kernel of its own so that the plain problem keeps its register allocation.
+template <int kMaxThreads, int kMinBlocks, bool OwnWind, bool Rolling>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const ProblemC P,
                                                        const DynState *__restrict__ dyn,
                                                        const float *__restrict__ u,
@@ -35,8 +35,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const 
     const int m = blockIdx.x / nLb;            // wind sample: block-uniform
     const long long l0 = (long long)(blockIdx.x - m * nLb) * kPB;
     const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
-    const TileResult r = rollout_tile_mode<OwnWind>(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0, i, j,
-                                                    m, J, cost_ms_soft != nullptr, spos, 0, blockDim.x);
+    const TileResult r = rollout_tile_mode<OwnWind, Rolling>(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0,
+                                                             i, j, m, J, cost_ms_soft != nullptr, spos, 0,
+                                                             blockDim.x);
     store_tile(r, P.N, L, l0 + j, i, j, m, cost_ms, cost_ms_soft, live);
 }
 
@@ -91,18 +92,23 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
     const size_t smem = (size_t)tile_smem_words(P.N, P.wind_mode) * sizeof(float);
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
     // above the default 48 KB of dynamic shared memory the kernel must opt in
-#define TMA_ROLLOUT_K(T, B, O)                                                                   \
+#define TMA_ROLLOUT_K(T, B, O, R)                                                                \
     do {                                                                                         \
         if (smem > 48 * 1024)                                                                    \
-            cudaFuncSetAttribute(rollout_kernel<T, B, O>,                                        \
+            cudaFuncSetAttribute(rollout_kernel<T, B, O, R>,                                     \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        rollout_kernel<T, B, O><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J,        \
-                                                           cost_ms, cost_ms_soft, live);         \
+        rollout_kernel<T, B, O, R><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J,     \
+                                                              cost_ms, cost_ms_soft, live);      \
     } while (0)
 #define TMA_ROLLOUT(T, B)                                                                        \
     do {                                                                                         \
-        if (P.wind_mode == 1) TMA_ROLLOUT_K(T, B, true);                                         \
-        else TMA_ROLLOUT_K(T, B, false);                                                         \
+        if (P.wind_mode == 1) {                                                                  \
+            if (P.rolling) TMA_ROLLOUT_K(T, B, true, true);                                      \
+            else TMA_ROLLOUT_K(T, B, true, false);                                               \
+        } else {                                                                                 \
+            if (P.rolling) TMA_ROLLOUT_K(T, B, false, true);                                     \
+            else TMA_ROLLOUT_K(T, B, false, false);                                              \
+        }                                                                                        \
     } while (0)
     switch (variant) {
     case 0: TMA_ROLLOUT(256, 4); break;

@@ -225,6 +225,28 @@ __device__ __forceinline__ void ac_init(AcState &s, const DynState *__restrict__
     s.th = s.beta = 0.0f;
 }
 
+// Arrival geometry (Eq. (flow)): the arc tangent to the runway through the
+// aircraft at bearing th = atan2(y, x) has length s = r th / sin th (capped at
+// 4 r); returns the glide angle atan2(z, s) and r, |th|.
+__device__ __forceinline__ float arc_glide(float x, float y, float z, float th, float &r, float &ath)
+{
+    r = sqrtf(fmaf(x, x, y * y));
+    ath = fabsf(th);
+    const float ratio = ath < 1e-3f ? fmaf(th * th, 1.0f / 6.0f, 1.0f)
+                                    : __fdividef(ath, fmaxf(__sinf(ath), 0.25f * ath));
+    return atan2_poly(z, r * ratio);
+}
+
+// The landing sector of Eq. (TO_init): range, glide angle, bearing cone on the
+// approach side (x > 0), heading within P_chi of the runway, speed.
+__device__ __forceinline__ bool in_landing_sector(const ProblemC &P, float x, float r, float ath,
+                                                  float beta, float chi, float v)
+{
+    const float hdg = angdist(chi - kPi);
+    return r <= P.P_runway && beta <= P.P_beta && x > 0.0f && ath <= P.P_chi && hdg <= P.P_chi &&
+           v <= P.P_vs;
+}
+
 // Per-step deviation sums of the objectives (Sec. 3.5, Sec. 7.1).
 struct CostSums {
     Kahan sA, sB, sC;
@@ -333,14 +355,9 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
         s.th = atan2_poly(s.y, s.x);
         if (A.type == 0) {
             // arrival: flow-field arc, glide angle and landing sector
-            const float r = sqrtf(fmaf(s.x, s.x, s.y * s.y));
-            const float ath = fabsf(s.th);
-            const float ratio = ath < 1e-3f ? fmaf(s.th * s.th, 1.0f / 6.0f, 1.0f)
-                                            : __fdividef(ath, fmaxf(__sinf(ath), 0.25f * ath));
-            s.beta = atan2_poly(s.z, r * ratio);
-            const float hdg = angdist(s.chi - kPi);
-            if (r <= P.P_runway && s.beta <= P.P_beta && s.x > 0.0f && ath <= P.P_chi &&
-                hdg <= P.P_chi && s.v <= P.P_vs) {
+            float r, ath;
+            s.beta = arc_glide(s.x, s.y, s.z, s.th, r, ath);
+            if (in_landing_sector(P, s.x, r, ath, s.beta, s.chi, s.v)) {
                 s.landed = true;
             } else {
                 visit.arrival(P, A, s);
@@ -355,26 +372,30 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
 
 // Departure altitude term: sup / inf of the per-step distance to Z reachable
 // from the current altitude at the maximum climb rate c (Sec. 3.5), in closed
-// form: sup = d0 + c (H+1)/2, inf = (K d0 - c K (K+1)/2) / H, K = min(H, floor(d0/c)).
+// form over the Ha scored steps (Ha = H, or a late entrant's active steps):
+// sup = d0 + c (Ha+1)/2, inf = (K d0 - c K (K+1)/2) / Ha, K = min(Ha, floor(d0/c)).
 struct AltBounds {
     float supB, invSupInf;
 };
 
-__device__ __forceinline__ AltBounds alt_bounds(const ProblemC &P, const AircraftC &A, float z0)
+__device__ __forceinline__ AltBounds alt_bounds(const ProblemC &P, const AircraftC &A, float z0, int Ha)
 {
     const float d0 = fabsf(A.Z - z0);
-    const float supB = fmaf(P.climb_step, 0.5f * (float)(P.H + 1), d0);
-    const float Kf = fminf((float)P.H, floorf(__fdividef(d0, P.climb_step)));
-    const float infB = (Kf * d0 - P.climb_step * 0.5f * Kf * (Kf + 1.0f)) / (float)P.H;
+    const float supB = fmaf(P.climb_step, 0.5f * (float)(Ha + 1), d0);
+    const float Kf = fminf((float)Ha, floorf(__fdividef(d0, P.climb_step)));
+    const float infB = (Kf * d0 - P.climb_step * 0.5f * Kf * (Kf + 1.0f)) / (float)Ha;
     return AltBounds{supB, 1.0f / (supB - infB)};
 }
 
-// J_T of Sec. 3.5 and Sec. 7.1 from the deviation sums and the fuel burned.
+// J_T of Sec. 3.5 and Sec. 7.1 from the deviation sums and the fuel burned,
+// per-step means over the Ha scored steps (the fuel bound too: A.invFmax is
+// for H steps).
 __device__ __forceinline__ float total_objective(const ProblemC &P, const AircraftC &A,
-                                                 const CostSums &c, float Fs, AltBounds ab)
+                                                 const CostSums &c, float Fs, AltBounds ab, int Ha)
 {
-    const float invH = 1.0f / (float)P.H;
-    const float Jf = fmaf(-Fs, A.invFmax, 1.0f);
+    const float invH = 1.0f / (float)Ha;
+    const float Jf = Ha == P.H ? fmaf(-Fs, A.invFmax, 1.0f)
+                               : fmaf(-Fs, A.invFmax * ((float)P.H * invH), 1.0f);
     float Jsum;
     if (A.type == 1) {
         const float J1 = fmaf(-c.sA.s * invH, 1.0f / kPi, 1.0f);
@@ -419,8 +440,9 @@ struct TileResult {
     unsigned int live;  // aircraft-steps simulated by this thread
 };
 
-// OwnWind: wind mode 1 (compiled apart, so mode 0 keeps its register budget).
-template <bool OwnWind>
+// OwnWind: wind mode 1; Rolling: the rolling window (each compiled apart, so
+// the plain problem keeps its register budget).
+template <bool OwnWind, bool Rolling>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
                                                         const float *__restrict__ u,
                                                         const float4 *__restrict__ Wm, long long L,
@@ -433,10 +455,27 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     const bool exists = l < L;
     const AircraftC &A = P.ac[i];
     const uint32_t mpc = dyn->mpc_step;
+    // rolling window: the first step this aircraft flies, and whether it is in
+    // the problem at all during this horizon (warp-uniform)
+    int k_in = 0;
+    bool out = false;
+    if (Rolling) {
+        const long long d = (long long)A.t_enter - (long long)mpc;
+        k_in = d > 0 ? (int)min(d, (long long)P.H) : 0;
+        out = ((dyn->finished >> i) & 1u) != 0u || k_in >= P.H;
+    }
+    const int Ha = P.H - k_in;
     AcState s;
-    ac_init(s, dyn, i, exists);
+    ac_init(s, dyn, i, exists && !out);
+    if (Rolling && (k_in & 1) && exists && !out) {
+        // entering at an odd step: the turbulence pair of that step comes from
+        // the draw of the even step before it, which this aircraft did not fly
+        const uint4 r = draw(P.key0, P.key1, (uint32_t)l, (uint32_t)i | ((uint32_t)m << 8),
+                             (uint32_t)(k_in >> 1), 0u, (uint32_t)J, mpc);
+        s.turb_next = box_muller_fast(r.z, r.w);
+    }
     const float m0 = dyn->x0[i][5];
-    const AltBounds ab = alt_bounds(P, A, s.z);
+    const AltBounds ab = alt_bounds(P, A, s.z, Ha);
     CostSums cs;
     float soft = 0.0f;
     bool sepv = false;
@@ -460,7 +499,8 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     }
 
     for (int k = 0; k < P.H; ++k) {
-        if (!s.dead && !s.landed) {
+        const bool entered = k >= k_in;
+        if (!s.dead && !s.landed && entered) {
             ++nlive;
             ac_step(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i, (uint32_t)m, k,
                     J, mpc, cs, own_wind ? pw + (k & 1) * 16 * kPB + j : nullptr);
@@ -469,7 +509,7 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
         if (own_wind && k + 1 < P.H) particle_wind_step(P, pw, i, N, j, (uint32_t)l, m, k + 1, mpc);
         // binary separation constraints at step k+1 among flying aircraft: every
         // thread publishes its position (a far-away altitude when not flying)
-        const bool act = !s.dead && !s.landed;
+        const bool act = !s.dead && !s.landed && entered;
         float4 *buf = pos + (k & 1) * plane;
         buf[i * kPB + j] = make_float4(s.x, s.y, act ? s.z : 1e30f, 0.0f);
         tile_barrier(bar_id, bar_count);
@@ -520,11 +560,15 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     }
 
     // the per-sample cost -ln J_T (Sec. 3.6)
-    const float JT = total_objective(P, A, cs, s.F.s, ab);
+    const float JT = total_objective(P, A, cs, s.F.s, ab, Ha);
     const float c = -logf(fmaxf(JT, 1e-30f));
     TileResult r;
     r.cost = (s.dead || sepv) ? __int_as_float(0x7f800000) : c;
     r.cost_soft = s.dead ? __int_as_float(0x7f800000) : fmaf(P.mu_sep, soft, c);
+    if (out) {                      // not in the problem this horizon: J_T = 1
+        r.cost = 0.0f;
+        r.cost_soft = 0.0f;
+    }
     r.live = exists ? nlive : 0u;
     return r;
 }
@@ -537,8 +581,14 @@ __device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynS
                                                    int bar_count)
 {
     if (P.wind_mode == 1)
-        return rollout_tile_mode<true>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos, bar_id, bar_count);
-    return rollout_tile_mode<false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos, bar_id, bar_count);
+        return P.rolling ? rollout_tile_mode<true, true>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+                                                         bar_id, bar_count)
+                         : rollout_tile_mode<true, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+                                                          bar_id, bar_count);
+    return P.rolling ? rollout_tile_mode<false, true>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+                                                      bar_id, bar_count)
+                     : rollout_tile_mode<false, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+                                                       bar_id, bar_count);
 }
 
 // Stores one thread's tile result: cost_ms[(m N + i) L + l] (and the soft

@@ -23,6 +23,7 @@ struct AircraftC {
     float thF, Z, vD;
     float invFmax;         // 1 / (H dt Tmax eta(vmax))
     float invCmax;         // departure speed-term normalisation
+    int t_enter;           // rolling window: MPC step at which the aircraft enters
 };
 
 // Problem constants passed by value to the rollout kernels.
@@ -45,6 +46,7 @@ struct ProblemC {
     float pop_lo[2], pop_hi[2], pop_inv_h[2];
     const float *popdense; // device [pop_n0][pop_n1] or nullptr
     float P_runway, P_beta, P_chi, P_vs, beta_f;
+    int rolling;           // 1: rolling window (t_enter, finished aircraft)
     int wind_mode;         // 1: a wind field per (particle, sample) on the box corners
     float wind_a, wind_b;  // AR(1) coefficients a, sqrt(1 - a^2) of that field
     float wchol[36];       // its Qhat: lower Cholesky factor of R_hat (8 x 8, packed rows)
@@ -56,6 +58,7 @@ struct ProblemC {
 struct DynState {
     float x0[kMaxN][6];
     uint32_t mpc_step;
+    uint32_t finished;     // rolling window: bit i = aircraft i has left the problem
 };
 
 // Parameters of the wind-field generation kernels.

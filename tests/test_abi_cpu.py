@@ -49,8 +49,8 @@ def test_struct_layout_matches_header(tmp_path):
                                                "wind_sigma", "sep_mode", "sp_beta", "ctrl_lo",
                                                "alpha_dep", "w_noise", "pop_n", "pop_lo",
                                                "popdense", "P_runway", "beta_f", "wind_mode",
-                                               "sample_mode", "L_sched"]),
-              "tma_aircraft": (pkg.TmaAircraft, ["type", "x0", "theta_F", "m_empty", "Tmax"]),
+                                               "sample_mode", "L_sched", "rolling"]),
+              "tma_aircraft": (pkg.TmaAircraft, ["type", "t_enter", "x0", "theta_F", "m_empty", "Tmax"]),
               "tma_state": (pkg.TmaState, ["x", "m"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(){"]
     for st, (_, fs) in fields.items():
@@ -89,7 +89,8 @@ def _create(p):
                                     dict(v_min=300.0), dict(wind_mode=2), dict(wind_mode=-1),
                                     dict(wind_mode=1, grid=(2, 2, 3)), dict(wind_mode=1, grid=(4, 4, 4)),
                                     dict(sample_mode=2), dict(sample_mode=-1),
-                                    dict(L_sched=(1024,) * 9 + (0,)), dict(L_sched=(2048,) + (1024,) * 9)])
+                                    dict(L_sched=(1024,) * 9 + (0,)), dict(L_sched=(2048,) + (1024,) * 9),
+                                    dict(rolling=2), dict(rolling=-1)])
 def test_create_rejects_invalid_problems(lib, change):
     p = S.config1().copy(**change)
     if "N" in change and change["N"] > 2:
@@ -118,6 +119,8 @@ def test_stage_calls_reject_invalid_arguments(lib):
     assert L.tma_resample_to(null, 2, 10, 7, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
     assert L.tma_resample_to(null, 0, 10, 7, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_OK
     assert L.tma_move_to(null, null, 4, null, 4, 0, null, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_set_finished(null, 0, null) == pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_get_status(null, None, None, null) == pkg.TMA_ERR_INVALID_ARG
 
 
 def test_workspace_sizes(lib):
