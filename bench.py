@@ -781,6 +781,65 @@ def run_schedule(args, local):
     return 0
 
 
+def run_layout_sweep(args, local):
+    """The paper's layout sweep (Sec. 4.4, Table comp_sense) re-run on GB300.
+    Its standard problem: 10 aircraft that all enter the problem at MPC step 5
+    with a horizon of 6 steps (rolling window: partly active horizons before
+    that), 10240 particles; the time of one MPC update (solve + plant step)
+    averaged over the steps after the settling period.  On GB300 the block is
+    fixed by the mapping (32 particles x N aircraft); what varies is the
+    launch-bound variant (block-size cap x minimum resident blocks, i.e.
+    registers per thread against resident blocks per SM), each forced in
+    turn.  Traffic: the first 10 aircraft of the 12-aircraft workload; M 16,
+    J_max 30, 16x16x4 wind grid."""
+    import numpy as np
+    import torch
+
+    import paper_1506_02869_gb300 as pkg
+    import scenarios as S
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    base = S.config4()
+    ac = base.aircraft[:10].copy()
+    ac["t_enter"] = 5
+    p = base.copy(N=10, aircraft=ac, L=10240, H=6, rolling=1, mpc_step=0)
+    names = {0: "256x4", 1: "256x3", 2: "512x2", 3: "512x1", 4: "1024x1", 5: "256x2",
+             6: "384x2", 7: "768x1"}
+    regs = {0: 64, 1: 85, 2: 64, 3: 128, 4: 64, 5: 128, 6: 85, 7: 85}
+    stream = torch.cuda.current_stream()
+    n_steps = args.mpc_steps if args.mpc_steps > 6 else 9
+    rows = []
+    auto = None
+    for v in range(8):
+        sol = pkg.Solver(p)
+        if auto is None:
+            auto = pkg.tma_get_tuning(sol.h)[0]
+        try:
+            pkg.tma_set_tuning(sol.h, v)
+        except pkg.TmaError:
+            sol.close()
+            continue
+        sol.solve()                    # warm
+        sol.set_state(mpc_step=0)
+        ms = []
+        for step in range(n_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            pkg.tma_mpc_run(sol.h, 1, p.N)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        sol.close()
+        rows.append({"variant": v, "layout": names[v], "threads_per_block": 32 * p.N,
+                     "max_registers": regs[v], "ms_per_update_by_step": [round(x, 2) for x in ms],
+                     "settled_ms_per_update": round(float(np.mean(ms[5:])), 3)})
+    print(json.dumps({"mode": "layout-sweep", "workload": "tma-10ac-enter5-L10240-M16-H6-J30-rolling",
+                      "autotuner_choice": auto, "rows": rows}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -814,6 +873,8 @@ def main(argv=None):
     ap.add_argument("--schedule", action="store_true",
                     help="compare fixed work with the sample schedule (the inner loop of Algorithm 1) "
                          "and a falling particle count")
+    ap.add_argument("--layout-sweep", action="store_true",
+                    help="re-run the paper's thread/block layout sweep (forced launch variants)")
     ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--eps-rw", type=float, default=1.0)
     ap.add_argument("--eps-mala", type=float, default=0.3)
@@ -827,6 +888,8 @@ def main(argv=None):
         return run_moves(args, local)
     if args.schedule:
         return run_schedule(args, local)
+    if args.layout_sweep:
+        return run_layout_sweep(args, local)
     if args.grad_only:
         return run_grad_only(args, local)
     if args.stages:

@@ -240,6 +240,12 @@ tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
 tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int32_t *h_variants,
                           float *h_ms);
 
+/* Force the rollout kernel's launch variant (0-7: block-size cap x minimum
+ * resident blocks = 256x4, 256x3, 512x2, 512x1, 1024x1, 256x2, 384x2, 768x1)
+ * for this solver, e.g. to sweep the layouts as Sec. 4.4 does; a variant whose
+ * cap is below the block (32 N threads) returns TMA_ERR_INVALID_ARG. */
+tma_status tma_set_tuning(tma_solver *s, int32_t variant);
+
 /* The same record for the kernel of tma_rollout_grad, tuned on its first use
  * (tma_rollout_grad or tma_set_move with TMA_MOVE_MALA); *variant is -1 before. */
 tma_status tma_get_grad_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed,

@@ -38,7 +38,7 @@ EXPORTS = [
     "tma_batch_mpc", "tma_batch_results", "tma_batch_latency", "tma_batch_live_steps",
     "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
     "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
-    "tma_resample_to", "tma_move_to", "tma_set_finished", "tma_get_status",
+    "tma_resample_to", "tma_move_to", "tma_set_finished", "tma_get_status", "tma_set_tuning",
 ]
 
 
@@ -139,6 +139,7 @@ def lib():
                 "tma_plant_step": ([vp, vp, st], C.c_int),
                 "tma_get_state": ([vp, P(TmaState), P(u32), st], C.c_int),
                 "tma_set_finished": ([vp, u32, st], C.c_int),
+                "tma_set_tuning": ([vp, i32], C.c_int),
                 "tma_get_status": ([vp, P(i32), P(u32), st], C.c_int),
                 "tma_mpc_run": ([vp, i32, P(TmaState), P(d), st], C.c_int),
                 "tma_get_error": ([vp, P(u32), st], C.c_int),
@@ -489,6 +490,10 @@ def tma_get_state(h, N, stream=None):
     mpc = C.c_uint32()
     _check(lib().tma_get_state(h, arr, C.byref(mpc), _stream(stream)), "tma_get_state")
     return np.array([[a.x, a.y, a.z, a.v, a.chi, a.m] for a in arr]), mpc.value
+
+
+def tma_set_tuning(h, variant):
+    _check(lib().tma_set_tuning(h, int(variant)), "tma_set_tuning")
 
 
 def tma_set_finished(h, mask, stream=None):

@@ -616,6 +616,19 @@ tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int
     return TMA_OK;
 }
 
+tma_status tma_set_tuning(tma_solver *s, int32_t variant)
+{
+    if (!s) return TMA_ERR_INVALID_ARG;
+    int cand[8];
+    const int n = rollout_variants(s->prob.N, cand);
+    for (int c = 0; c < n; ++c)
+        if (cand[c] == variant) {
+            s->rollout_variant = variant;
+            return TMA_OK;
+        }
+    return TMA_ERR_INVALID_ARG;
+}
+
 tma_status tma_get_grad_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed,
                                int32_t *h_variants, float *h_ms)
 {

@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(256) sample_mean_kernel(const float *__restric
 struct Variant {
     int max_threads, min_blocks;
 };
-constexpr Variant kVariants[] = {{256, 4}, {256, 3}, {512, 2}, {512, 1}, {1024, 1}};
+// registers per thread: 64, 85, 64, 128, 64, 128, 85, 85
+constexpr Variant kVariants[] = {{256, 4}, {256, 3}, {512, 2}, {512, 1}, {1024, 1},
+                                 {256, 2}, {384, 2}, {768, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 int rollout_variants(int N, int *out)
@@ -115,6 +117,9 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
     case 1: TMA_ROLLOUT(256, 3); break;
     case 2: TMA_ROLLOUT(512, 2); break;
     case 3: TMA_ROLLOUT(512, 1); break;
+    case 5: TMA_ROLLOUT(256, 2); break;
+    case 6: TMA_ROLLOUT(384, 2); break;
+    case 7: TMA_ROLLOUT(768, 1); break;
     default: TMA_ROLLOUT(1024, 1); break;
     }
 #undef TMA_ROLLOUT

@@ -167,6 +167,38 @@ def test_autotuner_choice_is_valid_and_cached(torch, pkg):
         assert not timed2            # the second solver reused the cached choice
 
 
+@pytest.mark.parametrize("n", [5, 12, 20])
+def test_every_launch_variant_computes_the_same(torch, pkg, n):
+    """The launch-bound variants only change the register budget: forced one
+    by one (as the layout sweep does), they give identical costs; a variant
+    whose block cap is below 32 N threads is refused."""
+    base = S.config5(n_scen=1)[0]
+    rng = _rng(19 + n)
+    ac = S._traffic(rng, n // 2, n - n // 2, ring=45000.0, z_top=9000.0, sep_h=base.sep_h,
+                    sep_v=base.sep_v)
+    p = base.copy(N=n, L=300, M=2, H=30, sep_mode=2)
+    p.aircraft = ac
+    u = torch.from_numpy(S.mild_controls(p, p.L, rng)).cuda()
+    sol = pkg.Solver(p)
+    ref = None
+    ran = 0
+    for v in range(8):
+        try:
+            pkg.tma_set_tuning(sol.h, v)
+        except pkg.TmaError:
+            assert 32 * n > {0: 256, 1: 256, 2: 512, 3: 512, 4: 1024, 5: 256, 6: 384, 7: 768}[v]
+            continue
+        c, cs = sol.rollout_cost(u, 1, soft=True)
+        out = (c.cpu().numpy(), cs.cpu().numpy())
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), v
+        ran += 1
+    sol.close()
+    assert ran >= 2
+
+
 def test_rollout_live_steps_counts_flying_aircraft(torch, pkg):
     p = S.config1()
     rng = _rng(18)
