@@ -234,8 +234,9 @@ tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
  * tma_create runs (Sec. 4.4 sweeps thread/block layouts by hand; here every
  * valid launch-bound variant -- block-size cap and minimum resident blocks --
  * is timed on the solver's own workload and the fastest kept; the choice is
- * cached per device and aircraft count).  *n_timed is 0 when the choice came
- * from the cache; h_variants/h_ms (up to 8 entries, may be NULL) receive the
+ * cached per device, aircraft count, problem kind and workload size class).
+ * *n_timed is 0 when the choice came from the cache; h_variants/h_ms (up to 8
+ * entries, may be NULL) receive the
  * candidates and their mean time per rollout in ms. */
 tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int32_t *h_variants,
                           float *h_ms);

@@ -426,8 +426,14 @@ static std::string tune_key(const tma_solver *s)
     cudaDeviceProp prop;
     char key[320];
     if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) prop.name[0] = 0;
-    snprintf(key, sizeof key, "%s|N=%d|pop=%d|wind=%d", prop.name, s->prob.N, s->prob.pop_n[0] > 0,
-             s->prob.wind_mode);
+    // the workload's size class: tiles of the tuning launch (32 particles x one
+    // wind sample each, at most 8192 particles), by power of two -- a small
+    // solver's choice is not reused for a large one
+    const long long tiles = (std::min<long long>(s->prob.L, 8192) + 31) / 32 * (long long)s->prob.M;
+    int lg = 0;
+    while ((2LL << lg) <= tiles) ++lg;
+    snprintf(key, sizeof key, "%s|N=%d|pop=%d|wind=%d|rolling=%d|sep=%d|tiles=2^%d", prop.name,
+             s->prob.N, s->prob.pop_n[0] > 0, s->prob.wind_mode, s->prob.rolling, s->prob.sep_mode, lg);
     return key;
 }
 
@@ -702,8 +708,8 @@ static tma_status gen_wind(tma_solver *s, cudaStream_t st);
 
 // Choose the rollout kernel's launch-bound variant by timing every valid
 // candidate on this solver's workload (uniform initial controls, at most 8192
-// particles, all wind samples); the choice is cached per device and aircraft
-// count for the life of the process.
+// particles, all wind samples); the choice is cached per device, aircraft
+// count, problem kind and workload size class for the life of the process.
 static tma_status autotune_rollout(tma_solver *s)
 {
     int cand[8];
