@@ -805,13 +805,15 @@ def run_layout_sweep(args, local):
     ac["t_enter"] = 5
     p = base.copy(N=10, aircraft=ac, L=10240, H=6, rolling=1, mpc_step=0)
     names = {0: "256x4", 1: "256x3", 2: "512x2", 3: "512x1", 4: "1024x1", 5: "256x2",
-             6: "384x2", 7: "768x1"}
-    regs = {0: 64, 1: 85, 2: 64, 3: 128, 4: 64, 5: 128, 6: 85, 7: 85}
+             6: "384x2", 7: "768x1", 8: "pair 256x3", 9: "pair 256x2", 10: "pair 384x2",
+             11: "pair 512x1", 12: "pair 768x1"}
+    regs = {0: 64, 1: 85, 2: 64, 3: 128, 4: 64, 5: 128, 6: 85, 7: 85, 8: 85, 9: 128, 10: 85,
+            11: 128, 12: 85}
     stream = torch.cuda.current_stream()
     n_steps = args.mpc_steps if args.mpc_steps > 6 else 9
     rows = []
     auto = None
-    for v in range(8):
+    for v in range(13):
         sol = pkg.Solver(p)
         if auto is None:
             auto = pkg.tma_get_tuning(sol.h)[0]

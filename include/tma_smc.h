@@ -235,16 +235,22 @@ tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
  * valid launch-bound variant -- block-size cap and minimum resident blocks --
  * is timed on the solver's own workload and the fastest kept; the choice is
  * cached per device, aircraft count, problem kind and workload size class).
- * *n_timed is 0 when the choice came from the cache; h_variants/h_ms (up to 8
+ * *n_timed is 0 when the choice came from the cache; h_variants/h_ms (up to 16
  * entries, may be NULL) receive the
  * candidates and their mean time per rollout in ms. */
 tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int32_t *h_variants,
                           float *h_ms);
 
-/* Force the rollout kernel's launch variant (0-7: block-size cap x minimum
- * resident blocks = 256x4, 256x3, 512x2, 512x1, 1024x1, 256x2, 384x2, 768x1)
- * for this solver, e.g. to sweep the layouts as Sec. 4.4 does; a variant whose
- * cap is below the block (32 N threads) returns TMA_ERR_INVALID_ARG. */
+/* Force the rollout kernel's launch variant for this solver, e.g. to sweep
+ * the layouts as Sec. 4.4 does.  0-7: one wind sample per thread, block-size
+ * cap x minimum resident blocks = 256x4, 256x3, 512x2, 512x1, 1024x1, 256x2,
+ * 384x2, 768x1.  8-12: two wind samples per thread (m and m + ceil(M/2); the
+ * wind-independent part of each step -- limits, drag, thrust, fuel, altitude,
+ * airspeed, heading -- computed once for both), 256x3, 256x2, 384x2, 512x1,
+ * 768x1; only for the shared wind field (wind mode 0) without the rolling
+ * window and M >= 2.  Every variant returns the same bits.  A variant whose cap
+ * is below the block (32 N threads) or that does not apply to the problem
+ * returns TMA_ERR_INVALID_ARG. */
 tma_status tma_set_tuning(tma_solver *s, int32_t variant);
 
 /* The same record for the kernel of tma_rollout_grad, tuned on its first use

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBPATH = os.path.join(LIBDIR, "libtma_smc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["wind.cu", "rollout.cu", "adjoint.cu", "mala.cu", "resample.cu", "move.cu", "select.cu",
+SOURCES = ["wind.cu", "rollout.cu", "rollout_pair.cu", "adjoint.cu", "mala.cu", "resample.cu", "move.cu", "select.cu",
            "batch.cu", "host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Every CUDA translation unit: single-precision square roots and divisions by

@@ -625,8 +625,8 @@ tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int
 tma_status tma_set_tuning(tma_solver *s, int32_t variant)
 {
     if (!s) return TMA_ERR_INVALID_ARG;
-    int cand[8];
-    const int n = rollout_variants(s->prob.N, cand);
+    int cand[kMaxRolloutVariants];
+    const int n = rollout_variants(s->P, cand);
     for (int c = 0; c < n; ++c)
         if (cand[c] == variant) {
             s->rollout_variant = variant;
@@ -712,8 +712,8 @@ static tma_status gen_wind(tma_solver *s, cudaStream_t st);
 // count, problem kind and workload size class for the life of the process.
 static tma_status autotune_rollout(tma_solver *s)
 {
-    int cand[8];
-    const int nc = rollout_variants(s->prob.N, cand);
+    int cand[kMaxRolloutVariants];
+    const int nc = rollout_variants(s->P, cand);
     s->rollout_variant = cand[0];
     s->n_tuned = 0;
     if (nc <= 1) return TMA_OK;

@@ -70,11 +70,14 @@ constexpr Variant kVariants[] = {{256, 4}, {256, 3}, {512, 2}, {512, 1}, {1024, 
                                  {256, 2}, {384, 2}, {768, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-int rollout_variants(int N, int *out)
+int rollout_variants(const ProblemC &P, int *out)
 {
     int n = 0;
     for (int v = 0; v < kNumVariants; ++v)
-        if (kVariants[v].max_threads >= N * kPB) out[n++] = v;
+        if (kVariants[v].max_threads >= P.N * kPB) out[n++] = v;
+    int pv[kMaxRolloutVariants];
+    const int np = rollout_pair_variants(P, pv);
+    for (int c = 0; c < np; ++c) out[n++] = kPairVariantBase + pv[c];
     return n;
 }
 
@@ -83,9 +86,17 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
                            unsigned long long *live, cudaStream_t st, int variant)
 {
     if (L <= 0) return cudaSuccess;
+    if (variant >= kPairVariantBase) {
+        int pv[kMaxRolloutVariants];
+        const int np = rollout_pair_variants(P, pv);
+        for (int c = 0; c < np; ++c)
+            if (pv[c] == variant - kPairVariantBase)
+                return launch_rollout_pair(P, dyn, u, W, L, J, cost_ms, cost_ms_soft, live, st, pv[c]);
+        variant = -1;                  // not valid for this problem: the one-sample kernel
+    }
     if (variant < 0 || variant >= kNumVariants || kVariants[variant].max_threads < P.N * kPB) {
-        int cand[kNumVariants];
-        rollout_variants(P.N, cand);
+        int cand[kMaxRolloutVariants];
+        rollout_variants(P, cand);
         variant = cand[0];
     }
     const long long nLb = (L + kPB - 1) / kPB;

@@ -14,6 +14,8 @@ namespace tma {
 
 constexpr int kMaxN = TMA_MAX_AIRCRAFT;
 constexpr int kTileParticles = 32;   // particles per rollout tile (one warp per aircraft)
+constexpr int kPairVariantBase = 8;  // first rollout variant index of the two-sample kernel
+constexpr int kMaxRolloutVariants = 16;
 
 // Per-aircraft constants in FP32 (derived on the host in FP64).
 struct AircraftC {
@@ -106,9 +108,16 @@ cudaError_t launch_wind_gemm(const WindC &w, const float *Lxy, int lda, const fl
 cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
                            int64_t L, int J, float *cost_ms, float *cost_ms_soft,
                            unsigned long long *live, cudaStream_t st, int variant);
-// Launch-bound variants of the rollout kernel valid for N aircraft (indices
-// into the variant table); returns their number (at least 1).
-int rollout_variants(int N, int *out);
+// Launch-bound variants of the rollout kernel valid for the problem (indices
+// into the variant table: 0-7 the one-sample kernel, kPairVariantBase + v the
+// two-sample kernel of rollout_pair.cu); returns their number (at least 1).
+int rollout_variants(const ProblemC &P, int *out);
+// The two-sample kernel (shared wind field, no rolling window, M >= 2): its
+// variants valid for the problem (0-based) and its launcher.
+int rollout_pair_variants(const ProblemC &P, int *out);
+cudaError_t launch_rollout_pair(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
+                                int64_t L, int J, float *cost_ms, float *cost_ms_soft,
+                                unsigned long long *live, cudaStream_t st, int variant);
 cudaError_t launch_sample_mean(const float *cost_ms, int64_t L, int M, int N, float *cbar,
                                cudaStream_t st);
 
@@ -265,8 +274,8 @@ struct tma_solver {
     // autotuned launch variant of the rollout kernel and the timings behind it
     int rollout_variant = -1;
     int n_tuned = 0;
-    int tuned_variant[8] = {0};
-    float tuned_ms[8] = {0};
+    int tuned_variant[tma::kMaxRolloutVariants] = {0};
+    float tuned_ms[tma::kMaxRolloutVariants] = {0};
 };
 
 struct tma_batch {

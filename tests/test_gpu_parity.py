@@ -169,9 +169,10 @@ def test_autotuner_choice_is_valid_and_cached(torch, pkg):
 
 @pytest.mark.parametrize("n", [5, 12, 20])
 def test_every_launch_variant_computes_the_same(torch, pkg, n):
-    """The launch-bound variants only change the register budget: forced one
-    by one (as the layout sweep does), they give identical costs; a variant
-    whose block cap is below 32 N threads is refused."""
+    """The launch-bound variants only change the register budget (0-7) or give
+    each thread two wind samples (8-12): forced one by one (as the layout sweep
+    does), they give identical costs; a variant whose block cap is below 32 N
+    threads is refused."""
     base = S.config5(n_scen=1)[0]
     rng = _rng(19 + n)
     ac = S._traffic(rng, n // 2, n - n // 2, ring=45000.0, z_top=9000.0, sep_h=base.sep_h,
@@ -182,11 +183,13 @@ def test_every_launch_variant_computes_the_same(torch, pkg, n):
     sol = pkg.Solver(p)
     ref = None
     ran = 0
-    for v in range(8):
+    caps = {0: 256, 1: 256, 2: 512, 3: 512, 4: 1024, 5: 256, 6: 384, 7: 768,
+            8: 256, 9: 256, 10: 384, 11: 512, 12: 768}
+    for v in range(13):
         try:
             pkg.tma_set_tuning(sol.h, v)
         except pkg.TmaError:
-            assert 32 * n > {0: 256, 1: 256, 2: 512, 3: 512, 4: 1024, 5: 256, 6: 384, 7: 768}[v]
+            assert 32 * n > caps[v]
             continue
         c, cs = sol.rollout_cost(u, 1, soft=True)
         out = (c.cpu().numpy(), cs.cpu().numpy())
@@ -401,3 +404,46 @@ def test_solve_quality_matches_oracle_statistically(torch, pkg):
     gpu, orc = np.array(gpu), np.array(orc)
     assert np.isfinite(gpu).all() and np.isfinite(orc).all()
     assert abs(np.median(gpu) - np.median(orc)) <= 0.1 * np.median(orc), (gpu, orc)
+
+
+@pytest.mark.parametrize("case", ["c1", "c2", "c3", "c4", "odd_M", "M2_L1"])
+def test_two_sample_kernel_matches_one_sample_kernel(torch, pkg, case):
+    """The two-sample kernel (variants 8-12: samples m and m + ceil(M/2) per
+    thread, the wind-independent part of each step computed once) performs
+    the one-sample kernel's operations in the same order: per-sample costs,
+    soft costs and live aircraft-steps are the same bits.  Odd M leaves the
+    last thread pair with one sample."""
+    cfg = {"c1": S.config1(),
+           "c2": S.shrink(S.config2(), L=700, M=6),
+           "c3": S.shrink(S.config3(), L=96, M=4),
+           "c4": S.shrink(S.config4(), L=500, M=4),
+           "odd_M": S.config1().copy(M=5, L=333),
+           "M2_L1": S.config1().copy(M=2, L=1)}[case]
+    rng = _rng(31)
+    u = torch.from_numpy(S.mild_controls(cfg, cfg.L, rng)).cuda()
+    u[: cfg.L // 3] = torch.from_numpy(S.random_controls(cfg, cfg.L // 3, rng)).cuda()
+    soft = cfg.sep_mode != 0
+    sol = pkg.Solver(cfg)
+    outs = {}
+    for v in range(13):
+        try:
+            pkg.tma_set_tuning(sol.h, v)
+        except pkg.TmaError:
+            continue
+        c, cs = sol.rollout_cost(u, 2, soft=soft)
+        live = sol.live_steps()
+        samp = sol.sample_costs(cfg.L).cpu().numpy()
+        samp_s = sol.sample_costs(cfg.L, soft=True).cpu().numpy() if soft else None
+        outs[v] = (c.cpu().numpy(), None if cs is None else cs.cpu().numpy(), samp, samp_s, live)
+    sol.close()
+    single = [v for v in outs if v < 8]
+    pair = [v for v in outs if v >= 8]
+    assert single and pair, sorted(outs)
+    ref = outs[single[0]]
+    for v in pair:
+        got = outs[v]
+        assert np.array_equal(got[0], ref[0]), (case, v, "cbar")
+        assert np.array_equal(got[2], ref[2]), (case, v, "per-sample costs")
+        if soft:
+            assert np.array_equal(got[1], ref[1]) and np.array_equal(got[3], ref[3]), (case, v, "soft")
+        assert got[4] == ref[4], (case, v, "live steps")
