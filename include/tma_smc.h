@@ -449,6 +449,21 @@ tma_status tma_resample_to(const double *d_wtilde, int32_t nseg, int64_t L, int6
                            uint64_t seed, uint32_t scenario_id, uint32_t J, uint32_t mpc_step,
                            int32_t *d_anc, void *d_work, size_t work_bytes, tma_stream_t stream);
 
+/* The annealed weights and the resampling of one SMC iteration in one
+ * stream-ordered call (Sec. 3.6-3.7; the stages between two rollouts of
+ * Algorithm 1): d_wtilde as tma_lse, then d_anc as tma_resample with L_out
+ * ancestors, the resampling's chunk sums of q formed by the pass that writes
+ * wtilde (one read of wtilde less than the two calls).  Neither synchronises:
+ * when d_degenerate (device int32, caller-owned, may be NULL) is given, bit 0
+ * is set there if a segment had Q = 0 (the caller zeroes it).  Scratch: d_work
+ * of tma_lse_resample_workspace(nseg, L) bytes; other arguments and errors as
+ * tma_lse and tma_resample_to. */
+size_t tma_lse_resample_workspace(int32_t nseg, int64_t L);
+tma_status tma_lse_resample(const float *d_cbar, int32_t nseg, int64_t L, int64_t L_out, double kappa,
+                            uint64_t seed, uint32_t scenario_id, uint32_t J, uint32_t mpc_step,
+                            double *d_wtilde, int32_t *d_anc, uint32_t *d_degenerate, void *d_work,
+                            size_t work_bytes, tma_stream_t stream);
+
 /* Final selection (Sec. 3.8): over particles l < L, the fewest aircraft with
  * infinite cost, then the smallest sum_i (double)cbar[i][l] summed in order
  * i = 0..N-1, ties to the lowest l.  Writes d_best (int64), d_best_sum (double;

@@ -39,6 +39,7 @@ EXPORTS = [
     "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
     "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
     "tma_resample_to", "tma_move_to", "tma_set_finished", "tma_get_status", "tma_set_tuning",
+    "tma_lse_resample_workspace", "tma_lse_resample",
 ]
 
 
@@ -131,6 +132,9 @@ def lib():
                 "tma_resample_workspace": ([i32, i64], sz),
                 "tma_resample": ([vp, i32, i64, u64, u32, u32, u32, vp, vp, sz, st], C.c_int),
                 "tma_resample_to": ([vp, i32, i64, i64, u64, u32, u32, u32, vp, vp, sz, st], C.c_int),
+                "tma_lse_resample_workspace": ([i32, i64], sz),
+                "tma_lse_resample": ([vp, i32, i64, i64, d, u64, u32, u32, u32, vp, vp, vp, vp, sz, st],
+                                     C.c_int),
                 "tma_select_workspace": ([i64], sz),
                 "tma_select": ([vp, i32, i64, vp, vp, vp, vp, sz, st], C.c_int),
                 "tma_profile_enable": ([vp, C.c_int], C.c_int),
@@ -614,6 +618,21 @@ def tma_resample_to(wtilde, seed, scenario_id, J, mpc_step, anc, work=None, stre
                                         int(mpc_step), _dptr(anc), _dptr(work), work.numel(),
                                         _stream(stream)),
                   "tma_resample_to", allow=(TMA_OK, TMA_WARN_DEGENERATE))
+
+
+def tma_lse_resample(cbar, kappa, seed, scenario_id, J, mpc_step, wtilde, anc, degenerate=None,
+                     work=None, stream=None):
+    """cbar: cuda float32 [nseg][L] -> wtilde float64 [nseg][L] and anc int32
+    [nseg][L_out] (L_out = anc.shape[1]) in one stream-ordered call; bit 0 of
+    degenerate (cuda int32 [1], zeroed by the caller) marks an all-zero segment."""
+    nseg, L = cbar.shape
+    need = lib().tma_lse_resample_workspace(nseg, L)
+    if work is None:
+        work = _workspace(need, cbar.device)
+    _check(lib().tma_lse_resample(_dptr(cbar), nseg, L, anc.shape[1], float(kappa),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(scenario_id), int(J),
+                                  int(mpc_step), _dptr(wtilde), _dptr(anc), _dptr(degenerate),
+                                  _dptr(work), work.numel(), _stream(stream)), "tma_lse_resample")
 
 
 def tma_resample_noalloc(wtilde, seed, scenario_id, J, mpc_step, anc, stream=None):

@@ -409,6 +409,9 @@ static ProblemC problem_at(const tma_solver *s, int J)
     return P;
 }
 
+// the resampling's part of the solver's workspace (after the LSE's)
+static void *res_work(const tma_solver *s) { return static_cast<char *>(s->d_work) + s->lse_work_bytes; }
+
 // device address of DynState::mpc_step (pointer arithmetic only)
 static const uint32_t *dyn_mpc(const tma_solver *s)
 {
@@ -556,8 +559,10 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
         if (p.sep_mode != 0 && (e = alloc(&s->d_cbar_soft, L * N * 4))) return fail(e);
         if ((e = alloc(&s->d_wtilde, L * N * 8))) return fail(e);
         if ((e = alloc(&s->d_anc, L * N * 4))) return fail(e);
-        s->work_bytes = std::max({lse_workspace(p.N, p.L), resample_workspace(p.N, p.L),
-                                  select_workspace(p.L)});
+        // the LSE's and the resampling's workspaces side by side: the LSE pass
+        // writes the resampling's chunk sums
+        s->lse_work_bytes = (lse_workspace(p.N, p.L) + 255) / 256 * 256;
+        s->work_bytes = std::max(s->lse_work_bytes + resample_workspace(p.N, p.L), select_workspace(p.L));
         if ((e = alloc(&s->d_work, s->work_bytes))) return fail(e);
         if ((e = alloc(&s->d_best, 8))) return fail(e);
         if ((e = alloc(&s->d_best_sum, 8))) return fail(e);
@@ -1244,12 +1249,13 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
             {
                 StageTimer t(s, 4, st);
                 TMA_CUDA(launch_lse(cb, p.N, Lj, exponent_of(p, J), s->d_wtilde, nullptr, nullptr,
-                                    s->d_work, st));
+                                    s->d_work, st, resample_partials(res_work(s))));
             }
             {
                 StageTimer t(s, 5, st);
                 TMA_CUDA(launch_resample(s->d_wtilde, p.N, Lj, Ln, s->P.key0, s->P.key1, (uint32_t)J,
-                                         dyn_mpc(s), 0u, s->d_anc, s->d_work, s->d_flags, st));
+                                         dyn_mpc(s), 0u, s->d_anc, res_work(s), s->d_flags, st, nullptr,
+                                         nullptr, true));
             }
             {
                 StageTimer t(s, 6, st);
@@ -1396,6 +1402,34 @@ tma_status tma_resample_to(const double *d_wtilde, int32_t nseg, int64_t L, int6
     TMA_CUDA(cudaMemcpyAsync(&h, flags, 4, cudaMemcpyDeviceToHost, st));
     TMA_CUDA(cudaStreamSynchronize(st));
     return (h & 1u) ? TMA_WARN_DEGENERATE : TMA_OK;
+}
+
+size_t tma_lse_resample_workspace(int32_t nseg, int64_t L)
+{
+    if (nseg < 0 || L < 0) return 0;
+    return (lse_workspace(nseg, L) + 255) / 256 * 256 + resample_workspace(nseg, L);
+}
+
+tma_status tma_lse_resample(const float *d_cbar, int32_t nseg, int64_t L, int64_t L_out, double kappa,
+                            uint64_t seed, uint32_t scenario_id, uint32_t J, uint32_t mpc_step,
+                            double *d_wtilde, int32_t *d_anc, uint32_t *d_degenerate, void *d_work,
+                            size_t work_bytes, tma_stream_t stream)
+{
+    if (nseg < 0 || L < 0 || L > TMA_MAX_PARTICLES || L_out < 0 || L_out > TMA_MAX_PARTICLES ||
+        J > 0xFFFF || mpc_step > 0xFFFF || (L == 0) != (L_out == 0) || !(kappa > 0) ||
+        !std::isfinite(kappa))
+        return TMA_ERR_INVALID_ARG;
+    if (nseg == 0 || L == 0) return TMA_OK;
+    if (!d_cbar || !d_wtilde || !d_anc || !d_work || work_bytes < tma_lse_resample_workspace(nseg, L))
+        return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t key = seed + (uint64_t)scenario_id * 0x9E3779B97F4A7C15ull;
+    void *rwork = static_cast<char *>(d_work) + (lse_workspace(nseg, L) + 255) / 256 * 256;
+    TMA_CUDA(launch_lse(d_cbar, nseg, L, kappa, d_wtilde, nullptr, nullptr, d_work, st,
+                        resample_partials(rwork)));
+    TMA_CUDA(launch_resample(d_wtilde, nseg, L, L_out, (uint32_t)key, (uint32_t)(key >> 32), J, nullptr,
+                             mpc_step, d_anc, rwork, d_degenerate, st, nullptr, nullptr, true));
+    return TMA_OK;
 }
 
 size_t tma_select_workspace(int64_t L) { return L < 0 ? 0 : select_workspace(L); }
@@ -1597,10 +1631,11 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
             TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms_soft, b->d_scen, b->d_seg_scen, b->nseg, L,
                                               b->M, Mj, b->d_cbar_soft, st));
         if (J < b->J_max - 1) {
+            void *rwork = static_cast<char *>(b->d_work) + b->lse_work_bytes;
             TMA_CUDA(launch_lse(cb, (int)b->nseg, L, exponent_of(b->probs[0], J), b->d_wtilde, nullptr,
-                                nullptr, b->d_work, st));
+                                nullptr, b->d_work, st, resample_partials(rwork)));
             TMA_CUDA(launch_resample(b->d_wtilde, (int)b->nseg, L, L, 0u, 0u, (uint32_t)J, nullptr, 0u,
-                                     b->d_anc, b->d_work, b->d_flags, st, b->d_segkeys, b->d_dyns));
+                                     b->d_anc, rwork, b->d_flags, st, b->d_segkeys, b->d_dyns, true));
             TMA_CUDA(launch_batch_move(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, L, b->S,
                                        b->d_u[cur], b->d_anc, J, b->d_u[cur ^ 1], st));
             cur ^= 1;
@@ -1771,7 +1806,8 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
         if (b->sep_mode && (e = alloc(&b->d_cbar_soft, nseg * L * 4))) return fail(e);
         if ((e = alloc(&b->d_wtilde, nseg * L * 8))) return fail(e);
         if ((e = alloc(&b->d_anc, nseg * L * 4))) return fail(e);
-        if ((e = alloc(&b->d_work, std::max(lse_workspace((int)nseg, L), resample_workspace((int)nseg, L)))))
+        b->lse_work_bytes = (lse_workspace((int)nseg, L) + 255) / 256 * 256;
+        if ((e = alloc(&b->d_work, b->lse_work_bytes + resample_workspace((int)nseg, L))))
             return fail(e);
         if ((e = alloc(&b->d_best, 8 * (size_t)n_scen))) return fail(e);
         if ((e = alloc(&b->d_best_sum, 8 * (size_t)n_scen))) return fail(e);

@@ -9,16 +9,20 @@
 //             kappa > 0 is monotone), writes wtilde = exp(-kappa c - lmax) in
 //             FP64 and a chunk partial sum; (3) the partial sums are added in
 //             chunk order into wsum.
-//   Resample: (1) chunk sums of q = floor(wtilde 2^40) (uint64, exact);
-//             (2) every block forms its chunk's inclusive prefix S_j in shared
-//             memory, finds the range of particles l whose threshold
-//             t_l = floor((l 2^32 + r) Q / (Lout 2^32)) falls in the chunk, and
-//             assigns a_l = min{j : S_j > t_l} by binary search.  Because
-//             S_j > floor(y) <=> S_j > y for integer S_j, both searches compare
-//             128-bit products S_j * Lout 2^32 against (l 2^32 + r) * Q and need
-//             no division.  Integer arithmetic makes the result independent of
-//             the summation order.  Lout ancestors are drawn from the Lin weighted
-//             particles of the segment (Lout = Lin for a fixed particle count).
+//   Resample: (1) chunk sums of q = floor(wtilde 2^40) (uint64, exact), by
+//             their own pass or by the LSE pass that writes wtilde;
+//             (2) every block forms its chunk's inclusive prefix S_j, and for
+//             every j the number n_j of particles l whose threshold
+//             t_l = floor((l 2^32 + r) Q / (Lout 2^32)) lies below S_j; the
+//             particles of the chunk are l in [n_(before), n_(last)) and
+//             a_l = min{j : S_j > t_l} = min{j : n_j > l}, a binary search over
+//             the 32-bit counts in shared memory.  Because S_j > floor(y) <=>
+//             S_j > y for integer S_j, a count is settled by comparing 128-bit
+//             products (l 2^32 + r) Q against S_j Lout 2^32 (no division); an
+//             FP32 estimate within one of the count says which l to compare.
+//             Integer arithmetic makes the result independent of the summation
+//             order.  Lout ancestors are drawn from the Lin weighted particles
+//             of the segment (Lout = Lin for a fixed particle count).
 #include <cfloat>
 #include <mutex>
 
@@ -33,8 +37,6 @@ constexpr int kThreads = 256;
 constexpr int kPer = 8;
 constexpr int kChunk = kThreads * kPer;  // 2048
 
-// padded shared-memory index of chunk element j (one extra word per 16)
-__device__ __forceinline__ int spad(int j) { return j + (j >> 4); }
 
 // q = floor(w 2^40) for w in (0, 1); w >= 1 (and +inf) counts as 2^40; NaN,
 // zero, subnormals and negative values as 0.  Scaling by a power of two is
@@ -104,13 +106,17 @@ __global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restric
     if (threadIdx.x == 0) cmin[(size_t)s * nchunk + c] = mn;
 }
 
+// Writes wtilde; csum (chunk sums of wtilde, fixed order) and cq (chunk sums
+// of q = floor(wtilde 2^40) for the resampling) when given.
 __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cbar, long long L,
                                                     int nchunk, double kappa,
                                                     const float *__restrict__ cmin,
                                                     double *__restrict__ wtilde,
-                                                    double *__restrict__ csum)
+                                                    double *__restrict__ csum,
+                                                    unsigned long long *__restrict__ cq)
 {
     __shared__ float shf[32];
+    __shared__ unsigned long long shq[32];
     const int s = blockIdx.y, c = blockIdx.x;
     float mn = __int_as_float(0x7f800000);
     for (int j = threadIdx.x; j < nchunk; j += kThreads) mn = fminf(mn, cmin[(size_t)s * nchunk + j]);
@@ -121,6 +127,7 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
     double *out = wtilde + (size_t)s * L;
     const long long base = (long long)c * kChunk;
     double acc = 0.0;
+    unsigned long long qacc = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const long long idx = base + threadIdx.x + j * kThreads;
@@ -130,8 +137,14 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
             if (any && !isinf(v) && !isnan(v)) w = exp(-kappa * (double)v - lmax);
             out[idx] = w;
             acc += w;
+            qacc += qfix(w);
         }
     }
+    if (cq) {
+        qacc = block_reduce(qacc, AddU64(), shq, 0ull);
+        if (threadIdx.x == 0) cq[(size_t)s * nchunk + c] = qacc;
+    }
+    if (!csum) return;
     // fixed-order block sum: per-thread partials through shared memory
     __shared__ double part[kThreads];
     part[threadIdx.x] = acc;
@@ -187,21 +200,82 @@ __global__ void __launch_bounds__(kThreads) res_chunk_sum(const double *__restri
     if (threadIdx.x == 0) cq[(size_t)s * nchunk + c] = acc;
 }
 
-// number of particles l in [0, L) with (l 2^32 + r) Q < X D, D = L 2^32
-__device__ long long count_below(unsigned long long X, unsigned long long Q, unsigned long long D,
-                                 uint32_t r, long long L)
+// a * b for a < 2^64, b < 2^32 (exact, 128-bit)
+__device__ __forceinline__ U128 mul64x32(unsigned long long a, uint32_t b)
 {
-    const U128 rhs = mul64x64(X, D);
-    long long lo = 0, hi = L;  // answer in [lo, hi]
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        const U128 lhs = mul64x64(((unsigned long long)mid << 32) + r, Q);
-        if (lt128(lhs, rhs)) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
+    const uint32_t alo = (uint32_t)a, ahi = (uint32_t)(a >> 32);
+    const unsigned long long lo = (unsigned long long)alo * b;   // 32 x 32 -> 64
+    const unsigned long long hi = (unsigned long long)ahi * b;
+    const unsigned long long rlo = lo + (hi << 32);
+    return U128{(hi >> 32) + (rlo < lo ? 1ull : 0ull), rlo};
 }
 
+__device__ __forceinline__ U128 add64(U128 a, unsigned long long b)
+{
+    const unsigned long long lo = a.lo + b;
+    return U128{a.hi + (lo < b ? 1ull : 0ull), lo};
+}
+
+// The thresholds of a segment.  With r Q = Rhi 2^32 + Rlo (Rlo < 2^32),
+//   t_l = floor((l 2^32 + r) Q / (Lout 2^32)) = floor((l Q + Rhi) / Lout)
+// (the multiple l Q 2^32 leaves the inner floor exact), and for an integer S
+//   S > t_l  <=>  S Lout > X_l = l Q + Rhi,
+// so a threshold is never formed: X_l steps by Q from particle to particle,
+// and S_j Lout is compared against it in 128-bit integers (no division; the
+// products stay below 2^85 for Q < 2^62 and Lout <= 2^22).
+struct Thresholds {
+    unsigned long long Q, Rhi;
+    uint32_t Lout;
+    float ratio;          // Lout / Q
+    float shift;          // r 2^-32
+};
+
+// a 64-bit value as FP32 (relative error 2^-23 at most)
+__device__ __forceinline__ float u64_to_float(unsigned long long v)
+{
+    return fmaf(__uint2float_rn((uint32_t)(v >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)v));
+}
+
+// S above particle l's threshold: S Lout > l Q + Rhi
+__device__ __forceinline__ bool above(const U128 &SL, unsigned long long Q, unsigned long long Rhi, int l)
+{
+    return lt128(add64(mul64x32(Q, (uint32_t)l), Rhi), SL);
+}
+
+// Number of particles l in [0, Lout) whose threshold lies below S (S Lout >
+// l Q + Rhi): the condition holds up to the count and fails beyond.  The FP32
+// estimate S Lout / Q - r 2^-32 has a relative error below 2^-22, so for
+// Lout <= 2^21 it lies within 1/2 of the count's real bound; with
+// n0 = ceil(estimate) the count is n0 - 1, n0 or n0 + 1, told apart by the
+// exact conditions at n0 - 1 and n0.  Larger Lout steps from n0 until both
+// conditions agree with the count.
+__device__ __forceinline__ int count_below(unsigned long long S, const Thresholds &T)
+{
+    const U128 SL = mul64x32(S, T.Lout);
+    const float est = fminf(fmaxf(fmaf(u64_to_float(S), T.ratio, -T.shift), 0.0f), (float)T.Lout);
+    int n = __float2int_ru(est);
+    if (T.Lout <= (1u << 21)) {
+        const bool below_prev = n > 0 && above(SL, T.Q, T.Rhi, n - 1);
+        const bool below_n = n < (int)T.Lout && above(SL, T.Q, T.Rhi, n);
+        return n - (n > 0 && !below_prev ? 1 : 0) + (below_n ? 1 : 0);
+    }
+    while (n < (int)T.Lout && above(SL, T.Q, T.Rhi, n)) ++n;
+    while (n > 0 && !above(SL, T.Q, T.Rhi, n - 1)) --n;
+    return n;
+}
+
+constexpr int kWin = 4096;                 // ancestors written per window
+constexpr int kWinPer = kWin / kThreads;   // 16 per thread
+// one padding word per 32: a thread's 16 consecutive entries fall in
+// distinct banks across the warp
+__device__ __forceinline__ int wpad(int k) { return k + (k >> 5); }
+
+// Copies of element j are the particles [n_(j-1), n_j), n_j the number of
+// thresholds below S_j.  Every element's count is formed independently (eight
+// per thread, no chain between them); the chunk's particles [lo, hi) are
+// then written in windows of kWin: each element with copies marks its first
+// particle with j + 1, a running maximum over the window fills in the rest,
+// and the window goes out with coalesced stores.
 __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict__ wtilde, long long L,
                                                        long long Lout, int nchunk,
                                                        const unsigned long long *__restrict__ cq,
@@ -212,41 +286,63 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
                                                        const SegKey *__restrict__ seg_keys,
                                                        const DynState *__restrict__ dyns)
 {
-    // S_j * D of the chunk (128-bit, hi and lo words), padded; the chunk's last S_j
-    __shared__ unsigned long long SDh[kChunk + kChunk / 16], SDl[kChunk + kChunk / 16];
-    __shared__ unsigned long long s_last;
+    __shared__ int win[kWin + kWin / 32];              // padded: wpad(k)
+    __shared__ int lastc[kThreads];
+    __shared__ int wmax[kThreads / 32];
     __shared__ unsigned long long wtot[kThreads / 32];
-    __shared__ unsigned long long sh[32];
-    __shared__ long long range[2];
+    __shared__ unsigned long long seg_before, seg_total;
+    __shared__ Thresholds Tsh;
+    __shared__ int n_before;
     const int s = blockIdx.y, c = blockIdx.x;
     const long long base = (long long)c * kChunk;
     const int len = (int)min((long long)kChunk, L - base);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
-    // offset of this chunk and the segment total (integer, order-free)
-    unsigned long long before = 0, total = 0;
-    for (int j = threadIdx.x; j < nchunk; j += kThreads) {
-        const unsigned long long v = cq[(size_t)s * nchunk + j];
-        total += v;
-        if (j < c) before += v;
-    }
-    before = block_reduce(before, AddU64(), sh, 0ull);
-    total = block_reduce(total, AddU64(), sh, 0ull);
-    int32_t *a = anc + (size_t)s * Lout;
-
-    if (total == 0) {
-        // degenerate segment: ancestors floor(l L / Lout) spread evenly (the
-        // identity when Lout = L); this chunk writes the l that map into it
-        const long long l0 = (base * Lout + L - 1) / L, l1 = ((base + len) * Lout + L - 1) / L;
-        for (long long l = l0 + threadIdx.x; l < l1; l += kThreads) a[l] = (int32_t)(l * L / Lout);
-        if (c == 0 && threadIdx.x == 0 && flags) atomicOr(flags, 1u);
-        return;
+    if (wid == 0) {
+        // the segment's bookkeeping, while the other warps load and scan: the
+        // chunk's offset and the segment total (integer, order-free), the
+        // uniform, the thresholds, the count below the chunk's start
+        unsigned long long before = 0, total = 0;
+        for (int j = lane; j < nchunk; j += 32) {
+            const unsigned long long v = cq[(size_t)s * nchunk + j];
+            total += v;
+            if (j < c) before += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            total += __shfl_xor_sync(0xffffffffu, total, o);
+        }
+        if (lane == 0) {
+            seg_before = before;
+            seg_total = total;
+            if (total != 0) {
+                uint32_t r;
+                if (seg_keys) {
+                    // batched: the segment's scenario key and aircraft index, its scenario's MPC step
+                    const SegKey sk = seg_keys[s];
+                    r = draw(sk.key0, sk.key1, 0u, sk.c1, 0u, 2u, J, dyns[sk.scen].mpc_step).x;
+                } else {
+                    const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
+                    r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
+                }
+                Thresholds T;
+                T.Q = total;
+                const U128 rQ = mul64x32(total, r);
+                T.Rhi = (rQ.hi << 32) | (rQ.lo >> 32);     // floor(r Q / 2^32) < 2^62
+                T.Lout = (uint32_t)Lout;
+                T.ratio = __fdiv_rn((float)(uint32_t)Lout, u64_to_float(total));
+                T.shift = (float)r * 2.3283064365386963e-10f;
+                Tsh = T;
+                n_before = count_below(before, T);
+            }
+        }
     }
 
     // inclusive prefix of q over the chunk: every thread loads its kPer
-    // consecutive values (16-byte loads where aligned), scans them in registers;
-    // warp scan of the thread totals, block scan of the warp totals.  The chunk's
-    // prefix goes to shared memory padded by one word per 16 (no bank conflicts)
-    // for the searches.
+    // consecutive values (16-byte loads where aligned; zero past the chunk),
+    // scans them in registers; warp scan of the thread totals, block scan of
+    // the warp totals
     const double *row = wtilde + (size_t)s * L;
     const int j0 = threadIdx.x * kPer;
     unsigned long long qv[kPer];
@@ -268,7 +364,6 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         run += qv[j];
         qv[j] = run;
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long incl = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -277,43 +372,71 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
     }
     if (lane == 31) wtot[wid] = incl;
     __syncthreads();
+    const unsigned long long before = seg_before, total = seg_total;
+    int32_t *a = anc + (size_t)s * Lout;
+    if (total == 0) {
+        // degenerate segment: ancestors floor(l L / Lout) spread evenly (the
+        // identity when Lout = L); this chunk writes the l that map into it
+        const long long l0 = (base * Lout + L - 1) / L, l1 = ((base + len) * Lout + L - 1) / L;
+        for (long long l = l0 + threadIdx.x; l < l1; l += kThreads) a[l] = (int32_t)(l * L / Lout);
+        if (c == 0 && threadIdx.x == 0 && flags) atomicOr(flags, 1u);
+        return;
+    }
     unsigned long long woff = 0;
     for (int w = 0; w < wid; ++w) woff += wtot[w];
     const unsigned long long add = before + woff + (incl - run);
-    // the searches compare thresholds against S_j * D: form the products once
-    const unsigned long long D = (unsigned long long)Lout << 32;
+    const Thresholds T = Tsh;
+    // the counts of this thread's elements, independent of each other (the
+    // elements past the chunk repeat the chunk's last prefix)
+    int nc[kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const unsigned long long S = qv[j] + add;
-        const U128 p = mul64x64(S, D);
-        SDh[spad(j0 + j)] = p.hi;
-        SDl[spad(j0 + j)] = p.lo;
-        if (j0 + j == len - 1) s_last = S;
-    }
+    for (int j = 0; j < kPer; ++j) nc[j] = count_below(qv[j] + add, T);
+    lastc[threadIdx.x] = nc[kPer - 1];
     __syncthreads();
+    const int lo = n_before, hi = lastc[kThreads - 1];
+    const int nprev0 = threadIdx.x == 0 ? lo : lastc[threadIdx.x - 1];
 
-    uint32_t r;
-    if (seg_keys) {
-        // batched: the segment's scenario key and aircraft index, its scenario's MPC step
-        const SegKey sk = seg_keys[s];
-        r = draw(sk.key0, sk.key1, 0u, sk.c1, 0u, 2u, J, dyns[sk.scen].mpc_step).x;
-    } else {
-        const uint32_t mpc = d_mpc ? *d_mpc : mpc_host;
-        r = draw(key0, key1, 0u, (uint32_t)s, 0u, 2u, J, mpc).x;
-    }
-    if (threadIdx.x == 0) range[0] = count_below(before, total, D, r, Lout);
-    if (threadIdx.x == 32) range[1] = count_below(s_last, total, D, r, Lout);
-    __syncthreads();
-    const long long lo = range[0], hi = range[1];
-    for (long long l = lo + threadIdx.x; l < hi; l += kThreads) {
-        const U128 target = mul64x64(((unsigned long long)l << 32) + r, total);
-        int jlo = 0, jhi = len - 1;  // smallest j with S_j * D > target
-        while (jlo < jhi) {
-            const int mid = (jlo + jhi) >> 1;
-            if (lt128(target, U128{SDh[spad(mid)], SDl[spad(mid)]})) jhi = mid;
-            else jlo = mid + 1;
+    int carry = 0;
+    for (int w0 = lo; w0 < hi; w0 += kWin) {
+        const int wl = min(kWin, hi - w0);
+        for (int k = threadIdx.x; k < wl; k += kThreads) win[wpad(k)] = 0;
+        __syncthreads();
+        int np = nprev0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            if (nc[j] > np && np >= w0 && np < w0 + wl) win[wpad(np - w0)] = j0 + j + 1;
+            np = nc[j];
         }
-        a[l] = (int32_t)(base + jlo);
+        __syncthreads();
+        // inclusive running maximum over the window: 16 entries per thread
+        const int k0 = threadIdx.x * kWinPer;
+        int v[kWinPer];
+        int m = 0;
+#pragma unroll
+        for (int q = 0; q < kWinPer; ++q) {
+            if (k0 + q < wl) m = max(m, win[wpad(k0 + q)]);
+            v[q] = m;
+        }
+        int inc = m;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc = max(inc, t);
+        }
+        if (lane == 31) wmax[wid] = inc;
+        int ex = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) ex = 0;
+        __syncthreads();
+        int pre = carry;
+        for (int w = 0; w < wid; ++w) pre = max(pre, wmax[w]);
+        ex = max(ex, pre);
+#pragma unroll
+        for (int q = 0; q < kWinPer; ++q)
+            if (k0 + q < wl) win[wpad(k0 + q)] = max(v[q], ex);
+        for (int w = 0; w < kThreads / 32; ++w) carry = max(carry, wmax[w]);
+        __syncthreads();
+        for (int k = threadIdx.x; k < wl; k += kThreads) a[w0 + k] = (int32_t)(base + win[wpad(k)] - 1);
+        __syncthreads();
     }
 }
 
@@ -332,8 +455,14 @@ size_t resample_workspace(int nseg, int64_t L)
     return (size_t)nseg * (size_t)n_chunks(L) * sizeof(unsigned long long) + 16;
 }
 
+unsigned long long *resample_partials(void *work)
+{
+    return reinterpret_cast<unsigned long long *>((reinterpret_cast<uintptr_t>(work) + 15) & ~uintptr_t(15));
+}
+
 cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, double *wtilde,
-                       double *lmax, double *wsum, void *work, cudaStream_t st)
+                       double *lmax, double *wsum, void *work, cudaStream_t st,
+                       unsigned long long *cq)
 {
     if (nseg <= 0 || L <= 0) return cudaSuccess;
     const int nc = n_chunks(L);
@@ -343,7 +472,7 @@ cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, dou
         (reinterpret_cast<uintptr_t>(cmin + n) + 15) & ~uintptr_t(15));
     dim3 grid(nc, nseg);
     lse_chunk_min<<<grid, kThreads, 0, st>>>(cbar, L, nc, cmin);
-    lse_exp<<<grid, kThreads, 0, st>>>(cbar, L, nc, kappa, cmin, wtilde, csum);
+    lse_exp<<<grid, kThreads, 0, st>>>(cbar, L, nc, kappa, cmin, wtilde, (lmax || wsum) ? csum : nullptr, cq);
     count_launch(2);
     if (lmax || wsum) {
         lse_finish<<<(nseg + 127) / 128, 128, 0, st>>>(cmin, csum, nseg, nc, kappa, lmax, wsum);
@@ -391,17 +520,19 @@ cudaError_t scratch_address(void **out)
 cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, int64_t Lout, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
                             int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st,
-                            const SegKey *seg_keys, const DynState *dyns)
+                            const SegKey *seg_keys, const DynState *dyns, bool sums_ready)
 {
     if (nseg <= 0 || L <= 0 || Lout <= 0) return cudaSuccess;
     const int nc = n_chunks(L);
-    auto *cq = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(work) + 15) & ~uintptr_t(15));
+    unsigned long long *cq = resample_partials(work);
     dim3 grid(nc, nseg);
-    res_chunk_sum<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq);
+    if (!sums_ready) {
+        res_chunk_sum<<<grid, kThreads, 0, st>>>(wtilde, L, nc, cq);
+        count_launch();
+    }
     res_expand<<<grid, kThreads, 0, st>>>(wtilde, L, Lout, nc, cq, key0, key1, J, d_mpc, mpc_host,
                                           anc, d_flags, seg_keys, dyns);
-    count_launch(2);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -121,14 +121,21 @@ cudaError_t launch_rollout_pair(const ProblemC &P, const DynState *dyn, const fl
 cudaError_t launch_sample_mean(const float *cost_ms, int64_t L, int M, int N, float *cbar,
                                cudaStream_t st);
 
+// cq: when given, the LSE pass also writes the resampling's chunk sums of
+// q = floor(wtilde 2^40) there (resample_partials of the resampling's
+// workspace), and launch_resample is then called with sums_ready.
 cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, double *wtilde,
-                       double *lmax, double *wsum, void *work, cudaStream_t st);
+                       double *lmax, double *wsum, void *work, cudaStream_t st,
+                       unsigned long long *cq = nullptr);
 size_t lse_workspace(int nseg, int64_t L);
 cudaError_t launch_resample(const double *wtilde, int nseg, int64_t L, int64_t Lout, uint32_t key0,
                             uint32_t key1, uint32_t J, const uint32_t *d_mpc, uint32_t mpc_host,
                             int32_t *anc, void *work, unsigned int *d_flags, cudaStream_t st,
-                            const SegKey *seg_keys = nullptr, const DynState *dyns = nullptr);
+                            const SegKey *seg_keys = nullptr, const DynState *dyns = nullptr,
+                            bool sums_ready = false);
 size_t resample_workspace(int nseg, int64_t L);
+// The chunk sums' place in a resampling workspace.
+unsigned long long *resample_partials(void *work);
 
 cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                         const float ctrl_hi[3], const float sigma[3], const float *u,
@@ -225,8 +232,8 @@ struct tma_solver {
     double *d_wtilde = nullptr;
     int32_t *d_anc = nullptr;
     float *d_popdense = nullptr;
-    void *d_work = nullptr;
-    size_t work_bytes = 0;
+    void *d_work = nullptr;             // LSE workspace, then the resampling's at lse_work_bytes
+    size_t work_bytes = 0, lse_work_bytes = 0;
     int64_t *d_best = nullptr;
     double *d_best_sum = nullptr;
     int32_t *d_ninf = nullptr;
@@ -304,7 +311,8 @@ struct tma_batch {
     float *d_cost_ms = nullptr, *d_cost_ms_soft = nullptr, *d_cbar = nullptr, *d_cbar_soft = nullptr;
     double *d_wtilde = nullptr;
     int32_t *d_anc = nullptr;
-    void *d_work = nullptr;
+    void *d_work = nullptr;             // LSE workspace, then the resampling's at lse_work_bytes
+    size_t lse_work_bytes = 0;
     long long *d_best = nullptr;
     double *d_best_sum = nullptr;
     int *d_ninf = nullptr;

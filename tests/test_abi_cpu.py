@@ -40,7 +40,7 @@ def test_every_declared_function_is_exported(lib):
     for n in names:
         assert callable(getattr(pkg, n, None)) or n in (
             "tma_status_str", "tma_last_error_string", "tma_launch_count", "tma_lse_workspace",
-            "tma_resample_workspace", "tma_select_workspace"), n
+            "tma_lse_resample_workspace", "tma_resample_workspace", "tma_select_workspace"), n
         getattr(lib, n)
 
 
@@ -118,6 +118,14 @@ def test_stage_calls_reject_invalid_arguments(lib):
     assert L.tma_resample_to(null, 2, 10, -1, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
     assert L.tma_resample_to(null, 2, 10, 7, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_ERR_INVALID_ARG
     assert L.tma_resample_to(null, 0, 10, 7, 0, 0, 0, 0, null, null, 0, null) == pkg.TMA_OK
+    # the fused weights + resampling call: kappa, counts and buffers checked first
+    assert L.tma_lse_resample(null, 2, 10, 10, 0.0, 0, 0, 0, 0, null, null, null, null, 0, null) == \
+        pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_lse_resample(null, 2, 10, 10, 8.0, 0, 0, 0, 0, null, null, null, null, 0, null) == \
+        pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_lse_resample(null, 2, 10, 0, 8.0, 0, 0, 0, 0, null, null, null, null, 0, null) == \
+        pkg.TMA_ERR_INVALID_ARG
+    assert L.tma_lse_resample(null, 0, 10, 10, 8.0, 0, 0, 0, 0, null, null, null, null, 0, null) == pkg.TMA_OK
     assert L.tma_move_to(null, null, 4, null, 4, 0, null, null) == pkg.TMA_ERR_INVALID_ARG
     assert L.tma_set_finished(null, 0, null) == pkg.TMA_ERR_INVALID_ARG
     assert L.tma_get_status(null, None, None, null) == pkg.TMA_ERR_INVALID_ARG
@@ -128,6 +136,8 @@ def test_workspace_sizes(lib):
         for f in (lib.tma_lse_workspace, lib.tma_resample_workspace):
             assert f(nseg, L) >= 16
         assert lib.tma_resample_workspace(nseg, L) >= lib.tma_resample_workspace(1, 1)
+        assert lib.tma_lse_resample_workspace(nseg, L) >= \
+            lib.tma_lse_workspace(nseg, L) + lib.tma_resample_workspace(nseg, L) - 16
     assert lib.tma_select_workspace(1 << 22) > 0
 
 

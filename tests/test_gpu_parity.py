@@ -268,6 +268,34 @@ def test_resample_concentrated_and_degenerate(torch, pkg):
     assert np.array_equal(anc, ref)
 
 
+@pytest.mark.parametrize("nseg,L,L_out", [(8, 65536, 65536), (3, 5000, 5000), (5, 4097, 1500),
+                                          (2, 2048, 9000), (1, 1, 1)])
+def test_lse_resample_fused_call(torch, pkg, nseg, L, L_out):
+    """One stream-ordered call (the chunk sums of q formed by the pass that
+    writes wtilde) gives the bits of tma_lse then tma_resample_to, and the
+    oracle's ancestors; an all-infinite segment sets the degenerate bit."""
+    rng = _rng(nseg * 7 + L)
+    c = S.random_cbar(nseg, L, rng)
+    if nseg > 2:
+        c[1] = np.inf
+    cd = torch.from_numpy(c).cuda()
+    seed, sid, J, mpc = 4242 + L, 1, 3, 2
+    wt = torch.empty((nseg, L), dtype=torch.float64, device="cuda")
+    anc = torch.full((nseg, L_out), -1, dtype=torch.int32, device="cuda")
+    deg = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pkg.tma_lse_resample(cd, 11.0, seed, sid, J, mpc, wt, anc, deg)
+    wt2 = torch.empty_like(wt)
+    pkg.tma_lse(cd, 11.0, wt2)
+    anc2 = torch.empty_like(anc)
+    st = pkg.tma_resample_to(wt2, seed, sid, J, mpc, anc2)
+    assert torch.equal(wt, wt2)
+    assert torch.equal(anc, anc2)
+    assert (int(deg.item()) & 1) == (1 if st == pkg.TMA_WARN_DEGENERATE else 0)
+    p = S.config1().copy(seed=seed, scenario_id=sid, mpc_step=mpc)
+    ref, _ = O.resample(wt.cpu().numpy(), [O.resample_uniform(p, s, J) for s in range(nseg)], L_out)
+    assert np.array_equal(anc.cpu().numpy(), ref)
+
+
 def test_lse_then_resample_chain(torch, pkg):
     # the two stateless stages composed as in one SMC iteration
     rng = _rng(21)
