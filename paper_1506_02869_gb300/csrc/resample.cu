@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "device_common.cuh"
+#include "exp_table.h"
 #include "tma_internal.h"
 
 namespace tma {
@@ -106,6 +107,36 @@ __global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restric
     if (threadIdx.x == 0) cmin[(size_t)s * nchunk + c] = mn;
 }
 
+// exp(x) for x = kappa (cmin - c) <= 0 in FP64, by the table-driven method of
+// Tang (ACM TOMS 15(2), 1989) with 256 table entries: k = rint(x 256 / ln 2),
+// x = k ln2/256 + r with |r| <= ln2/512 (plus a sliver: k comes from the FP32
+// copy xf of x), exp(x) = 2^(k >> 8) 2^((k & 255)/256) exp(r) and
+// exp(r) = 1 + r + r^2 (1/2 + r/6 + r^2/24) + O(r^5 / 120 < 4e-17).  The
+// reduction is two fused multiply-adds with the head and tail of ln2/256; the
+// small term r^2 (1/2 + r/6 + r^2/24) < 1e-6 is formed in FP32 (absolute error
+// below 1e-13).  Relative error of the result: about 2e-13.  FP64 carries x,
+// r and the result; the FP64 instructions per call are about half of a
+// general-purpose exp's.  tab: 2^(j/256) (kExp2Frac), staged in shared memory.
+__device__ __forceinline__ double exp_nonpos(double x, float xf, const double *tab)
+{
+    if (!(xf > -745.0f)) return 0.0;               // below the smallest subnormal (and -inf)
+    const int k = __float2int_rn(xf * 369.329794f); // 256 / ln 2
+    const double kd = (double)k;
+    double r = fma(-kd, kExpL1, x);
+    r = fma(-kd, kExpL2, r);
+    const float rf = __double2float_rn(r);
+    const float small = rf * rf * fmaf(fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f), rf, 0.5f);
+    const double p = r + (double)small;            // exp(r) - 1
+    const double t = tab[k & 255];
+    const double y = fma(t, p, t);                  // in [0.99, 2)
+    // times 2^m, m = floor(k / 256) in [-1075, 0]: into the exponent field, with
+    // a final scaling by 2^-64 when the result is subnormal
+    const int m = k >> 8;
+    if (m >= -1000)
+        return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+    return __longlong_as_double(__double_as_longlong(y) + ((long long)(m + 64) << 52)) * 0x1p-64;
+}
+
 // Writes wtilde; csum (chunk sums of wtilde, fixed order) and cq (chunk sums
 // of q = floor(wtilde 2^40) for the resampling) when given.
 __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cbar, long long L,
@@ -117,15 +148,19 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
 {
     __shared__ float shf[32];
     __shared__ unsigned long long shq[32];
+    __shared__ double tab[256];
     const int s = blockIdx.y, c = blockIdx.x;
+    for (int j = threadIdx.x; j < 256; j += kThreads) tab[j] = kExp2Frac[j];
     float mn = __int_as_float(0x7f800000);
     for (int j = threadIdx.x; j < nchunk; j += kThreads) mn = fminf(mn, cmin[(size_t)s * nchunk + j]);
-    mn = block_reduce(mn, MinOp(), shf, __int_as_float(0x7f800000));
+    mn = block_reduce(mn, MinOp(), shf, __int_as_float(0x7f800000));   // its barriers also cover tab
     const bool any = !isinf(mn);
     const double lmax = -kappa * (double)mn;
+    const float kf = (float)kappa;
     const float *row = cbar + (size_t)s * L;
     double *out = wtilde + (size_t)s * L;
     const long long base = (long long)c * kChunk;
+    const bool want_sum = csum != nullptr;
     double acc = 0.0;
     unsigned long long qacc = 0;
 #pragma unroll
@@ -134,9 +169,10 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
         if (idx < L) {
             const float v = __ldg(row + idx);
             double w = 0.0;
-            if (any && !isinf(v) && !isnan(v)) w = exp(-kappa * (double)v - lmax);
+            // -kappa c - lmax = kappa (cmin - c) <= 0; its FP32 copy picks the table entry
+            if (any && !isinf(v) && !isnan(v)) w = exp_nonpos(-kappa * (double)v - lmax, kf * (mn - v), tab);
             out[idx] = w;
-            acc += w;
+            if (want_sum) acc += w;
             qacc += qfix(w);
         }
     }

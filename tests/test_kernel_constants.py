@@ -46,3 +46,77 @@ def test_atan2_octants_in_fp32():
     a = np.where(x < 0, np.float32(np.pi) - a, a).astype(np.float32)
     a = np.copysign(a, y)
     assert np.abs(a.astype(np.float64) - np.arctan2(y.astype(np.float64), x.astype(np.float64))).max() < 5e-7
+
+
+# ---- the normalisation's FP64 exponential (exp_table.h, exp_nonpos in resample.cu)
+
+def _exp_table():
+    src = open(os.path.join(CSRC, "exp_table.h")).read()
+    L1 = float.fromhex(re.search(r"kExpL1 = (\S+);", src).group(1))
+    L2 = float.fromhex(re.search(r"kExpL2 = (\S+);", src).group(1))
+    body = src[src.index("kExp2Frac[256] = {"):]
+    tab = [float.fromhex(v) for v in re.findall(r"(0x1\.[0-9a-f]+p[+-]\d+)", body)]
+    return L1, L2, tab
+
+
+def test_exp_table_is_the_generator_output():
+    out = subprocess.run([sys.executable, os.path.join(CSRC, "gen_exp_table.py")], capture_output=True,
+                         text=True, check=True).stdout
+    assert out.strip() == open(os.path.join(CSRC, "exp_table.h")).read().strip()
+    L1, L2, tab = _exp_table()
+    assert len(tab) == 256 and tab[0] == 1.0
+    j = np.arange(256)
+    # every entry within half an ulp of 2^(j/256) (numpy's exp2 is within one)
+    assert np.all(np.abs(np.array(tab) - np.exp2(j / 256.0)) <= np.spacing(np.array(tab)))
+    assert abs((L1 + L2) - np.log(2.0) / 256) < 1e-18 and abs(L2) < 2.0 ** -60
+
+
+def _fma(a, b, c):
+    from fractions import Fraction
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def _exp_nonpos(x, xf, L1, L2, tab):
+    """The kernel's steps: FP64 where it uses FP64 (fused multiply-adds
+    emulated exactly), FP32 where it uses FP32."""
+    f32 = np.float32
+    if not np.float32(xf) > np.float32(-745.0):
+        return 0.0
+    k = int(np.rint(f32(xf) * f32(369.329794)))
+    r = _fma(-float(k), L1, x)
+    r = _fma(-float(k), L2, r)
+    rf = f32(r)
+    h = f32(f32(f32(rf * f32(1.0 / 24.0)) + f32(1.0 / 6.0)) * rf) + f32(0.5)
+    small = f32(f32(rf * rf) * f32(h))
+    p = r + float(small)
+    t = tab[k & 255]
+    y = _fma(t, p, t)
+    return float(np.ldexp(y, k >> 8))
+
+
+def test_exp_nonpos_meets_its_error_bound():
+    """Relative error below 5e-13 against the correctly rounded exp over the
+    range the weights use (kappa (cmin - c) from 0 down to -740), including
+    table boundaries and the subnormal end."""
+    import math
+    L1, L2, tab = _exp_table()
+    rng = np.random.default_rng(3)
+    kappa = 11.0
+    c = np.float32(rng.uniform(0, 60, 3000))
+    xs = [(-kappa * float(ci), np.float32(kappa) * (np.float32(0) - ci)) for ci in c]
+    # multiples of ln2/256 and half-way points, and the far end
+    for k in (1, 2, 255, 256, 257, 5000, 100000, 275000):
+        for d in (0.0, 0.5, -0.5, 1e-9):
+            x = -(k + d) * math.log(2.0) / 256
+            xs.append((x, np.float32(x)))
+    xs += [(0.0, np.float32(0.0)), (-744.0, np.float32(-744.0)), (-700.0, np.float32(-700.0))]
+    worst = 0.0
+    for x, xf in xs:
+        got = _exp_nonpos(x, xf, L1, L2, tab)
+        ref = math.exp(x)
+        if ref > 1e-300:
+            worst = max(worst, abs(got - ref) / ref)
+        else:
+            assert abs(got - ref) <= 2 * 5e-324 + 1e-12 * ref
+    assert worst < 5e-13, worst
+    assert _exp_nonpos(0.0, np.float32(0.0), L1, L2, tab) == 1.0
