@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restric
 // general-purpose exp's.  tab: 2^(j/256) (kExp2Frac), staged in shared memory.
 __device__ __forceinline__ double exp_nonpos(double x, float xf, const double *tab)
 {
-    if (!(xf > -745.0f)) return 0.0;               // below the smallest subnormal (and -inf)
+    if (!(xf > -746.0f)) return 0.0;               // exp(x) below half the smallest subnormal (and -inf)
     const int k = __float2int_rn(xf * 369.329794f); // 256 / ln 2
     const double kd = (double)k;
     double r = fma(-kd, kExpL1, x);

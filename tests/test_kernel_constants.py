@@ -80,7 +80,7 @@ def _exp_nonpos(x, xf, L1, L2, tab):
     """The kernel's steps: FP64 where it uses FP64 (fused multiply-adds
     emulated exactly), FP32 where it uses FP32."""
     f32 = np.float32
-    if not np.float32(xf) > np.float32(-745.0):
+    if not np.float32(xf) > np.float32(-746.0):
         return 0.0
     k = int(np.rint(f32(xf) * f32(369.329794)))
     r = _fma(-float(k), L1, x)
