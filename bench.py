@@ -64,15 +64,21 @@ def flops_per_unit(p):
 
 
 # DRAM bytes (read + write) of one full-size rollout launch of the 8-aircraft
-# workload, from a one-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, iteration 20 of a solve); valid only for the kernel
-# sources it was taken on.
-ROLLOUT_TRAFFIC = {"bytes_per_launch": 1.0047e9 + 68.48e6, "sources_sha256_16": "4bb27b2e823f3bcc"}
+# workload per rollout kernel, from a one-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, iteration 20 of a solve);
+# valid only for the kernel sources they were taken on.
+ROLLOUT_TRAFFIC = {"sources_sha256_16": "ead05d49ee93a106",
+                   "bytes_per_launch": {"rollout_kernel": 999779328 + 68229632}}
+
+
+def rollout_kernel_name(variant):
+    """The rollout kernel a launch variant runs (8 and up: two wind samples per thread)."""
+    return "rollout_pair_kernel" if variant is not None and variant >= 8 else "rollout_kernel"
 
 
 def rollout_sources_digest():
     h = hashlib.sha256()
-    for f in ("rollout.cu", "rollout_tile.cuh", "device_common.cuh"):
+    for f in ("rollout.cu", "rollout_pair.cu", "rollout_tile.cuh", "device_common.cuh"):
         with open(os.path.join(ROOT, "paper_1506_02869_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -311,10 +317,12 @@ def run_ours(args, world, rank, local):
     sm_clock = 2070.0
     peak = fp32_peak_tflops(sm_clock)
     total_ms = sum(v[0] for v in prof.values())
+    variant, timed = pkg.tma_get_tuning(h)
+    kname = rollout_kernel_name(variant)
     roofline = {
-        "bound": "alu", "kernel": "rollout_kernel", "achieved": achieved, "peak": peak,
+        "bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-        "traffic": (ROLLOUT_TRAFFIC["bytes_per_launch"]
+        "traffic": (ROLLOUT_TRAFFIC["bytes_per_launch"].get(kname)
                     if rollout_sources_digest() == ROLLOUT_TRAFFIC["sources_sha256_16"] else None),
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
         "flops_per_unit": fpu, "live_units_per_launch": live_per_launch,
@@ -324,7 +332,6 @@ def run_ours(args, world, rank, local):
     pk = measured_peaks()
     if pk:
         roofline["hbm_peak_gbs_measured"] = pk.get("hbm_gbs")
-    variant, timed = pkg.tma_get_tuning(h)
     roofline["launch_variant"] = {"chosen": variant,
                                   "timed_ms": {str(k): round(v, 4) for k, v in timed.items()}}
 
