@@ -73,6 +73,25 @@ def test_rollout_matches_oracle(torch, pkg, J, soft):
     assert err.max() <= COST_TOL
 
 
+def test_rolling_window_with_corner_wind_and_sample_schedule(torch, pkg):
+    """The combination the paper's standard problem uses (Sec. 4.4, Sec. 5.1):
+    rolling window, each particle's wind on the 2x2x2 corner grid drawn in the
+    kernel, and iteration J rolling out min(SampleSchedule(J), M) samples."""
+    p = windowed(H=12, L=256, M=12).copy(grid=(2, 2, 2), wind_mode=1, sample_mode=1)
+    rng = np.random.default_rng(61)
+    u = S.mild_controls(p, p.L, rng)
+    J = 5                                        # SampleSchedule(5) = 9 < M
+    sol = _solver(pkg, p)
+    cbar, _ = sol.rollout_cost(torch.from_numpy(u).cuda(), J)
+    sol.close()
+    # the oracle's rollout averages over all of p.M: hand it the iteration's samples
+    ref = O.rollout(p.copy(M=O.samples(p, J)), u, J, soft=False)
+    got = cbar.cpu().numpy().astype(np.float64)
+    emax, n, _ = compare_costs(got, ref["cbar"], ref["margin"], ref["smargin"], "rolling corner wind")
+    assert n > 300
+    assert (got[4] == 0).all() and (got[5] == 0).all()
+
+
 def test_everyone_present_is_the_plain_rollout(torch, pkg):
     p = windowed(finished=0)
     ac = p.aircraft.copy()
