@@ -842,7 +842,7 @@ def run_layout_sweep(args, local):
     n_steps = args.mpc_steps if args.mpc_steps > 6 else 9
     rows = []
     auto = None
-    for v in range(13):
+    for v in (range(13) if args.variant < 0 else [args.variant]):
         sol = pkg.Solver(p)
         if auto is None:
             auto = pkg.tma_get_tuning(sol.h)[0]
@@ -915,6 +915,8 @@ def main(argv=None):
                          "and a falling particle count")
     ap.add_argument("--layout-sweep", action="store_true",
                     help="re-run the paper's thread/block layout sweep (forced launch variants)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="with --layout-sweep: only this launch variant")
     ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--eps-rw", type=float, default=1.0)
     ap.add_argument("--eps-mala", type=float, default=0.3)
