@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     const long long l = l0 + j;
     const bool exists = l < L;
     const bool soft_on = cost_ms_soft != nullptr;
-    const AircraftC &A = P.ac[i];
+    const AircraftC A = P.ac[i];   // a copy: the warp-uniform constants stay in registers
     const uint32_t mpc = dyn->mpc_step;
     const float4 *WA = W + (size_t)mA * P.H * P.P;
     const float4 *WB = W + (size_t)(hasB ? mB : mA) * P.H * P.P;

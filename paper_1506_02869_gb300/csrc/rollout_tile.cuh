@@ -442,7 +442,10 @@ struct TileResult {
 
 // OwnWind: wind mode 1; Rolling: the rolling window (each compiled apart, so
 // the plain problem keeps its register budget).
-template <bool OwnWind, bool Rolling>
+// CopyAc: the aircraft's constants copied into registers once (the plain
+// kernels: a reference into the parameter space reloads them at every use);
+// the batched kernel keeps the reference, its register budget is full.
+template <bool OwnWind, bool Rolling, bool CopyAc = true>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
                                                         const float *__restrict__ u,
                                                         const float4 *__restrict__ Wm, long long L,
@@ -453,7 +456,9 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     const int N = P.N;
     const long long l = l0 + j;
     const bool exists = l < L;
-    const AircraftC &A = P.ac[i];
+    AircraftC Acopy;
+    if constexpr (CopyAc) Acopy = P.ac[i];
+    const AircraftC &A = CopyAc ? Acopy : P.ac[i];
     const uint32_t mpc = dyn->mpc_step;
     // rolling window: the first step this aircraft flies, and whether it is in
     // the problem at all during this horizon (warp-uniform)
@@ -581,13 +586,13 @@ __device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynS
                                                    int bar_count)
 {
     if (P.wind_mode == 1)
-        return P.rolling ? rollout_tile_mode<true, true>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+        return P.rolling ? rollout_tile_mode<true, true, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
                                                          bar_id, bar_count)
-                         : rollout_tile_mode<true, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+                         : rollout_tile_mode<true, false, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
                                                           bar_id, bar_count);
-    return P.rolling ? rollout_tile_mode<false, true>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+    return P.rolling ? rollout_tile_mode<false, true, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
                                                       bar_id, bar_count)
-                     : rollout_tile_mode<false, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
+                     : rollout_tile_mode<false, false, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
                                                        bar_id, bar_count);
 }
 
