@@ -24,6 +24,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same block function with the round keys given: rk[2r], rk[2r + 1] =
+// (k0, k1) + r (0x9E3779B9, 0xBB67AE85), the key of round r (a kernel that has
+// them in its parameter space reads them as constant operands instead of
+// forming them round by round).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 // Counter layout of every random stream: (c0, c1, q | stream << 24, J | mpc << 16).
 __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
                                       uint32_t q, uint32_t stream, uint32_t J, uint32_t mpc)
@@ -31,6 +46,13 @@ __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t c0, uin
     return philox4x32_10(make_uint4(c0, c1, (q & 0xFFFFFFu) | (stream << 24),
                                     (J & 0xFFFFu) | (mpc << 16)),
                          k0, k1);
+}
+
+__device__ __forceinline__ uint4 draw_rk(const uint32_t *rk, uint32_t c0, uint32_t c1, uint32_t q,
+                                         uint32_t stream, uint32_t J, uint32_t mpc)
+{
+    return philox4x32_10_rk(make_uint4(c0, c1, (q & 0xFFFFFFu) | (stream << 24), (J & 0xFFFFu) | (mpc << 16)),
+                            rk);
 }
 
 // Uniform in (0, 1) from the top 23 bits: ((x >> 9) + 1/2) / 2^23, exact in FP32.

@@ -273,6 +273,10 @@ static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraf
     const uint64_t key = p.seed + (uint64_t)p.scenario_id * 0x9E3779B97F4A7C15ull;
     P.key0 = (uint32_t)key;
     P.key1 = (uint32_t)(key >> 32);
+    for (int r = 0; r < 10; ++r) {      // the round keys: (k0, k1) + r (Weyl constants)
+        P.rk[2 * r] = P.key0 + (uint32_t)r * 0x9E3779B9u;
+        P.rk[2 * r + 1] = P.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     for (int i = 0; i < p.N; ++i) {
         const tma_aircraft &a = aircraft[i];
         AircraftC &c = P.ac[i];

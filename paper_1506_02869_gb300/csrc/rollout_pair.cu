@@ -180,12 +180,12 @@ __device__ __forceinline__ void pair_step(const ProblemC &P, const AircraftC &A,
     float2 n0 = make_float2(0.0f, 0.0f), n1 = n0;
     if ((k & 1) == 0) {
         if (s.fly[0]) {
-            const uint4 r = draw(P.key0, P.key1, l, i | (mA << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
+            const uint4 r = draw_rk(P.rk, l, i | (mA << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
             n0 = box_muller_fast(r.x, r.y);
             s.turb_next[0] = box_muller_fast(r.z, r.w);
         }
         if (s.fly[1]) {
-            const uint4 r = draw(P.key0, P.key1, l, i | (mB << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
+            const uint4 r = draw_rk(P.rk, l, i | (mB << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
             n1 = box_muller_fast(r.x, r.y);
             s.turb_next[1] = box_muller_fast(r.z, r.w);
         }

@@ -280,7 +280,9 @@ struct CostSums {
 // move); otherwise s.dead / s.landed tell whether it stopped at this step.
 // ul = this particle's controls of this aircraft [S][3]; the wind is the
 // sample's shared field Wk, or the particle's own field when pwk is given.
-template <class Visit>
+// ParamP: P is the kernel's parameter (the turbulence draw takes the round
+// keys precomputed in it).
+template <bool ParamP = false, class Visit>
 __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, AcState &s,
                                         const float *__restrict__ ul,
                                         const float4 *__restrict__ Wk, float m0, uint32_t l,
@@ -323,7 +325,8 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
                    : wind_interp(wind_fetch(P, Wk, s.x, s.y, s.z));
     float2 n;
     if ((k & 1) == 0) {
-        const uint4 r = draw(P.key0, P.key1, l, i | (m << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
+        const uint4 r = ParamP ? draw_rk(P.rk, l, i | (m << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc)
+                               : draw(P.key0, P.key1, l, i | (m << 8), (uint32_t)(k >> 1), 0u, (uint32_t)J, mpc);
         n = box_muller_fast(r.x, r.y);
         s.turb_next = box_muller_fast(r.z, r.w);
     } else {
@@ -442,10 +445,12 @@ struct TileResult {
 
 // OwnWind: wind mode 1; Rolling: the rolling window (each compiled apart, so
 // the plain problem keeps its register budget).
-// CopyAc: the aircraft's constants copied into registers once (the plain
-// kernels: a reference into the parameter space reloads them at every use);
-// the batched kernel keeps the reference, its register budget is full.
-template <bool OwnWind, bool Rolling, bool CopyAc = true>
+// ParamP: P is the kernel's parameter (the plain kernels): the aircraft's
+// constants are copied into registers once (a reference into the parameter
+// space reloads them at every use) and the turbulence draws take the
+// precomputed round keys.  The batched kernel reads P from global memory and
+// keeps the reference, its register budget is full.
+template <bool OwnWind, bool Rolling, bool ParamP = true>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
                                                         const float *__restrict__ u,
                                                         const float4 *__restrict__ Wm, long long L,
@@ -457,8 +462,8 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     const long long l = l0 + j;
     const bool exists = l < L;
     AircraftC Acopy;
-    if constexpr (CopyAc) Acopy = P.ac[i];
-    const AircraftC &A = CopyAc ? Acopy : P.ac[i];
+    if constexpr (ParamP) Acopy = P.ac[i];
+    const AircraftC &A = ParamP ? Acopy : P.ac[i];
     const uint32_t mpc = dyn->mpc_step;
     // rolling window: the first step this aircraft flies, and whether it is in
     // the problem at all during this horizon (warp-uniform)
@@ -507,8 +512,8 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
         const bool entered = k >= k_in;
         if (!s.dead && !s.landed && entered) {
             ++nlive;
-            ac_step(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i, (uint32_t)m, k,
-                    J, mpc, cs, own_wind ? pw + (k & 1) * 16 * kPB + j : nullptr);
+            ac_step<ParamP>(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i, (uint32_t)m,
+                            k, J, mpc, cs, own_wind ? pw + (k & 1) * 16 * kPB + j : nullptr);
         }
         // the particles' wind state of the next step, read after this step's barrier
         if (own_wind && k + 1 < P.H) particle_wind_step(P, pw, i, N, j, (uint32_t)l, m, k + 1, mpc);

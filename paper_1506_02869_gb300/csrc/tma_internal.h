@@ -53,6 +53,7 @@ struct ProblemC {
     float wind_a, wind_b;  // AR(1) coefficients a, sqrt(1 - a^2) of that field
     float wchol[36];       // its Qhat: lower Cholesky factor of R_hat (8 x 8, packed rows)
     uint32_t key0, key1;   // Philox key (seed + scenario_id * golden)
+    uint32_t rk[20];       // its ten round keys (k0, k1 of round r at 2r, 2r + 1)
     AircraftC ac[kMaxN];
 };
 
