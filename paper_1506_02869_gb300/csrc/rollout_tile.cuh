@@ -413,14 +413,16 @@ __device__ __forceinline__ float total_objective(const ProblemC &P, const Aircra
     return (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-c.sN, invH, 1.0f);
 }
 
-// Shared memory of one tile (32-bit words): positions float4 [2][N][32]
-// (double-buffered by step), separation flags [N][32], the received
-// separation penalties [2][N][floor((N-1)/2) + 1][32] of the soft form, and in
-// wind mode 1 the particles' wind state [2][16][32].
+// Shared memory of one tile (32-bit words): positions float4 [2][2N][32]
+// (double-buffered by step; every aircraft's row written twice, at i and
+// i + N, so that the partners i+1 .. i+N/2 are consecutive rows without a
+// wrap), separation flags [N][32], the received separation penalties
+// [2][N][floor((N-1)/2) + 1][32] of the soft form, and in wind mode 1 the
+// particles' wind state [2][16][32].
 __host__ __device__ constexpr int tile_pair_slots(int N) { return (N - 1) / 2 + 1; }
 __host__ __device__ constexpr int tile_smem_words(int N, int wind_mode)
 {
-    return (9 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) * kTileParticles;
+    return (17 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) * kTileParticles;
 }
 
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
@@ -492,9 +494,9 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
     unsigned int nlive = 0;
     const int plane = N * kPB;
-    float4 *pos = reinterpret_cast<float4 *>(spos);                 // [2][N][32]
-    int *vflag = reinterpret_cast<int *>(spos + 8 * plane);        // [N][32]
-    float *recv = spos + 9 * plane;                                 // [2][N][slots][32]
+    float4 *pos = reinterpret_cast<float4 *>(spos);                 // [2][2N][32]
+    int *vflag = reinterpret_cast<int *>(spos + 16 * plane);       // [N][32]
+    float *recv = spos + 17 * plane;                                // [2][N][slots][32]
     const int slots = tile_pair_slots(N);
     vflag[i * kPB + j] = 0;       // ordered before any partner's mark by the step-0 barrier
     const int n_half = (N - 1) >> 1;
@@ -502,7 +504,7 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     const int n_pairs = n_half + ((even && i < (N >> 1)) ? 1 : 0);
     const int n_recv = n_half + ((even && i >= (N >> 1)) ? 1 : 0);
     constexpr bool own_wind = OwnWind;
-    float *pw = spos + (9 * N + 2 * N * slots) * kPB;      // mode 1: [2][16][32]
+    float *pw = spos + (17 * N + 2 * N * slots) * kPB;     // mode 1: [2][16][32]
     if constexpr (own_wind) {
         particle_wind_step(P, pw, i, N, j, (uint32_t)l, m, 0, mpc);
         tile_barrier(bar_id, bar_count);
@@ -520,9 +522,14 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
         // binary separation constraints at step k+1 among flying aircraft: every
         // thread publishes its position (a far-away altitude when not flying)
         const bool act = !s.dead && !s.landed && entered;
-        float4 *buf = pos + (k & 1) * plane;
-        buf[i * kPB + j] = make_float4(s.x, s.y, act ? s.z : 1e30f, 0.0f);
+        float4 *buf = pos + (k & 1) * 2 * plane;
+        const float4 me = make_float4(s.x, s.y, act ? s.z : 1e30f, 0.0f);
+        buf[i * kPB + j] = me;
+        buf[(i + N) * kPB + j] = me;
         tile_barrier(bar_id, bar_count);
+        // partner i + 1 + d is row i + 1 + d of buf (no wrap); its index mod N
+        // only where a mark or a penalty slot is written
+        const float4 *qrow = buf + (i + 1) * kPB + j;
         if (soft_on) {
             // penalties the partners computed for this aircraft at the previous step
             if (k > 0) {
@@ -530,10 +537,9 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
                 for (int d = 0; d < n_recv; ++d) soft += rr[d * kPB];
             }
             float *rw = recv + ((k & 1) * N * slots) * kPB + j;
-            int i2 = i;
             for (int d = 0; d < n_pairs; ++d) {
-                i2 = (i2 + 1 == N) ? 0 : i2 + 1;
-                const float4 q = buf[i2 * kPB + j];
+                const int i2 = i + 1 + d < N ? i + 1 + d : i + 1 + d - N;
+                const float4 q = qrow[d * kPB];
                 const float dx = s.x - q.x, dy = s.y - q.y, adz = fabsf(s.z - q.z);
                 const float dh2 = fmaf(dx, dx, dy * dy);
                 float pen = 0.0f;
@@ -549,13 +555,12 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
                 rw[(i2 * slots + d) * kPB] = pen;
             }
         } else if (act) {
-            int i2 = i;
             for (int d = 0; d < n_pairs; ++d) {
-                i2 = (i2 + 1 == N) ? 0 : i2 + 1;
-                const float4 q = buf[i2 * kPB + j];
+                const float4 q = qrow[d * kPB];
                 const float dx = s.x - q.x, dy = s.y - q.y;
                 if (fmaf(dx, dx, dy * dy) < P.Sh2 && fabsf(s.z - q.z) < P.Sv) {
                     sepv = true;
+                    const int i2 = i + 1 + d < N ? i + 1 + d : i + 1 + d - N;
                     vflag[i2 * kPB + j] = 1;
                 }
             }
