@@ -249,6 +249,14 @@ static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraf
     P.sep_mode = p.sep_mode;
     P.sp_beta = (float)p.sp_beta;
     P.sp_inv_beta = (float)(p.sp_beta != 0 ? 1.0 / p.sp_beta : 0.0);
+    {
+        // g = min(1 - d_h/S_h, 1 - |dz|/S_v) < -30/beta when d_h > S_h (1 + 30/beta)
+        // or |dz| > S_v (1 + 30/beta)
+        const double f = p.sp_beta > 0 ? 1.0 + 30.0 / p.sp_beta : 1e30;
+        const double fh = p.sep_h * f;
+        P.sp_far_h2 = (float)std::min(fh * fh, 1e30);
+        P.sp_far_v = (float)std::min(p.sep_v * f, 1e30);
+    }
     P.mu_sep = (float)p.mu_sep;
     P.z_min = (float)p.z_min;
     P.z_max = (float)p.z_max;

@@ -357,8 +357,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
                             sepv[g] = true;
                             vflag[g * plane + i2 * kPB + j] = 1;
                         }
-                        pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
-                                       P.sp_beta, P.sp_inv_beta);
+                        if (dh2 < P.sp_far_h2 && adz < P.sp_far_v)   // else below e^-30 / beta
+                            pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
+                                           P.sp_beta, P.sp_inv_beta);
                         soft[g] += pen;
                     }
                     recv[((((k & 1) * 2 + g) * N + i2) * slots + d) * kPB + j] = pen;

@@ -548,8 +548,9 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
                         sepv = true;
                         vflag[i2 * kPB + j] = 1;
                     }
-                    pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
-                                   P.sp_beta, P.sp_inv_beta);
+                    if (dh2 < P.sp_far_h2 && adz < P.sp_far_v)   // else below e^-30 / beta
+                        pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
+                                       P.sp_beta, P.sp_inv_beta);
                     soft += pen;
                 }
                 rw[(i2 * slots + d) * kPB] = pen;

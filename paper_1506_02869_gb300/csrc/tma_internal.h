@@ -41,6 +41,10 @@ struct ProblemC {
     float Sh2, Sh_inv, Sv, Sv_inv;
     int sep_mode;
     float sp_beta, sp_inv_beta, mu_sep;
+    // beyond these (d_h^2 above sp_far_h2 or |dz| above sp_far_v) the margin g
+    // lies below -30 / beta and the softplus penalty below e^-30 / beta: it is
+    // taken as 0 without evaluating it
+    float sp_far_h2, sp_far_v;
     float z_min, z_max, v_min, v_max;
     float a_dep[4], a_arr[3];
     float w_noise, Ac_inv;
