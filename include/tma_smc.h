@@ -50,7 +50,7 @@ typedef enum {
     TMA_ERR_UNSUPPORTED = 7
 } tma_status;
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define TMA_MAX_AIRCRAFT 32          /* N: one warp lane per aircraft */
 #define TMA_MAX_PARTICLES (1 << 22)  /* L: keeps the fixed-point CDF products in 128 bits */
 #define TMA_MAX_GRID_Z 16
