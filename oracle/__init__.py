@@ -363,6 +363,41 @@ def rollout(p, u, J, pidx=None, W=None, nthreads=1, m_chunk=None, soft=True):
     return out
 
 
+def rollout_at_samples(p, u, J, samples, pidx=None, soft=True, nthreads=1):
+    """Per-sample costs of controls u[Lsub][N][S][3] under the listed wind
+    samples only (each field generated alone, so that full-size problems stay
+    tractable): dict of cost / cost_soft [Lsub][len(samples)][N] and margin /
+    smargin as `rollout` returns them per sample ([Lsub][len][N], [Lsub][len])."""
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, p.N, p.S, 3)
+    Ls = u.shape[0]
+    if pidx is None:
+        pidx = np.arange(Ls, dtype=np.int64)
+    pidx = np.ascontiguousarray(pidx, np.int64)
+    ns = len(samples)
+    out = {"cost": np.empty((Ls, ns, p.N)), "margin": np.empty((Ls, ns, p.N)),
+           "smargin": np.empty((Ls, ns))}
+    if soft:
+        out["cost_soft"] = np.empty((Ls, ns, p.N))
+    m = _Marshalled(p)
+    for q, ms in enumerate(samples):
+        Wc = np.ascontiguousarray(wind_field(p, int(ms), 1), np.float64)
+        ch = np.empty((Ls, 1, p.N))
+        cs = np.empty((Ls, 1, p.N)) if soft else None
+        mg = np.empty((Ls, 1, p.N))
+        sm = np.empty((Ls, 1))
+        live = C.c_int64(0)
+        lib().orc_rollout(m.ps, m.ac, _ptr(Wc, C.c_double), int(ms), 1, _ptr(u, C.c_double),
+                          _ptr(pidx, C.c_int64), Ls, J, nthreads, _ptr(ch, C.c_double),
+                          _ptr(cs, C.c_double) if soft else None, _ptr(mg, C.c_double),
+                          _ptr(sm, C.c_double), C.byref(live))
+        out["cost"][:, q] = ch[:, 0]
+        out["margin"][:, q] = mg[:, 0]
+        out["smargin"][:, q] = sm[:, 0]
+        if soft:
+            out["cost_soft"][:, q] = cs[:, 0]
+    return out
+
+
 def trajectory(p, u_l, W_m, l=0, m=0, J=0):
     """States of one (particle, sample) rollout: (traj[H+1][N][8], cost_hard[N],
     cost_soft[N]); traj columns x, y, z, v, chi, m, F, flags (1 violated,
