@@ -157,3 +157,27 @@ def test_error_word_reports_an_infeasible_choice(torch, pkg):
     assert pkg.tma_get_error(sol.h) & 2
     assert pkg.tma_get_error(sol.h) == 0        # cleared by the read
     sol.close()
+
+
+def test_batch_full_size_in_one_launch_equals_single_solves(torch, pkg):
+    """The batched workload at full size -- 256 scenarios of 2 to 32 aircraft,
+    L 16384, M 16, H 60, all in one persistent launch per stage -- for one
+    iteration (J_max = 1: initial controls, rollout, selection), against the
+    single-scenario solver on sampled scenarios (the smallest, the largest and
+    two between); the chosen controls and their costs are the same bits."""
+    ps = [p.copy(J_max=1) for p in S.config5(n_scen=256)]
+    assert len(ps) == 256 and ps[0].L == 16384 and ps[0].M == 16 and ps[0].H == 60
+    Ns = [p.N for p in ps]
+    b = pkg.tma_batch_create(ps)
+    pkg.tma_batch_solve(b)
+    res = pkg.tma_batch_results(b, Ns, ps[0].S)
+    pkg.tma_batch_destroy(b)
+    order = sorted(range(len(ps)), key=lambda s: ps[s].N)
+    for k in (order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]):
+        sol = pkg.Solver(ps[k])
+        bu, c, _ = sol.solve()
+        best = sol.best_index()
+        sol.close()
+        assert np.array_equal(res["best_u"][k], bu.cpu().numpy()), k
+        assert res["best_cost"][k] == c or (np.isinf(c) and np.isinf(res["best_cost"][k])), k
+        assert res["best"][k] == best, k
