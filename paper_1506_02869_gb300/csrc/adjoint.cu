@@ -346,7 +346,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
     const int chunk = blockIdx.x / nLb;
     const long long l = (long long)(blockIdx.x - chunk * nLb) * kPB + j;
     const bool exists = l < L;
-    const AircraftC &A = P.ac[i];
+    const AircraftC A = P.ac[i];   // a copy: the warp-uniform constants stay in registers
     const uint32_t mpc = dyn->mpc_step;
     const float m0 = dyn->x0[i][5];
     const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
@@ -385,7 +385,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
         for (int k = 0; k < P.H; ++k) {
             if (k % kCkEvery == 0) ck[k / kCkEvery] = save(s);
             if (!s.dead && !s.landed)
-                ac_step(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i,
+                ac_step<true>(P, A, s, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i,
                         (uint32_t)m, k, J, mpc, cs);
         }
         const float JT = total_objective(P, A, cs, s.F.s, ab, P.H);
@@ -412,7 +412,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
                 TermGrad tg;
                 tg.cg = cg;
                 if (!r.dead && !r.landed &&
-                    ac_step(P, A, r, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i,
+                    ac_step<true>(P, A, r, ul, Wm + (size_t)k * P.P, m0, (uint32_t)l, (uint32_t)i,
                             (uint32_t)m, k, J, mpc, tg))
                     upd |= 1u << t;
                 const bool act = !r.dead && !r.landed;
