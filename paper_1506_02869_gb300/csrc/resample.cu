@@ -7,22 +7,24 @@
 //   LSE:      (1) chunk minima of the finite costs; (2) every block reduces its
 //             segment's minima to lmax = -kappa * min c (exact: multiplying by
 //             kappa > 0 is monotone), writes wtilde = exp(-kappa c - lmax) in
-//             FP64 and a chunk partial sum; (3) the partial sums are added in
-//             chunk order into wsum.
+//             FP64 (table-driven exponential) and, when asked, a chunk partial
+//             sum; (3) the partial sums are added in chunk order into wsum.
 //   Resample: (1) chunk sums of q = floor(wtilde 2^40) (uint64, exact), by
 //             their own pass or by the LSE pass that writes wtilde;
 //             (2) every block forms its chunk's inclusive prefix S_j, and for
 //             every j the number n_j of particles l whose threshold
 //             t_l = floor((l 2^32 + r) Q / (Lout 2^32)) lies below S_j; the
-//             particles of the chunk are l in [n_(before), n_(last)) and
-//             a_l = min{j : S_j > t_l} = min{j : n_j > l}, a binary search over
-//             the 32-bit counts in shared memory.  Because S_j > floor(y) <=>
-//             S_j > y for integer S_j, a count is settled by comparing 128-bit
-//             products (l 2^32 + r) Q against S_j Lout 2^32 (no division); an
-//             FP32 estimate within one of the count says which l to compare.
-//             Integer arithmetic makes the result independent of the summation
-//             order.  Lout ancestors are drawn from the Lin weighted particles
-//             of the segment (Lout = Lin for a fixed particle count).
+//             chunk's particles are l in [n_(before), n_(last)), element j's
+//             copies [n_(j-1), n_j), so a_l = min{j : S_j > t_l} = min{j :
+//             n_j > l}: each element with copies marks its first particle in a
+//             shared-memory window and a running maximum fills in the rest.
+//             Because S_j > floor(y) <=> S_j > y for integer S_j, a count is
+//             settled by comparing 128-bit integers (S_j Lout against
+//             l Q + floor(r Q / 2^32), no division); an FP32 estimate within
+//             one of the count says which l to compare.  Integer arithmetic
+//             makes the result independent of the summation order.  Lout
+//             ancestors are drawn from the Lin weighted particles of the
+//             segment (Lout = Lin for a fixed particle count).
 #include <cfloat>
 #include <mutex>
 
