@@ -57,12 +57,15 @@ __device__ __forceinline__ void restore(const ProblemC &P, AcState &s, const Che
     s.dead = (c.segflags >> 20) & 1;
     s.landed = (c.segflags >> 21) & 1;
     if (s.seg >= 0) {
-        s.knext = ((s.seg + 1) * P.H + P.S - 1) / P.S;
+        const long long B = (long long)(s.seg + 1) * P.H + P.S - 1;
+        s.knext = (int)(B / P.S);
+        s.srem = (int)(B % P.S);
         s.uw = __ldg(ul + 3 * s.seg);
         s.uh = __ldg(ul + 3 * s.seg + 1);
         s.ua = __ldg(ul + 3 * s.seg + 2);
     } else {
         s.knext = 0;
+        s.srem = P.S - 1;
     }
 }
 
@@ -379,7 +382,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
         // ---------------- pass 1: forward rollout of this aircraft alone, with
         // checkpoints; J_T fixes the cost coefficients of the reverse sweep
         AcState s;
-        ac_init(s, dyn, i, exists);
+        ac_init(s, dyn, i, exists, P.S);
         const AltBounds ab = alt_bounds(P, A, s.z, P.H);
         CostSums cs;
         for (int k = 0; k < P.H; ++k) {
@@ -401,7 +404,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
         for (int c_i = nck - 1; c_i >= 0; --c_i) {
             const int k0 = c_i * kCkEvery, k1 = min(P.H, k0 + kCkEvery);
             AcState r;
-            ac_init(r, dyn, i, exists);
+            ac_init(r, dyn, i, exists, P.S);
             restore(P, r, ck[c_i], ul);
             unsigned upd = 0;
             // the previous interval's last exchange may still be read

@@ -279,6 +279,8 @@ static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraf
     P.P_vs = (float)p.P_vs;
     P.beta_f = (float)p.beta_f;
     const uint64_t key = p.seed + (uint64_t)p.scenario_id * 0x9E3779B97F4A7C15ull;
+    P.seg_q = p.H / p.S;
+    P.seg_r = p.H % p.S;
     P.key0 = (uint32_t)key;
     P.key1 = (uint32_t)(key >> 32);
     for (int r = 0; r < 10; ++r) {      // the round keys: (k0, k1) + r (Weyl constants)

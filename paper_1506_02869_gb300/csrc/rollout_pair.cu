@@ -124,7 +124,7 @@ struct PairState {
     float z, v, chi;
     Kahan F;
     float zb, vb, cb;
-    int ks, knext;
+    int seg, ks, knext, srem;
     float uw, uh, ua;
     // per sample
     float2 P[2];             // (x, y) of sample g
@@ -146,8 +146,17 @@ __device__ __forceinline__ void pair_step(const ProblemC &P, const AircraftC &A,
 {
     const float dt = P.dt;
     if (k >= s.knext) {
-        const int seg = (k * P.S) / P.H;
-        s.knext = ((seg + 1) * P.H + P.S - 1) / P.S;
+        // the next segment(s), as ac_step advances them (no division)
+        do {
+            ++s.seg;
+            s.knext += P.seg_q;
+            s.srem += P.seg_r;
+            if (s.srem >= P.S) {
+                s.srem -= P.S;
+                ++s.knext;
+            }
+        } while (k >= s.knext);
+        const int seg = s.seg;
         s.ks = k;
         s.uw = __ldg(ul + 3 * seg);
         s.uh = __ldg(ul + 3 * seg + 1);
@@ -292,6 +301,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     s.zb = s.vb = s.cb = 0.0f;
     s.ks = 0;
     s.knext = 0;
+    s.seg = -1;
+    s.srem = P.S - 1;
     s.uw = s.uh = s.ua = 0.0f;
     s.P[0] = s.P[1] = make_float2(dyn->x0[i][0], dyn->x0[i][1]);
     s.fly[0] = exists;

@@ -198,6 +198,7 @@ struct AcState {
     Kahan F;                 // fuel burned
     float zb, vb, cb;        // z, v, chi at the start of the current control segment
     int seg, ks, knext;      // current segment, its first step, first step of the next
+    int srem;                // ((seg + 1) H + S - 1) mod S: knext's remainder
     float uw, uh, ua;        // controls of the current segment
     bool dead, landed;
     float2 turb_next;        // second normal pair of the last even-step draw
@@ -206,7 +207,7 @@ struct AcState {
 };
 
 __device__ __forceinline__ void ac_init(AcState &s, const DynState *__restrict__ dyn, int i,
-                                        bool exists)
+                                        bool exists, int S)
 {
     s.x = dyn->x0[i][0];
     s.y = dyn->x0[i][1];
@@ -216,6 +217,7 @@ __device__ __forceinline__ void ac_init(AcState &s, const DynState *__restrict__
     s.F = Kahan();
     s.zb = s.vb = s.cb = 0.0f;
     s.seg = -1;
+    s.srem = S - 1;
     s.ks = 0;
     s.knext = 0;
     s.uw = s.uh = s.ua = 0.0f;
@@ -291,9 +293,19 @@ __device__ __forceinline__ bool ac_step(const ProblemC &P, const AircraftC &A, A
 {
     const float dt = P.dt;
     if (k >= s.knext) {
-        // segment s = floor(k S / H) starts at step ceil(s H / S)
-        s.seg = (k * P.S) / P.H;
-        s.knext = ((s.seg + 1) * P.H + P.S - 1) / P.S;
+        // segment s covers the steps [ceil(s H / S), ceil((s + 1) H / S)) (every
+        // segment has a step: S <= H); knext = ceil((seg + 1) H / S) advances by
+        // H = seg_q S + seg_r with its remainder carried, so no division (a late
+        // entrant passes several segments at its first step)
+        do {
+            ++s.seg;
+            s.knext += P.seg_q;
+            s.srem += P.seg_r;
+            if (s.srem >= P.S) {
+                s.srem -= P.S;
+                ++s.knext;
+            }
+        } while (k >= s.knext);
         s.ks = k;
         s.uw = __ldg(ul + 3 * s.seg);
         s.uh = __ldg(ul + 3 * s.seg + 1);
@@ -478,7 +490,7 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     }
     const int Ha = P.H - k_in;
     AcState s;
-    ac_init(s, dyn, i, exists && !out);
+    ac_init(s, dyn, i, exists && !out, P.S);
     if (Rolling && (k_in & 1) && exists && !out) {
         // entering at an odd step: the turbulence pair of that step comes from
         // the draw of the even step before it, which this aircraft did not fly

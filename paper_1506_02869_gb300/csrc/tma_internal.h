@@ -31,6 +31,7 @@ struct AircraftC {
 // Problem constants passed by value to the rollout kernels.
 struct ProblemC {
     int N, H, S, M, G;     // G = lanes per (particle, sample) group = next_pow2(N)
+    int seg_q, seg_r;      // H = seg_q S + seg_r: the control segments' lengths step by these
     int P;                 // wind grid nodes
     int grid[3];
     float dt;
