@@ -122,6 +122,9 @@ __global__ void __launch_bounds__(256) batch_sample_mean(const float *__restrict
 
 // ----------------------------------------------------------- move and init
 
+// kS: the segment count when fixed at compile time (4: the loop unrolls and
+// every control's component is known), 0 when taken from S.
+template <int kS = 0>
 __global__ void __launch_bounds__(256) batch_move(const BatchScen *__restrict__ scen,
                                                   const int *__restrict__ seg_scen,
                                                   const DynState *__restrict__ dyns, long long nseg,
@@ -137,10 +140,11 @@ __global__ void __launch_bounds__(256) batch_move(const BatchScen *__restrict__ 
     const int i = (int)(seg - sc.seg_off);
     int a = __ldg(anc + t);
     if ((unsigned long long)a >= (unsigned long long)L) a = (int)l;
-    const int nc = 3 * S;
+    const int nc = 3 * (kS > 0 ? kS : S);
     const float *src = u + sc.u_off + ((size_t)a * sc.N + i) * nc;
     float *dst = u_out + sc.u_off + ((size_t)l * sc.N + i) * nc;
     const uint32_t mpc = dyns[s].mpc_step;
+#pragma unroll
     for (int q = 0; q < (nc + 3) / 4; ++q) {
         const uint4 r = draw(sc.key0, sc.key1, (uint32_t)l, (uint32_t)i, (uint32_t)q, 1u, (uint32_t)J, mpc);
         const float2 z01 = box_muller(r.x, r.y), z23 = box_muller(r.z, r.w);
@@ -463,7 +467,10 @@ cudaError_t launch_batch_move(const BatchScen *scen, const int *seg_scen, const 
                               long long nseg, long long L, int S, const float *u,
                               const int32_t *anc, int J, float *u_out, cudaStream_t st)
 {
-    batch_move<<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J, u_out);
+    if (S == 4)
+        batch_move<4><<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J, u_out);
+    else
+        batch_move<<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J, u_out);
     count_launch();
     return cudaGetLastError();
 }

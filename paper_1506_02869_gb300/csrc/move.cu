@@ -16,11 +16,15 @@ struct MoveC {
     int N, nc;             // nc = S*3 controls per (particle, aircraft)
     float lo[3], hi[3], sigma[3];
     uint32_t key0, key1;
+    uint32_t rk[20];       // Philox round keys of (key0, key1)
 };
 
 __device__ __forceinline__ float clip(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
-template <bool kVec>
+// kNC: the number of controls per (particle, aircraft) when fixed at compile
+// time (12 = four segments: the loop unrolls and the per-control constants
+// become fixed operands), 0 when taken from C.nc.
+template <bool kVec, int kNC = 0>
 __global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState *__restrict__ dyn,
                                                    const float *__restrict__ u,
                                                    const int32_t *__restrict__ anc, long long L,
@@ -35,11 +39,13 @@ __global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState
     if ((unsigned long long)a >= (unsigned long long)Lin)   // out-of-range ancestor: own index (clamped)
         a = (int)(l < Lin ? l : Lin - 1);
     const uint32_t mpc = dyn ? dyn->mpc_step : 0u;
-    const float *src = u + ((size_t)a * C.N + i) * C.nc;
-    float *dst = u_out + ((size_t)l * C.N + i) * C.nc;
-    const int nq = (C.nc + 3) / 4;
+    const int nc = kNC > 0 ? kNC : C.nc;
+    const float *src = u + ((size_t)a * C.N + i) * nc;
+    float *dst = u_out + ((size_t)l * C.N + i) * nc;
+    const int nq = (nc + 3) / 4;
+#pragma unroll
     for (int q = 0; q < nq; ++q) {
-        const uint4 r = draw(C.key0, C.key1, (uint32_t)l, (uint32_t)i, (uint32_t)q, 1u, (uint32_t)J, mpc);
+        const uint4 r = draw_rk(C.rk, (uint32_t)l, (uint32_t)i, (uint32_t)q, 1u, (uint32_t)J, mpc);
         const float2 z01 = box_muller(r.x, r.y), z23 = box_muller(r.z, r.w);
         const float z[4] = {z01.x, z01.y, z23.x, z23.y};
         if (kVec) {
@@ -56,7 +62,7 @@ __global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int n = 4 * q + e;
-                if (n < C.nc) {
+                if (n < nc) {
                     const int c = n % 3;
                     dst[n] = clip(fmaf(C.sigma[c], z[e], __ldg(src + n)), C.lo[c], C.hi[c]);
                 }
@@ -101,6 +107,7 @@ MoveC make_move(const ProblemC &P, const float lo[3], const float hi[3], const f
     }
     C.key0 = P.key0;
     C.key1 = P.key1;
+    for (int r = 0; r < 20; ++r) C.rk[r] = P.rk[r];
     return C;
 }
 
@@ -114,7 +121,8 @@ cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl
     const MoveC C = make_move(P, ctrl_lo, ctrl_hi, sigma);
     const long long n = (long long)L * P.N;
     const unsigned grid = (unsigned)((n + 255) / 256);
-    if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
+    if (C.nc == 12) move_kernel<true, 12><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
+    else if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
     else move_kernel<false><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
     count_launch();
     return cudaGetLastError();
