@@ -114,18 +114,19 @@ __global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restric
 // x = k ln2/256 + r with |r| <= ln2/512 (plus a sliver: k comes from the FP32
 // copy xf of x), exp(x) = 2^(k >> 8) 2^((k & 255)/256) exp(r) and
 // exp(r) = 1 + r + r^2 (1/2 + r/6 + r^2/24) + O(r^5 / 120 < 4e-17).  The
-// reduction is two fused multiply-adds with the head and tail of ln2/256; the
-// small term r^2 (1/2 + r/6 + r^2/24) < 1e-6 is formed in FP32 (absolute error
-// below 1e-13).  Relative error of the result: about 2e-13.  FP64 carries x,
-// r and the result; the FP64 instructions per call are about half of a
-// general-purpose exp's.  tab: 2^(j/256) (kExp2Frac), staged in shared memory.
+// reduction is one fused multiply-add with ln2/256 rounded to FP64 (kExpL1; the
+// tail kExpL2 < 1e-19 left out moves r by k kExpL2 < 2.5e-14 over the range,
+// k < 2.8e5); the small term r^2 (1/2 + r/6 + r^2/24) < 1e-6 is formed in FP32
+// (absolute error below 1e-13).  Relative error of the result: about 2e-13.
+// FP64 carries x, r and the result; the FP64 instructions per call are about
+// half of a general-purpose exp's.  tab: 2^(j/256) (kExp2Frac), staged in
+// shared memory.
 __device__ __forceinline__ double exp_nonpos(double x, float xf, const double *tab)
 {
     if (!(xf > -746.0f)) return 0.0;               // exp(x) below half the smallest subnormal (and -inf)
     const int k = __float2int_rn(xf * 369.329794f); // 256 / ln 2
     const double kd = (double)k;
-    double r = fma(-kd, kExpL1, x);
-    r = fma(-kd, kExpL2, r);
+    const double r = fma(-kd, kExpL1, x);
     const float rf = __double2float_rn(r);
     const float small = rf * rf * fmaf(fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f), rf, 0.5f);
     const double p = r + (double)small;            // exp(r) - 1
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
         if (idx < L) {
             const float v = __ldg(row + idx);
             double w = 0.0;
-            // -kappa c - lmax = kappa (cmin - c) <= 0; its FP32 copy picks the table entry
+            // -kappa c - lmax = kappa (cmin - c) <= 0 (0 at the minimum: both
+            // products rounded alike); its FP32 copy picks the table entry
             if (any && !isinf(v) && !isnan(v)) w = exp_nonpos(-kappa * (double)v - lmax, kf * (mn - v), tab);
             out[idx] = w;
             if (want_sum) acc += w;
