@@ -62,6 +62,23 @@ def test_batch_solve_equals_single_solves(torch, pkg):
     assert (lat > 0).all() and np.isfinite(lat).all()
 
 
+def test_batch_solve_with_five_segments_equals_single_solves(torch, pkg):
+    """S = 5 (15 controls per aircraft) takes the batched move's general form
+    (four segments take the unrolled one)."""
+    ps = [p.copy(S=5) for p in mixed_batch(3, L=512, M=3, H=20, J=3)]
+    Ns = [p.N for p in ps]
+    b = pkg.tma_batch_create(ps)
+    pkg.tma_batch_solve(b)
+    res = pkg.tma_batch_results(b, Ns, 5)
+    pkg.tma_batch_destroy(b)
+    for k, p in enumerate(ps):
+        sol = pkg.Solver(p)
+        bu, c, _ = sol.solve()
+        sol.close()
+        assert np.array_equal(res["best_u"][k], bu.cpu().numpy()), k
+        assert res["best_cost"][k] == c or (np.isinf(c) and np.isinf(res["best_cost"][k]))
+
+
 def test_batch_mpc_graph_equals_eager_and_single_loop(torch, pkg):
     ps = mixed_batch(4, L=512, M=3, H=20, J=3)
     Ns = [p.N for p in ps]

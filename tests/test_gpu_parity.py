@@ -313,9 +313,11 @@ def test_lse_then_resample_chain(torch, pkg):
 
 # ------------------------------------------------------------ move / init
 
-@pytest.mark.parametrize("cfg,L", [(1, 1024), (2, 65536), (1, 777)])
-def test_move_matches_oracle(torch, pkg, cfg, L):
-    p = S.shrink(S.make_config(cfg), L=L).copy(mpc_step=2)
+@pytest.mark.parametrize("cfg,L,nseg", [(1, 1024, 4), (2, 65536, 4), (1, 777, 4), (1, 1024, 5), (1, 1000, 8)])
+def test_move_matches_oracle(torch, pkg, cfg, L, nseg):
+    """Four segments take the kernel's 12-control form; five (15 controls, the
+    scalar form) and eight (24, the general 16-byte form) the others."""
+    p = S.shrink(S.make_config(cfg), L=L).copy(mpc_step=2, S=nseg)
     rng = _rng(cfg * 7 + L)
     u = S.random_controls(p, L, rng)
     anc = S.random_ancestors(p.N, L, rng)
