@@ -181,17 +181,73 @@ def units_per_solve(p):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_sample(L_sample, nthreads):
-    """The FP64 oracle's full solve on the workload's traffic with L_sample
-    particles (all other sizes full); returns (units/s, seconds, units)."""
+_ORACLE_WIND = {}
+
+
+def oracle_wind():
+    """The workload's wind field from the oracle (FP64), generated once per
+    process; returns (field, generation seconds)."""
     import oracle as O
     import scenarios as S
-    p = S.config2().copy(L=L_sample)
+    if not _ORACLE_WIND:
+        t0 = time.perf_counter()
+        W = O.wind_field(S.config2())
+        _ORACLE_WIND.update(W=W, seconds=time.perf_counter() - t0)
+    return _ORACLE_WIND["W"], _ORACLE_WIND["seconds"]
+
+
+def oracle_sample(L_sample, nthreads):
+    """The FP64 oracle's full solve on the workload's traffic with L_sample
+    particles (all other sizes full) on the workload's wind field, whose
+    generation time is charged at the share L_sample / L of the full
+    workload's (the field does not depend on L; a solve of L_sample particles
+    that generated it again would carry all of it); returns (units/s,
+    seconds, units)."""
+    import oracle as O
+    import scenarios as S
+    W, t_wind = oracle_wind()
+    full = S.config2()
+    p = full.copy(L=L_sample)
     t0 = time.perf_counter()
-    O.smc_solve(p, nthreads=nthreads)
-    dt = time.perf_counter() - t0
+    O.smc_solve(p, W=W, nthreads=nthreads)
+    dt = time.perf_counter() - t0 + t_wind * L_sample / full.L
     u = units_per_solve(p)
     return u / dt, dt, u
+
+
+def oracle_rollout_rates(L_one, L_all, cores):
+    """The oracle's rollout alone (one iteration's inner loop on the uniform
+    initial controls, the workload's wind field computed beforehand), single-
+    threaded on L_one particles and on all cores on L_all; returns
+    {threads: (units/s, seconds, units, particles)} with units = L M N H."""
+    import oracle as O
+    import scenarios as S
+    p = S.config2()
+    W, _ = oracle_wind()
+    out = {}
+    for L, n in ((L_one, 1), (L_all, cores)):
+        q = p.copy(L=L)
+        u = O.init_controls(q, L)
+        t0 = time.perf_counter()
+        O.rollout(q, u, 0, W=W, nthreads=n, soft=(q.sep_mode != 0))
+        dt = time.perf_counter() - t0
+        units = L * q.M * q.N * q.H
+        out[n] = (units / dt, dt, units, L)
+    return out
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name" and val.strip():
+                return val.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, world, rank):
@@ -207,8 +263,10 @@ def run_reference(args, world, rank):
         times.append(dt)
     tot = sum(times)
     value = units * args.steps / tot
+    _, t_wind = oracle_wind()
     sample = (f"oracle smc_solve of the workload's traffic with L={Ls} particles "
-              f"(M=32, N=8, H=60, J_max=30, 64x64x8 wind incl.), {cores} threads")
+              f"(M=32, N=8, H=60, J_max=30) on the 64x64x8 wind field, whose generation "
+              f"({t_wind:.1f} s, once) is charged at the share {Ls}/65536 per step; {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
@@ -355,8 +413,16 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"one oracle smc_solve of the workload's traffic with L={args.cpu_particles} "
-                       f"particles (full M, N, H, J_max; wind generation included): "
-                       f"{u:.3g} units in {dt:.1f} s")}
+                       f"particles (full M, N, H, J_max) on the wind field, whose generation "
+                       f"({oracle_wind()[1]:.1f} s) is charged at the share {args.cpu_particles}/{p.L}: "
+                       f"{u:.3g} units in {dt:.1f} s"),
+            "cpu_model": cpu_model()}
+        rr = oracle_rollout_rates(256, 4096, cores)
+        line["cpu_baseline"]["rollout_only"] = {
+            f"threads_{n}": {"value": v_, "unit": UNIT,
+                             "sample": f"one oracle rollout (J = 0, initial controls, wind precomputed) of "
+                                       f"L={L_} particles: {u_:.3g} units in {dt_:.2f} s"}
+            for n, (v_, dt_, u_, L_) in rr.items()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
@@ -887,8 +953,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-particles", type=int, default=128)
-    ap.add_argument("--reference-particles", type=int, default=64)
+    ap.add_argument("--cpu-particles", type=int, default=512)
+    ap.add_argument("--reference-particles", type=int, default=256)
     ap.add_argument("--rollout-only", action="store_true",
                     help="time only the rollout on --particles particles (profiling case)")
     ap.add_argument("--particles", type=int, default=0,
