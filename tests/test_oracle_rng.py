@@ -94,6 +94,23 @@ def test_box_muller_is_standard_normal():
     assert abs(stats.kurtosis(z0)) < 0.1
 
 
+def test_box_muller_inverts_to_its_uniforms():
+    """The inverse of the polar transform recovers the two uniforms: the
+    squared radius z0^2 + z1^2 = -2 ln u_a and the angle atan2(z1, z0) = 2 pi u_b
+    (mod 2 pi), u_a from the first word and u_b from the second.  A swapped
+    word, a swapped sine and cosine, a sign or a factor in the radius fails."""
+    rng = np.random.default_rng(11)
+    words = [(int(a), int(b)) for a, b in rng.integers(0, 2 ** 32, size=(2000, 2), dtype=np.uint64)]
+    words += [(0, 0), (0xFFFFFFFF, 0x80000000), (0x80000000, 0xFFFFFFFF), (12345, 0x40000000)]
+    for xa, xb in words:
+        z0, z1 = O.box_muller(xa, xb)
+        ua, ub = O.uniform23(xa), O.uniform23(xb)
+        assert math.exp(-0.5 * (z0 * z0 + z1 * z1)) == pytest.approx(ua, rel=1e-12, abs=1e-300)
+        ang = math.atan2(z1, z0) / (2 * math.pi) % 1.0
+        d = abs(ang - ub)
+        assert min(d, 1.0 - d) < 1e-12, (xa, xb, ang, ub)
+
+
 def test_draw_counter_layout_and_scenario_key():
     p = S.config1().copy(mpc_step=3, scenario_id=5)
     s = (p.seed + 5 * 0x9E3779B97F4A7C15) & (2 ** 64 - 1)
