@@ -225,7 +225,7 @@ def oracle_rollout_rates(L_one, L_all, cores):
     p = S.config2()
     W, _ = oracle_wind()
     out = {}
-    for L, n in ((L_one, 1), (L_all, cores)):
+    for L, n in ((L_one, 1), (L_all, cores)) if cores > 1 else ((L_one, 1),):
         q = p.copy(L=L)
         u = O.init_controls(q, L)
         t0 = time.perf_counter()
