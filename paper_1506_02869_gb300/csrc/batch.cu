@@ -38,6 +38,10 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fm
 // ------------------------------------------------------------------ rollout
 
 
+// OwnWind: wind mode 1 (the same for every scenario of a batch), fixed at
+// compile time so that the kernel holds only the two tile forms it can run
+// (with and without the rolling window) within its 64 registers.
+template <bool OwnWind>
 __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
     const ProblemC *__restrict__ probs, const BatchScen *__restrict__ scen, int n_scen,
     const DynState *__restrict__ dyns, const float *__restrict__ u, const float4 *__restrict__ W,
@@ -82,10 +86,14 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
                 if (it >= items) break;
                 const int m = (int)(it / nLb);
                 const long long l0 = (it - (long long)m * nLb) * kPB;
-                const TileResult r = rollout_tile(
-                    Ps, dyns + s, u + Sc.u_off, W + Sc.w_off + (size_t)m * Ps.H * Ps.P, L, l0, i, lane,
-                    m, J, cost_ms_soft != nullptr, spos + (size_t)q * tile_smem_words(Ns, Ps.wind_mode),
-                    bar, cnt);
+                const float4 *Wm = W + Sc.w_off + (size_t)m * Ps.H * Ps.P;
+                float *sp = spos + (size_t)q * tile_smem_words(Ns, Ps.wind_mode);
+                const bool soft_on = cost_ms_soft != nullptr;
+                const TileResult r =
+                    Ps.rolling ? rollout_tile_mode<OwnWind, true, false>(Ps, dyns + s, u + Sc.u_off, Wm, L, l0, i,
+                                                                         lane, m, J, soft_on, sp, bar, cnt)
+                               : rollout_tile_mode<OwnWind, false, false>(Ps, dyns + s, u + Sc.u_off, Wm, L, l0,
+                                                                          i, lane, m, J, soft_on, sp, bar, cnt);
                 const size_t cbase = (size_t)Sc.seg_off * Ps.M * (size_t)L;
                 store_tile(r, Ns, L, l0 + lane, i, lane, m, cost_ms + cbase,
                            cost_ms_soft ? cost_ms_soft + cbase : nullptr, live);
@@ -427,14 +435,18 @@ cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, i
                                  const DynState *dyns, const float *u, const float *W, long long L,
                                  int J, int Mj, float *cost_ms, float *cost_ms_soft,
                                  unsigned long long *live, unsigned long long *claimed, int grid,
-                                 cudaStream_t st)
+                                 int wind_mode, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(claimed, 0, sizeof(unsigned long long) * (size_t)n_scen, st);
     if (e != cudaSuccess) return e;
     const int nLb = (int)((L + kPB - 1) / kPB);
-    rollout_batched_kernel<<<grid, 1024, batch_rollout_smem(), st>>>(
-        probs, scen, n_scen, dyns, u, reinterpret_cast<const float4 *>(W), L, nLb, J, Mj, cost_ms,
-        cost_ms_soft, live, claimed);
+    const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    if (wind_mode == 1)
+        rollout_batched_kernel<true><<<grid, 1024, batch_rollout_smem(), st>>>(
+            probs, scen, n_scen, dyns, u, W4, L, nLb, J, Mj, cost_ms, cost_ms_soft, live, claimed);
+    else
+        rollout_batched_kernel<false><<<grid, 1024, batch_rollout_smem(), st>>>(
+            probs, scen, n_scen, dyns, u, W4, L, nLb, J, Mj, cost_ms, cost_ms_soft, live, claimed);
     count_launch();
     return cudaGetLastError();
 }
@@ -444,12 +456,18 @@ int batch_rollout_grid()
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(rollout_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(rollout_batched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)batch_rollout_smem());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_batched_kernel, 1024,
+    cudaFuncSetAttribute(rollout_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batch_rollout_smem());
+    // both instances: 1024 threads, the same shared memory, 64 registers
+    int per_sm1 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_batched_kernel<false>, 1024,
                                                       batch_rollout_smem()) != cudaSuccess ||
-        per_sm < 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, rollout_batched_kernel<true>, 1024,
+                                                      batch_rollout_smem()) != cudaSuccess)
         per_sm = 1;
+    per_sm = std::max(1, std::min(per_sm, per_sm1));
     return sms * per_sm;
 }
 

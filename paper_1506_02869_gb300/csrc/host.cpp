@@ -1638,7 +1638,7 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
         TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, b->d_u[cur],
                                       b->d_W, L, J, Mj, b->d_cost_ms,
                                       soft ? b->d_cost_ms_soft : nullptr, b->d_live, b->d_queue,
-                                      b->grid, st));
+                                      b->grid, b->probs[0].wind_mode, st));
         TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms, b->d_scen, b->d_seg_scen, b->nseg, L, b->M,
                                           Mj, b->d_cbar, st));
         if (soft)

@@ -188,7 +188,7 @@ cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, i
                                  const DynState *dyns, const float *u, const float *W, long long L,
                                  int J, int Mj, float *cost_ms, float *cost_ms_soft,
                                  unsigned long long *live, unsigned long long *claimed, int grid,
-                                 cudaStream_t st);
+                                 int wind_mode, cudaStream_t st);
 cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen,
                                      const int *seg_scen, long long nseg, long long L, int M,
                                      int Mj, float *cbar, cudaStream_t st);
