@@ -68,8 +68,8 @@ def flops_per_unit(p):
 # workload per rollout kernel, from a one-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, iteration 20 of a solve);
 # valid only for the kernel sources they were taken on.
-ROLLOUT_TRAFFIC = {"sources_sha256_16": "602872d0269a3e2d",
-                   "bytes_per_launch": {"rollout_kernel": 1001319680 + 68082944}}
+ROLLOUT_TRAFFIC = {"sources_sha256_16": "6aaf6fb629fdd898",
+                   "bytes_per_launch": {"rollout_kernel": 1000901376 + 68202496}}
 
 
 def rollout_kernel_name(variant):

@@ -462,7 +462,7 @@ struct TileResult {
 // ParamP: P is the kernel's parameter (the plain kernels): the aircraft's
 // constants are copied into registers once (a reference into the parameter
 // space reloads them at every use) and the turbulence draws take the
-// precomputed round keys.  The batched kernel reads P from global memory and
+// precomputed round keys.  The batched kernel holds P in shared memory and
 // keeps the reference, its register budget is full.
 template <bool OwnWind, bool Rolling, bool ParamP = true>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
@@ -599,24 +599,6 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     }
     r.live = exists ? nlive : 0u;
     return r;
-}
-
-__device__ __forceinline__ TileResult rollout_tile(const ProblemC &P, const DynState *__restrict__ dyn,
-                                                   const float *__restrict__ u,
-                                                   const float4 *__restrict__ Wm, long long L,
-                                                   long long l0, int i, int j, int m, int J,
-                                                   bool soft_on, float *spos, int bar_id,
-                                                   int bar_count)
-{
-    if (P.wind_mode == 1)
-        return P.rolling ? rollout_tile_mode<true, true, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
-                                                         bar_id, bar_count)
-                         : rollout_tile_mode<true, false, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
-                                                          bar_id, bar_count);
-    return P.rolling ? rollout_tile_mode<false, true, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
-                                                      bar_id, bar_count)
-                     : rollout_tile_mode<false, false, false>(P, dyn, u, Wm, L, l0, i, j, m, J, soft_on, spos,
-                                                       bar_id, bar_count);
 }
 
 // Stores one thread's tile result: cost_ms[(m N + i) L + l] (and the soft
