@@ -380,8 +380,9 @@ tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_str
 /* Many independent TMA scenarios solved together (receding-horizon MPC per
  * scenario, Sec. 2; Algorithm 1 each).  Scenarios may differ in aircraft
  * (N_s = 1..32, states, targets, coefficients), weights, control box and
- * seeds; they must share L, M, H, S, J_max, dt, sep_mode and the wind model
- * (grid, box, rates, sigma).  Weight segments are (scenario, aircraft) pairs,
+ * seeds; they must share L, M, H, S, J_max, dt, sep_mode, sample_mode and the
+ * wind model (wind_mode, grid, box, rates, sigma); otherwise
+ * TMA_ERR_INVALID_ARG.  Weight segments are (scenario, aircraft) pairs,
  * at most 65535 in total.  aircraft[s] points to probs[s].N records.
  * The rollout of all scenarios is one persistent launch over a work queue. */
 typedef struct tma_batch tma_batch;
