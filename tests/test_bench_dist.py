@@ -53,3 +53,27 @@ def test_units_and_flops_per_unit():
     assert 150 < f < 260
     assert bench.flops_per_unit(S.config3()) > f          # more pairs, soft form, noise
     assert bench.fp32_peak_tflops(2070) == pytest.approx(80.54, rel=1e-3)
+
+
+def test_oracle_sample_charges_the_wind_generation_at_its_share(monkeypatch):
+    """The CPU baseline's solve runs on the workload's wind field, generated
+    once; the generation time enters each sample at the share L_sample / L."""
+    import time
+
+    import oracle as O
+    seen = []
+    monkeypatch.setattr(O, "wind_field", lambda p: (time.sleep(0.25), "field")[1])
+    monkeypatch.setattr(O, "smc_solve", lambda p, W=None, nthreads=1: seen.append((p.L, W, nthreads)))
+    bench._ORACLE_WIND.clear()
+    try:
+        v, dt, units = bench.oracle_sample(512, 3)
+        _, dt2, _ = bench.oracle_sample(512, 3)          # the field is not generated again
+        t_wind = bench.oracle_wind()[1]
+    finally:
+        bench._ORACLE_WIND.clear()
+    assert seen == [(512, "field", 3), (512, "field", 3)]
+    assert units == 512 * 32 * 8 * 60 * 30
+    assert t_wind >= 0.25
+    share = t_wind * 512 / 65536
+    assert share <= dt < share + 0.05 and share <= dt2 < share + 0.05
+    assert v == pytest.approx(units / dt)
