@@ -38,10 +38,11 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fm
 // ------------------------------------------------------------------ rollout
 
 
-// OwnWind: wind mode 1 (the same for every scenario of a batch), fixed at
-// compile time so that the kernel holds only the two tile forms it can run
-// (with and without the rolling window) within its 64 registers.
-template <bool OwnWind>
+// OwnWind: wind mode 1 and Soft: the softplus penalties evaluated (both the
+// same for every scenario of a batch), fixed at compile time so that the
+// kernel holds only the two tile forms it can run (with and without the
+// rolling window) within its 64 registers.
+template <bool OwnWind, bool Soft>
 __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
     const ProblemC *__restrict__ probs, const BatchScen *__restrict__ scen, int n_scen,
     const DynState *__restrict__ dyns, const float *__restrict__ u, const float4 *__restrict__ W,
@@ -88,12 +89,11 @@ __global__ void __launch_bounds__(1024, 1) rollout_batched_kernel(
                 const long long l0 = (it - (long long)m * nLb) * kPB;
                 const float4 *Wm = W + Sc.w_off + (size_t)m * Ps.H * Ps.P;
                 float *sp = spos + (size_t)q * tile_smem_words(Ns, Ps.wind_mode);
-                const bool soft_on = cost_ms_soft != nullptr;
                 const TileResult r =
-                    Ps.rolling ? rollout_tile_mode<OwnWind, true, false>(Ps, dyns + s, u + Sc.u_off, Wm, L, l0, i,
-                                                                         lane, m, J, soft_on, sp, bar, cnt)
-                               : rollout_tile_mode<OwnWind, false, false>(Ps, dyns + s, u + Sc.u_off, Wm, L, l0,
-                                                                          i, lane, m, J, soft_on, sp, bar, cnt);
+                    Ps.rolling ? rollout_tile_mode<OwnWind, true, Soft, false>(Ps, dyns + s, u + Sc.u_off, Wm, L,
+                                                                               l0, i, lane, m, J, sp, bar, cnt)
+                               : rollout_tile_mode<OwnWind, false, Soft, false>(Ps, dyns + s, u + Sc.u_off, Wm, L,
+                                                                                l0, i, lane, m, J, sp, bar, cnt);
                 const size_t cbase = (size_t)Sc.seg_off * Ps.M * (size_t)L;
                 store_tile(r, Ns, L, l0 + lane, i, lane, m, cost_ms + cbase,
                            cost_ms_soft ? cost_ms_soft + cbase : nullptr, live);
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) batch_move(const BatchScen *__restrict__ 
                                                   const DynState *__restrict__ dyns, long long nseg,
                                                   long long L, int S, const float *__restrict__ u,
                                                   const int32_t *__restrict__ anc, int J,
-                                                  float *__restrict__ u_out)
+                                                  float *__restrict__ u_out, unsigned int *__restrict__ err)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nseg * L) return;
@@ -147,7 +147,10 @@ __global__ void __launch_bounds__(256) batch_move(const BatchScen *__restrict__ 
     const BatchScen sc = scen[s];
     const int i = (int)(seg - sc.seg_off);
     int a = __ldg(anc + t);
-    if ((unsigned long long)a >= (unsigned long long)L) a = (int)l;
+    if ((unsigned long long)a >= (unsigned long long)L) {   // reported, and a defined parent kept
+        if (err) atomicOr(err, TMA_DEVERR_BOUNDS);
+        a = (int)l;
+    }
     const int nc = 3 * (kS > 0 ? kS : S);
     const float *src = u + sc.u_off + ((size_t)a * sc.N + i) * nc;
     float *dst = u_out + sc.u_off + ((size_t)l * sc.N + i) * nc;
@@ -441,12 +444,17 @@ cudaError_t launch_batch_rollout(const ProblemC *probs, const BatchScen *scen, i
     if (e != cudaSuccess) return e;
     const int nLb = (int)((L + kPB - 1) / kPB);
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
-    if (wind_mode == 1)
-        rollout_batched_kernel<true><<<grid, 1024, batch_rollout_smem(), st>>>(
-            probs, scen, n_scen, dyns, u, W4, L, nLb, J, Mj, cost_ms, cost_ms_soft, live, claimed);
-    else
-        rollout_batched_kernel<false><<<grid, 1024, batch_rollout_smem(), st>>>(
-            probs, scen, n_scen, dyns, u, W4, L, nLb, J, Mj, cost_ms, cost_ms_soft, live, claimed);
+#define TMA_BATCH_K(O, F)                                                                        \
+    rollout_batched_kernel<O, F><<<grid, 1024, batch_rollout_smem(), st>>>(                      \
+        probs, scen, n_scen, dyns, u, W4, L, nLb, J, Mj, cost_ms, cost_ms_soft, live, claimed)
+    if (wind_mode == 1) {
+        if (cost_ms_soft) TMA_BATCH_K(true, true);
+        else TMA_BATCH_K(true, false);
+    } else {
+        if (cost_ms_soft) TMA_BATCH_K(false, true);
+        else TMA_BATCH_K(false, false);
+    }
+#undef TMA_BATCH_K
     count_launch();
     return cudaGetLastError();
 }
@@ -456,18 +464,19 @@ int batch_rollout_grid()
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(rollout_batched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)batch_rollout_smem());
-    cudaFuncSetAttribute(rollout_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)batch_rollout_smem());
-    // both instances: 1024 threads, the same shared memory, 64 registers
-    int per_sm1 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_batched_kernel<false>, 1024,
-                                                      batch_rollout_smem()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, rollout_batched_kernel<true>, 1024,
-                                                      batch_rollout_smem()) != cudaSuccess)
-        per_sm = 1;
-    per_sm = std::max(1, std::min(per_sm, per_sm1));
+    // every instance: 1024 threads, the same shared memory, 64 registers
+    const void *kernels[] = {(const void *)rollout_batched_kernel<false, false>,
+                             (const void *)rollout_batched_kernel<false, true>,
+                             (const void *)rollout_batched_kernel<true, false>,
+                             (const void *)rollout_batched_kernel<true, true>};
+    per_sm = 1 << 30;
+    for (const void *k : kernels) {
+        int n = 0;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_rollout_smem());
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 1024, batch_rollout_smem()) != cudaSuccess) n = 1;
+        per_sm = std::min(per_sm, n);
+    }
+    per_sm = std::max(1, per_sm);
     return sms * per_sm;
 }
 
@@ -483,12 +492,14 @@ cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen
 
 cudaError_t launch_batch_move(const BatchScen *scen, const int *seg_scen, const DynState *dyns,
                               long long nseg, long long L, int S, const float *u,
-                              const int32_t *anc, int J, float *u_out, cudaStream_t st)
+                              const int32_t *anc, int J, float *u_out, cudaStream_t st, unsigned int *err)
 {
     if (S == 4)
-        batch_move<4><<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J, u_out);
+        batch_move<4><<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J,
+                                                                 u_out, err);
     else
-        batch_move<<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J, u_out);
+        batch_move<<<blocks_for(nseg * L, 256), 256, 0, st>>>(scen, seg_scen, dyns, nseg, L, S, u, anc, J, u_out,
+                                                              err);
     count_launch();
     return cudaGetLastError();
 }

@@ -22,7 +22,7 @@ namespace {
 // among the variants whose cap fits the block (32 * N threads).  OwnWind is
 // wind mode 1 (per-particle fields) and Rolling the rolling window, each a
 // kernel of its own so that the plain problem keeps its register allocation.
-template <int kMaxThreads, int kMinBlocks, bool OwnWind, bool Rolling>
+template <int kMaxThreads, int kMinBlocks, bool OwnWind, bool Rolling, bool Soft>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const ProblemC P,
                                                        const DynState *__restrict__ dyn,
                                                        const float *__restrict__ u,
@@ -35,9 +35,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const 
     const int m = blockIdx.x / nLb;            // wind sample: block-uniform
     const long long l0 = (long long)(blockIdx.x - m * nLb) * kPB;
     const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
-    const TileResult r = rollout_tile_mode<OwnWind, Rolling>(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0,
-                                                             i, j, m, J, cost_ms_soft != nullptr, spos, 0,
-                                                             blockDim.x);
+    const TileResult r = rollout_tile_mode<OwnWind, Rolling, Soft>(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0,
+                                                                   i, j, m, J, spos, 0, blockDim.x);
     store_tile(r, P.N, L, l0 + j, i, j, m, cost_ms, cost_ms_soft, live);
 }
 
@@ -105,13 +104,18 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
     const size_t smem = (size_t)tile_smem_words(P.N, P.wind_mode) * sizeof(float);
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
     // above the default 48 KB of dynamic shared memory the kernel must opt in
-#define TMA_ROLLOUT_K(T, B, O, R)                                                                \
+#define TMA_ROLLOUT_KS(T, B, O, R, F)                                                            \
     do {                                                                                         \
         if (smem > 48 * 1024)                                                                    \
-            cudaFuncSetAttribute(rollout_kernel<T, B, O, R>,                                     \
+            cudaFuncSetAttribute(rollout_kernel<T, B, O, R, F>,                                  \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        rollout_kernel<T, B, O, R><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J,     \
-                                                              cost_ms, cost_ms_soft, live);      \
+        rollout_kernel<T, B, O, R, F><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J,  \
+                                                                 cost_ms, cost_ms_soft, live);   \
+    } while (0)
+#define TMA_ROLLOUT_K(T, B, O, R)                                                                \
+    do {                                                                                         \
+        if (cost_ms_soft) TMA_ROLLOUT_KS(T, B, O, R, true);                                      \
+        else TMA_ROLLOUT_KS(T, B, O, R, false);                                                  \
     } while (0)
 #define TMA_ROLLOUT(T, B)                                                                        \
     do {                                                                                         \
@@ -135,6 +139,7 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
     }
 #undef TMA_ROLLOUT
 #undef TMA_ROLLOUT_K
+#undef TMA_ROLLOUT_KS
     count_launch();
     return cudaGetLastError();
 }

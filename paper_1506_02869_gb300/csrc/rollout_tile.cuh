@@ -136,6 +136,8 @@ __device__ __forceinline__ float softplus(float g, float beta, float inv_beta)
 }
 
 constexpr int kPB = kTileParticles;
+// partners screened per group (the group's loads in flight together)
+constexpr int kScreen = 2;
 
 // Mode-1 wind (a field per (particle, sample) on the 2x2x2 grid of the box
 // corners, the paper's scheme): the state B of the particle's eight nodes lives
@@ -425,51 +427,62 @@ __device__ __forceinline__ float total_objective(const ProblemC &P, const Aircra
     return (1.0f - P.w_noise) * Jsum + P.w_noise * fmaf(-c.sN, invH, 1.0f);
 }
 
-// Shared memory of one tile (32-bit words): positions float4 [2][2N][32]
+// Shared memory of one tile (32-bit words): positions float4 [2][2N + 4][32]
 // (double-buffered by step; every aircraft's row written twice, at i and
 // i + N, so that the partners i+1 .. i+N/2 are consecutive rows without a
-// wrap), separation flags [N][32], the received separation penalties
-// [2][N][floor((N-1)/2) + 1][32] of the soft form, and in wind mode 1 the
-// particles' wind state [2][16][32].
+// wrap; the screening pass reads partners in groups, up to kScreen - 1 rows
+// past the last, which the four spare rows hold), separation flags [N][32],
+// the soft form's received penalties [2][N][floor((N-1)/2) + 1][32] with a
+// word per (step parity, aircraft, particle) marking the slots written
+// [2][N][32], and in wind mode 1 the particles' wind state [2][16][32].
 __host__ __device__ constexpr int tile_pair_slots(int N) { return (N - 1) / 2 + 1; }
+__host__ __device__ constexpr int tile_pos_rows(int N) { return 2 * N + 4; }
 __host__ __device__ constexpr int tile_smem_words(int N, int wind_mode)
 {
-    return (17 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) * kTileParticles;
+    return (4 * 2 * tile_pos_rows(N) + N + 2 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) *
+           kTileParticles;
 }
 
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
 // packed wind field Wm of sample m and returns its per-sample costs (the
-// softplus variant when soft_on); the caller stores them (store_tile), so
+// softplus variant too when Soft); the caller stores them (store_tile), so
 // that no output pointer is live during the steps.  spos is the tile's
 // tile_smem_words(N, P.wind_mode) buffer; every warp of the tile must call this
 // with the same barrier (bar_id, bar_count threads).
 //
 // Separation (Eq. (avoidance)) checks every unordered pair once: warp i takes
 // the partners i+d, d = 1 .. floor((N-1)/2) (mod N), and for even N also
-// d = N/2 when i < N/2, so every warp has the same load.  A violation marks both
-// aircraft (the partner through its flag in shared memory).  The softplus
-// penalty of a pair enters both aircraft's costs: the owner adds it and stores
-// it in the partner's slot d-1; after the next step's barrier every aircraft
-// adds its received slots in a fixed order (deterministic sums).
+// d = N/2 when i < N/2, so every warp has the same load.  A violation marks
+// both aircraft (the partner through its flag in shared memory).  In the soft
+// form a branch-free screening pass first marks the partners within reach (the
+// distance beyond which the penalty is below e^-30 / beta, a region that
+// contains the hard one); only a warp with a lane within reach of some partner
+// evaluates those pairs (the softplus and the hard test).  The softplus
+// penalty of a pair enters both aircraft's costs: the owner adds it, stores it
+// in the partner's slot d and sets bit d of the partner's mark word; after the
+// next step's barrier every aircraft adds its marked slots in increasing d and
+// clears the word (deterministic sums; a pair out of reach has penalty 0,
+// which neither side adds).
 struct TileResult {
     float cost;         // -ln J_T, +inf if infeasible or separation violated (hard)
     float cost_soft;    // with the softplus penalty, +inf if infeasible
     unsigned int live;  // aircraft-steps simulated by this thread
 };
 
-// OwnWind: wind mode 1; Rolling: the rolling window (each compiled apart, so
-// the plain problem keeps its register budget).
+// OwnWind: wind mode 1; Rolling: the rolling window; Soft: the softplus
+// penalties are evaluated and exchanged besides the hard test (each compiled
+// apart, so the plain problem keeps its register budget).
 // ParamP: P is the kernel's parameter (the plain kernels): the aircraft's
 // constants are copied into registers once (a reference into the parameter
 // space reloads them at every use) and the turbulence draws take the
 // precomputed round keys.  The batched kernel holds P in shared memory and
 // keeps the reference, its register budget is full.
-template <bool OwnWind, bool Rolling, bool ParamP = true>
+template <bool OwnWind, bool Rolling, bool Soft, bool ParamP = true>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
                                                         const float *__restrict__ u,
                                                         const float4 *__restrict__ Wm, long long L,
                                                         long long l0, int i, int j, int m, int J,
-                                                        bool soft_on, float *spos, int bar_id,
+                                                        float *spos, int bar_id,
                                                         int bar_count)
 {
     const int N = P.N;
@@ -506,17 +519,24 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     const float *ul = u + ((size_t)(exists ? l : 0) * N + i) * (size_t)(P.S * 3);
     unsigned int nlive = 0;
     const int plane = N * kPB;
-    float4 *pos = reinterpret_cast<float4 *>(spos);                 // [2][2N][32]
-    int *vflag = reinterpret_cast<int *>(spos + 16 * plane);       // [N][32]
-    float *recv = spos + 17 * plane;                                // [2][N][slots][32]
+    const int rows = tile_pos_rows(N);
+    float4 *pos = reinterpret_cast<float4 *>(spos);                          // [2][2N + 4][32]
+    int *vflag = reinterpret_cast<int *>(spos + 8 * rows * kPB);            // [N][32]
+    unsigned *rmark = reinterpret_cast<unsigned *>(vflag + plane);         // [2][N][32]
+    float *recv = reinterpret_cast<float *>(rmark + 2 * plane);           // [2][N][slots][32]
     const int slots = tile_pair_slots(N);
-    vflag[i * kPB + j] = 0;       // ordered before any partner's mark by the step-0 barrier
+    // ordered before any partner's mark by the step-0 (and step-1) barrier
+    vflag[i * kPB + j] = 0;
+    if constexpr (Soft) {
+        rmark[i * kPB + j] = 0u;
+        rmark[plane + i * kPB + j] = 0u;
+    }
     const int n_half = (N - 1) >> 1;
     const bool even = (N & 1) == 0;
-    const int n_pairs = n_half + ((even && i < (N >> 1)) ? 1 : 0);
-    const int n_recv = n_half + ((even && i >= (N >> 1)) ? 1 : 0);
+    const int n_pairs = n_half + ((even && i < (N >> 1)) ? 1 : 0);   // at most 16
+    const unsigned pair_bits = (1u << n_pairs) - 1u;
     constexpr bool own_wind = OwnWind;
-    float *pw = spos + (17 * N + 2 * N * slots) * kPB;     // mode 1: [2][16][32]
+    float *pw = recv + 2 * N * slots * kPB;                               // mode 1: [2][16][32]
     if constexpr (own_wind) {
         particle_wind_step(P, pw, i, N, j, (uint32_t)l, m, 0, mpc);
         tile_barrier(bar_id, bar_count);
@@ -534,7 +554,7 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
         // binary separation constraints at step k+1 among flying aircraft: every
         // thread publishes its position (a far-away altitude when not flying)
         const bool act = !s.dead && !s.landed && entered;
-        float4 *buf = pos + (k & 1) * 2 * plane;
+        float4 *buf = pos + (k & 1) * rows * kPB;
         const float4 me = make_float4(s.x, s.y, act ? s.z : 1e30f, 0.0f);
         buf[i * kPB + j] = me;
         buf[(i + N) * kPB + j] = me;
@@ -542,32 +562,59 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
         // partner i + 1 + d is row i + 1 + d of buf (no wrap); its index mod N
         // only where a mark or a penalty slot is written
         const float4 *qrow = buf + (i + 1) * kPB + j;
-        if (soft_on) {
-            // penalties the partners computed for this aircraft at the previous step
+        if constexpr (Soft) {
+            // penalties the partners marked for this aircraft at the previous step
             if (k > 0) {
-                const float *rr = recv + ((((k - 1) & 1) * N + i) * slots) * kPB + j;
-                for (int d = 0; d < n_recv; ++d) soft += rr[d * kPB];
+                unsigned *mw = rmark + ((k - 1) & 1) * plane + i * kPB + j;
+                unsigned rm = *mw;
+                if (rm != 0u) {
+                    *mw = 0u;
+                    const float *rr = recv + ((((k - 1) & 1) * N + i) * slots) * kPB + j;
+                    do {
+                        soft += rr[(__ffs(rm) - 1) * kPB];
+                        rm &= rm - 1u;
+                    } while (rm != 0u);
+                }
             }
-            float *rw = recv + ((k & 1) * N * slots) * kPB + j;
-            for (int d = 0; d < n_pairs; ++d) {
-                const int i2 = i + 1 + d < N ? i + 1 + d : i + 1 + d - N;
-                const float4 q = qrow[d * kPB];
-                const float dx = s.x - q.x, dy = s.y - q.y, adz = fabsf(s.z - q.z);
-                const float dh2 = fmaf(dx, dx, dy * dy);
-                float pen = 0.0f;
-                if (act) {
+            // screening in groups of kScreen partners: bit d set when partner d
+            // is within reach
+            unsigned near = 0u;
+#pragma unroll
+            for (int d0 = 0; d0 < 16; d0 += kScreen) {
+                if (d0 < n_pairs) {
+#pragma unroll
+                    for (int e = 0; e < kScreen; ++e) {
+                        const float4 q = qrow[(d0 + e) * kPB];
+                        const float dx = s.x - q.x, dy = s.y - q.y;
+                        if (fmaf(dx, dx, dy * dy) < P.sp_far_h2 && fabsf(s.z - q.z) < P.sp_far_v)
+                            near |= 1u << (d0 + e);
+                    }
+                }
+            }
+            near = act ? (near & pair_bits) : 0u;
+            if (__any_sync(0xffffffffu, near != 0u)) {
+                float *rw = recv + ((k & 1) * N * slots) * kPB + j;
+                unsigned *mark = rmark + (k & 1) * plane + j;
+                while (near != 0u) {
+                    const int d = __ffs(near) - 1;
+                    near &= near - 1u;
+                    const int i2 = i + 1 + d < N ? i + 1 + d : i + 1 + d - N;
+                    const float4 q = qrow[d * kPB];
+                    const float dx = s.x - q.x, dy = s.y - q.y, adz = fabsf(s.z - q.z);
+                    const float dh2 = fmaf(dx, dx, dy * dy);
                     if (dh2 < P.Sh2 && adz < P.Sv) {
                         sepv = true;
                         vflag[i2 * kPB + j] = 1;
                     }
-                    if (dh2 < P.sp_far_h2 && adz < P.sp_far_v)   // else below e^-30 / beta
-                        pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
-                                       P.sp_beta, P.sp_inv_beta);
+                    const float pen = softplus(fminf(fmaf(-sqrtf(dh2), P.Sh_inv, 1.0f), fmaf(-adz, P.Sv_inv, 1.0f)),
+                                               P.sp_beta, P.sp_inv_beta);
                     soft += pen;
+                    rw[(i2 * slots + d) * kPB] = pen;
+                    atomicOr(mark + i2 * kPB, 1u << d);
                 }
-                rw[(i2 * slots + d) * kPB] = pen;
             }
         } else if (act) {
+            // hard form: a violation is rare, its branch almost never taken
             for (int d = 0; d < n_pairs; ++d) {
                 const float4 q = qrow[d * kPB];
                 const float dx = s.x - q.x, dy = s.y - q.y;
@@ -582,9 +629,10 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     // marks and penalties the partners wrote at the last step
     tile_barrier(bar_id, bar_count);
     sepv = sepv || vflag[i * kPB + j] != 0;
-    if (soft_on) {
+    if constexpr (Soft) {
+        unsigned rm = rmark[((P.H - 1) & 1) * plane + i * kPB + j];
         const float *rr = recv + ((((P.H - 1) & 1) * N + i) * slots) * kPB + j;
-        for (int d = 0; d < n_recv; ++d) soft += rr[d * kPB];
+        for (; rm != 0u; rm &= rm - 1u) soft += rr[(__ffs(rm) - 1) * kPB];
     }
 
     // the per-sample cost -ln J_T (Sec. 3.6)
