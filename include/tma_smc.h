@@ -57,6 +57,11 @@ typedef enum {
 #define TMA_MAX_GRAD_HORIZON 320     /* H of tma_rollout_grad: checkpoints kept per thread */
 
 /* Move kinds of tma_set_move. */
+/* Bits of the sticky device error word (tma_get_error, tma_batch_results). */
+#define TMA_DEVERR_DEGENERATE 1u  /* some weight segment was all zero: identity ancestors used */
+#define TMA_DEVERR_INFEASIBLE 2u  /* the chosen particle had an infeasible aircraft */
+#define TMA_DEVERR_BOUNDS 4u      /* a perturbation read an ancestor index out of range */
+
 #define TMA_MOVE_PAPER 0   /* Gaussian random walk, clipped, no accept step (Algorithm 1) */
 #define TMA_MOVE_RWMH 1    /* random walk with a Metropolis-Hastings accept step */
 #define TMA_MOVE_MALA 2    /* Langevin proposal (gradient of the soft cost) with accept step */
@@ -199,9 +204,11 @@ tma_status tma_move(tma_solver *s, const float *d_u, const int32_t *d_anc, int64
 
 /* The perturbation with another number of parents (varying particle count,
  * Sec. 9): L children d_u_out[L][N][S][3] from the L_in parents d_u[L_in],
- * d_anc[N][L] in [0, L_in) (tma_resample_to's output); an out-of-range
- * ancestor is replaced by min(l, L_in - 1).  L, L_in <= the solver's L;
- * tma_move is this call with L_in = L. */
+ * d_anc[N][L] in [0, L_in) (tma_resample_to's output).  An out-of-range
+ * ancestor sets TMA_DEVERR_BOUNDS in the solver's sticky device error word
+ * (tma_get_error then returns TMA_ERR_BOUNDS) and the child takes the parent
+ * min(l, L_in - 1), so every output is defined; nothing traps.  L, L_in <= the
+ * solver's L; tma_move is this call with L_in = L. */
 tma_status tma_move_to(tma_solver *s, const float *d_u, int64_t L_in, const int32_t *d_anc, int64_t L,
                        int32_t J, float *d_u_out, tma_stream_t stream);
 
@@ -355,10 +362,13 @@ tma_status tma_plant_step(tma_solver *s, const float *d_u, tma_stream_t stream);
 tma_status tma_mpc_run(tma_solver *s, int32_t n_steps, tma_state *h_traj, double *h_costs,
                        tma_stream_t stream);
 
-/* Sticky device status of the solves since the last call: bit 0 some weight
- * segment was all zero (identity ancestors were used), bit 1 the chosen
- * particle had an infeasible aircraft (no particle satisfied every limit).
- * Clears the word; syncs. */
+/* Sticky device status of the solves and stage calls since the last call, in
+ * *h_err: TMA_DEVERR_DEGENERATE (bit 0) some weight segment was all zero
+ * (identity ancestors were used), TMA_DEVERR_INFEASIBLE (bit 1) the chosen
+ * particle had an infeasible aircraft (no particle satisfied every limit),
+ * TMA_DEVERR_BOUNDS (bit 2) a perturbation met an ancestor index out of range.
+ * Clears the word; syncs.  Returns TMA_ERR_BOUNDS when bit 2 was set (the word
+ * is written all the same), else TMA_OK. */
 tma_status tma_get_error(tma_solver *s, uint32_t *h_err, tma_stream_t stream);
 
 /* Rolling window: set the mask of aircraft that have left the problem (bit i =
@@ -401,10 +411,27 @@ tma_status tma_batch_solve(tma_batch *b, tma_stream_t stream);
  * into a CUDA graph (re-captured when n_steps changes) and launched; the
  * results equal those without the graph. */
 tma_status tma_batch_mpc(tma_batch *b, int32_t n_steps, int32_t use_graph, tma_stream_t stream);
+/* The batched rollout alone (the persistent launch inside tma_batch_solve;
+ * Sec. 3.3-3.6 for every scenario), on given controls: generates every
+ * scenario's wind field for its current MPC step, then rolls out d_u at
+ * iteration J (the first SampleSchedule(J) samples in sample mode 1, else all
+ * M) and writes the per-sample costs.  Packed layouts, scenario after scenario
+ * (offsets by the aircraft counts N_s' of the scenarios s' before s):
+ *   d_u            [L][N_s][S][3] at float offset L * 3S * sum N_s' (device, in)
+ *   d_cost_ms      [M][N_s][L] at float offset M * L * sum N_s' (device, out):
+ *                  -ln J_T, +inf when infeasible or separated too little
+ *   d_cost_ms_soft the softplus form in the same layout (device, out; may be
+ *                  NULL; ignored when sep_mode = 0)
+ * All caller-owned; stream-ordered, no synchronisation.  Rows of samples not
+ * rolled out (sample mode 1) are left as they were. */
+tma_status tma_batch_rollout_cost(tma_batch *b, const float *d_u, int32_t J, float *d_cost_ms,
+                                  float *d_cost_ms_soft, tma_stream_t stream);
 /* Results of the last solve: chosen controls h_best_u (sum N_s x S x 3,
  * scenario-major), cost sums h_best_cost[n_scen], particle indices
  * h_best[n_scen]; current states h_x (sum N_s) and MPC steps h_mpc[n_scen].
- * Any pointer may be NULL; syncs. */
+ * Any pointer may be NULL; syncs.  Returns TMA_ERR_BOUNDS (the outputs are
+ * written all the same) when a perturbation since the last call met an
+ * ancestor index out of range (the batch's sticky error word, cleared here). */
 tma_status tma_batch_results(tma_batch *b, float *h_best_u, double *h_best_cost, int64_t *h_best,
                              tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream);
 /* Per-scenario solve latency of the last solve in ms: device clock from the
@@ -465,11 +492,6 @@ tma_status tma_lse_resample(const float *d_cbar, int32_t nseg, int64_t L, int64_
                             double *d_wtilde, int32_t *d_anc, uint32_t *d_degenerate, void *d_work,
                             size_t work_bytes, tma_stream_t stream);
 
-/* Final selection (Sec. 3.8): over particles l < L, the fewest aircraft with
- * infinite cost, then the smallest sum_i (double)cbar[i][l] summed in order
- * i = 0..N-1, ties to the lowest l.  Writes d_best (int64), d_best_sum (double;
- * +inf when the chosen particle has an infeasible aircraft), d_ninf (int32).
- * Scratch: d_work of tma_select_workspace() bytes. */
 /* Systematic resampling exactly as tma_resample, for callers that cannot
  * allocate device memory: a control loop that must never block in (or fail
  * inside) the CUDA allocator once it is running, or a host application whose
@@ -485,6 +507,9 @@ tma_status tma_lse_resample(const float *d_cbar, int32_t nseg, int64_t L, int64_
  *     degenerate-segment status.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     After cudaDeviceReset the next call on that device sees a new context
+ *     and looks the address up again (so does the first call after the
+ *     context was created, when an earlier call ran before it existed).
  *   - All calls share the one array, which keeps the last call's contents:
  *     calls that overlap on the GPU (different streams or threads at the same
  *     time) race and must be serialised by the caller. */
@@ -492,6 +517,11 @@ tma_status tma_resample_noalloc(const double *d_wtilde, int32_t nseg, int64_t L,
                                 uint32_t scenario_id, uint32_t J, uint32_t mpc_step, int32_t *d_anc,
                                 tma_stream_t stream);
 
+/* Final selection (Sec. 3.8): over particles l < L, the fewest aircraft with
+ * infinite cost, then the smallest sum_i (double)cbar[i][l] summed in order
+ * i = 0..N-1, ties to the lowest l.  Writes d_best (int64), d_best_sum (double;
+ * +inf when the chosen particle has an infeasible aircraft), d_ninf (int32).
+ * Scratch: d_work of tma_select_workspace() bytes. */
 size_t tma_select_workspace(int64_t L);
 tma_status tma_select(const float *d_cbar, int32_t N, int64_t L, int64_t *d_best, double *d_best_sum,
                       int32_t *d_ninf, void *d_work, size_t work_bytes, tma_stream_t stream);

@@ -26,6 +26,7 @@ TMA_MAX_AIRCRAFT = 32
 TMA_MAX_PARTICLES = 1 << 22
 TMA_MAX_GRAD_HORIZON = 320
 TMA_MOVE_PAPER, TMA_MOVE_RWMH, TMA_MOVE_MALA = 0, 1, 2
+TMA_DEVERR_DEGENERATE, TMA_DEVERR_INFEASIBLE, TMA_DEVERR_BOUNDS = 1, 2, 4
 
 EXPORTS = [
     "tma_status_str", "tma_last_error_string", "tma_launch_count", "tma_create", "tma_destroy",
@@ -39,7 +40,7 @@ EXPORTS = [
     "tma_set_wind_stream", "tma_rollout_grad", "tma_set_move", "tma_mh_propose", "tma_mh_accept",
     "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
     "tma_resample_to", "tma_move_to", "tma_set_finished", "tma_get_status", "tma_set_tuning",
-    "tma_lse_resample_workspace", "tma_lse_resample",
+    "tma_lse_resample_workspace", "tma_lse_resample", "tma_batch_rollout_cost",
 ]
 
 
@@ -155,6 +156,7 @@ def lib():
                 "tma_batch_results": ([vp, vp, P(d), P(i64), P(TmaState), P(u32), st], C.c_int),
                 "tma_batch_latency": ([vp, P(d), st], C.c_int),
                 "tma_batch_live_steps": ([vp, P(u64), st], C.c_int),
+                "tma_batch_rollout_cost": ([vp, vp, i32, vp, vp, st], C.c_int),
                 "tma_resample_noalloc": ([vp, i32, i64, u64, u32, u32, u32, vp, st], C.c_int),
                 "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
                 "tma_set_wind_stream": ([vp, u32], C.c_int),
@@ -483,8 +485,12 @@ def tma_mpc_run(h, n_steps, N, stream=None):
 
 
 def tma_get_error(h, stream=None):
+    """The solver's sticky device error word (TMA_DEVERR_* bits), cleared by
+    the call; the word is returned also when its bounds bit makes the call
+    return TMA_ERR_BOUNDS."""
     v = C.c_uint32()
-    _check(lib().tma_get_error(h, C.byref(v), _stream(stream)), "tma_get_error")
+    _check(lib().tma_get_error(h, C.byref(v), _stream(stream)), "tma_get_error",
+           allow=(TMA_OK, TMA_ERR_BOUNDS))
     return v.value
 
 
@@ -542,6 +548,14 @@ def tma_batch_solve(h, stream=None):
 
 def tma_batch_mpc(h, n_steps, use_graph=True, stream=None):
     _check(lib().tma_batch_mpc(h, int(n_steps), int(bool(use_graph)), _stream(stream)), "tma_batch_mpc")
+
+
+def tma_batch_rollout_cost(h, u, J, cost_ms, cost_ms_soft=None, stream=None):
+    """The batched rollout alone on packed controls u (scenario after
+    scenario, [L][N_s][S][3] each) -> packed per-sample costs ([M][N_s][L] each)."""
+    _check(lib().tma_batch_rollout_cost(h, _dptr(u), int(J), _dptr(cost_ms),
+                                        _dptr(cost_ms_soft) if cost_ms_soft is not None else None,
+                                        _stream(stream)), "tma_batch_rollout_cost")
 
 
 def tma_batch_results(h, Ns, S, stream=None):

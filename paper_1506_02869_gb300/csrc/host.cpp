@@ -902,7 +902,7 @@ tma_status tma_move_to(tma_solver *s, const float *d_u, int64_t L_in, const int3
     float lo[3], hi[3], sg[3];
     ctrl_f(s->prob, lo, hi, sg);
     TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, sg, d_u, d_anc, L, L_in, J, d_u_out,
-                         (cudaStream_t)stream));
+                         (cudaStream_t)stream, s->d_err));
     return TMA_OK;
 }
 
@@ -1276,7 +1276,7 @@ static tma_status solve_device(tma_solver *s, cudaStream_t st, bool *degenerate)
                 // the accepted moves start from the resampled particles themselves
                 const float zero[3] = {0.0f, 0.0f, 0.0f};
                 TMA_CUDA(launch_move(s->P, s->d_dyn, lo, hi, s->move_kind == TMA_MOVE_PAPER ? sg : zero,
-                                     s->d_u[cur], s->d_anc, Ln, Lj, J, s->d_u[cur ^ 1], st));
+                                     s->d_u[cur], s->d_anc, Ln, Lj, J, s->d_u[cur ^ 1], st, s->d_err));
             }
             cur ^= 1;
             if (s->move_kind != TMA_MOVE_PAPER) {
@@ -1541,7 +1541,7 @@ tma_status tma_get_error(tma_solver *s, uint32_t *h_err, tma_stream_t stream)
     TMA_CUDA(cudaMemcpyAsync(h_err, s->d_err, 4, cudaMemcpyDeviceToHost, st));
     TMA_CUDA(cudaMemsetAsync(s->d_err, 0, 4, st));
     TMA_CUDA(cudaStreamSynchronize(st));
-    return TMA_OK;
+    return (*h_err & TMA_DEVERR_BOUNDS) ? TMA_ERR_BOUNDS : TMA_OK;
 }
 
 tma_status tma_get_state(tma_solver *s, tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream)
@@ -1596,7 +1596,7 @@ static void batch_free(tma_batch *b)
                     b->d_Btmp, b->d_W, b->d_u[0], b->d_u[1], b->d_cost_ms, b->d_cost_ms_soft,
                     b->d_cbar, b->d_cbar_soft, b->d_wtilde, b->d_anc, b->d_work, b->d_best,
                     b->d_best_sum, b->d_ninf, b->d_best_u, b->d_t_start, b->d_t_end, b->d_live,
-                    b->d_queue, b->d_flags};
+                    b->d_queue, b->d_flags, b->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (float *p : b->d_pops)
@@ -1614,18 +1614,28 @@ static bool same_shape(const tma_problem &a, const tma_problem &b)
     return ok;
 }
 
-static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
+// Every scenario's wind field for its current MPC step (wind mode 1, the same
+// for the whole batch, draws each particle's field in the rollout instead).
+static tma_status batch_wind(tma_batch *b, cudaStream_t st)
 {
-    const long long L = b->L;
     const size_t P = (size_t)b->probs[0].grid[0] * b->probs[0].grid[1] * b->probs[0].grid[2];
-    TMA_CUDA(launch_stamp_start(b->d_t_start, st));
-    // wind mode 1 (the same for the whole batch) draws each particle's field in the rollout
     for (size_t g = 0; g < b->wind_groups.size() && b->probs[0].wind_mode == 0; ++g) {
         const WindC &w = b->wind_groups[g];
         const int s0 = b->group_start[g];
         TMA_CUDA(launch_batch_wind_normals(w, s0, b->M, b->d_scen, b->d_dyns, b->d_Btmp, st));
         TMA_CUDA(launch_wind_gemm(w, b->d_Lxy, b->lda, b->d_Btmp,
                                   b->d_W + (size_t)s0 * b->M * b->H * P * 4, st));
+    }
+    return TMA_OK;
+}
+
+static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
+{
+    const long long L = b->L;
+    TMA_CUDA(launch_stamp_start(b->d_t_start, st));
+    {
+        tma_status r = batch_wind(b, st);
+        if (r != TMA_OK) return r;
     }
     TMA_CUDA(launch_batch_init(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, L, b->S, b->d_u[0], st));
     TMA_CUDA(cudaMemsetAsync(b->d_flags, 0, 4, st));
@@ -1651,7 +1661,7 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
             TMA_CUDA(launch_resample(b->d_wtilde, (int)b->nseg, L, L, 0u, 0u, (uint32_t)J, nullptr, 0u,
                                      b->d_anc, rwork, b->d_flags, st, b->d_segkeys, b->d_dyns, true));
             TMA_CUDA(launch_batch_move(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, L, b->S,
-                                       b->d_u[cur], b->d_anc, J, b->d_u[cur ^ 1], st));
+                                       b->d_u[cur], b->d_anc, J, b->d_u[cur ^ 1], st, b->d_err));
             cur ^= 1;
         }
     }
@@ -1832,6 +1842,8 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
         if ((e = alloc(&b->d_live, 8))) return fail(e);
         if ((e = alloc(&b->d_queue, 8 * (size_t)n_scen))) return fail(e);
         if ((e = alloc(&b->d_flags, 4))) return fail(e);
+        if ((e = alloc(&b->d_err, 4))) return fail(e);
+        if ((e = cudaMemset(b->d_err, 0, 4))) return fail(e);
         if ((e = cudaMemcpy(b->d_probs, pc.data(), sizeof(ProblemC) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
         if ((e = cudaMemcpy(b->d_scen, b->scen.data(), sizeof(BatchScen) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
         if ((e = cudaMemcpy(b->d_seg_scen, b->seg_scen.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice))) return fail(e);
@@ -1930,6 +1942,21 @@ tma_status tma_batch_mpc(tma_batch *b, int32_t n_steps, int32_t use_graph, tma_s
     return TMA_OK;
 }
 
+tma_status tma_batch_rollout_cost(tma_batch *b, const float *d_u, int32_t J, float *d_cost_ms,
+                                  float *d_cost_ms_soft, tma_stream_t stream)
+{
+    if (!b || !d_u || !d_cost_ms || J < 0 || J > 0xFFFF) return TMA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    tma_status r = batch_wind(b, st);
+    if (r != TMA_OK) return r;
+    const bool soft = b->sep_mode != 0 && d_cost_ms_soft != nullptr;
+    TMA_CUDA(cudaMemsetAsync(b->d_live, 0, 8, st));
+    TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, d_u, b->d_W, b->L, J,
+                                  samples_of(b->probs[0], J), d_cost_ms, soft ? d_cost_ms_soft : nullptr,
+                                  b->d_live, b->d_queue, b->grid, b->probs[0].wind_mode, st));
+    return TMA_OK;
+}
+
 tma_status tma_batch_results(tma_batch *b, float *h_best_u, double *h_best_cost, int64_t *h_best,
                              tma_state *h_x, uint32_t *h_mpc, tma_stream_t stream)
 {
@@ -1944,6 +1971,9 @@ tma_status tma_batch_results(tma_batch *b, float *h_best_u, double *h_best_cost,
         TMA_CUDA(cudaMemcpyAsync(h_best, b->d_best, 8 * (size_t)b->n_scen, cudaMemcpyDeviceToHost, st));
     TMA_CUDA(cudaMemcpyAsync(b->dyn_h.data(), b->d_dyns, sizeof(DynState) * b->n_scen,
                              cudaMemcpyDeviceToHost, st));
+    unsigned int err = 0;
+    TMA_CUDA(cudaMemcpyAsync(&err, b->d_err, 4, cudaMemcpyDeviceToHost, st));
+    TMA_CUDA(cudaMemsetAsync(b->d_err, 0, 4, st));
     TMA_CUDA(cudaStreamSynchronize(st));
     long long k = 0;
     for (int s = 0; s < b->n_scen; ++s) {
@@ -1954,7 +1984,7 @@ tma_status tma_batch_results(tma_batch *b, float *h_best_u, double *h_best_cost,
             h_x[k] = tma_state{d[0], d[1], d[2], d[3], d[4], d[5]};
         }
     }
-    return TMA_OK;
+    return (err & TMA_DEVERR_BOUNDS) ? TMA_ERR_BOUNDS : TMA_OK;
 }
 
 tma_status tma_batch_latency(tma_batch *b, double *h_ms, tma_stream_t stream)

@@ -28,7 +28,8 @@ template <bool kVec, int kNC = 0>
 __global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState *__restrict__ dyn,
                                                    const float *__restrict__ u,
                                                    const int32_t *__restrict__ anc, long long L,
-                                                   long long Lin, int J, float *__restrict__ u_out)
+                                                   long long Lin, int J, float *__restrict__ u_out,
+                                                   unsigned int *__restrict__ err)
 {
     // L children from Lin parents
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,8 +37,12 @@ __global__ void __launch_bounds__(256) move_kernel(const MoveC C, const DynState
     const long long l = t / C.N;
     const int i = (int)(t - l * C.N);
     int a = __ldg(anc + (size_t)i * L + l);
-    if ((unsigned long long)a >= (unsigned long long)Lin)   // out-of-range ancestor: own index (clamped)
+    if ((unsigned long long)a >= (unsigned long long)Lin) {
+        // out-of-range ancestor: reported in the sticky error word, and the
+        // child still gets a defined parent (its own index, clamped)
+        if (err) atomicOr(err, TMA_DEVERR_BOUNDS);
         a = (int)(l < Lin ? l : Lin - 1);
+    }
     const uint32_t mpc = dyn ? dyn->mpc_step : 0u;
     const int nc = kNC > 0 ? kNC : C.nc;
     const float *src = u + ((size_t)a * C.N + i) * nc;
@@ -115,15 +120,16 @@ MoveC make_move(const ProblemC &P, const float lo[3], const float hi[3], const f
 
 cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                         const float ctrl_hi[3], const float sigma[3], const float *u,
-                        const int32_t *anc, int64_t L, int64_t Lin, int J, float *u_out, cudaStream_t st)
+                        const int32_t *anc, int64_t L, int64_t Lin, int J, float *u_out, cudaStream_t st,
+                        unsigned int *err)
 {
     if (L <= 0 || Lin <= 0) return cudaSuccess;
     const MoveC C = make_move(P, ctrl_lo, ctrl_hi, sigma);
     const long long n = (long long)L * P.N;
     const unsigned grid = (unsigned)((n + 255) / 256);
-    if (C.nc == 12) move_kernel<true, 12><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
-    else if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
-    else move_kernel<false><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out);
+    if (C.nc == 12) move_kernel<true, 12><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out, err);
+    else if (C.nc % 4 == 0) move_kernel<true><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out, err);
+    else move_kernel<false><<<grid, 256, 0, st>>>(C, dyn, u, anc, L, Lin, J, u_out, err);
     count_launch();
     return cudaGetLastError();
 }

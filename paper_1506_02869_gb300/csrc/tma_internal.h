@@ -146,7 +146,7 @@ unsigned long long *resample_partials(void *work);
 cudaError_t launch_move(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                         const float ctrl_hi[3], const float sigma[3], const float *u,
                         const int32_t *anc, int64_t L, int64_t Lin, int J, float *u_out,
-                        cudaStream_t st);
+                        cudaStream_t st, unsigned int *err = nullptr);
 cudaError_t launch_init_controls(const ProblemC &P, const DynState *dyn, const float ctrl_lo[3],
                                  const float ctrl_hi[3], float *u, int64_t L, cudaStream_t st);
 
@@ -194,7 +194,8 @@ cudaError_t launch_batch_sample_mean(const float *cost_ms, const BatchScen *scen
                                      int Mj, float *cbar, cudaStream_t st);
 cudaError_t launch_batch_move(const BatchScen *scen, const int *seg_scen, const DynState *dyns,
                               long long nseg, long long L, int S, const float *u,
-                              const int32_t *anc, int J, float *u_out, cudaStream_t st);
+                              const int32_t *anc, int J, float *u_out, cudaStream_t st,
+                              unsigned int *err = nullptr);
 cudaError_t launch_batch_init(const BatchScen *scen, const int *seg_scen, const DynState *dyns,
                               long long nseg, long long L, int S, float *u, cudaStream_t st);
 cudaError_t launch_batch_wind_normals(const WindC &w, int s0, int M_scen, const BatchScen *scen,
@@ -325,6 +326,7 @@ struct tma_batch {
     float *d_best_u = nullptr;
     unsigned long long *d_t_start = nullptr, *d_t_end = nullptr, *d_live = nullptr, *d_queue = nullptr;
     unsigned int *d_flags = nullptr;
+    unsigned int *d_err = nullptr;      // sticky error word (TMA_DEVERR_BOUNDS), read by tma_batch_results
     std::vector<float *> d_pops;
     int final_u = 0;
     // captured MPC loop

@@ -1,5 +1,6 @@
 """GPU parity: every stage of the CUDA path, called through the C-ABI, against
 the FP64 oracle on the same seeded inputs."""
+import ctypes
 import math
 
 import numpy as np
@@ -332,6 +333,36 @@ def test_move_matches_oracle(torch, pkg, cfg, L, nseg):
     d = np.abs(out - ref)
     tol = 2e-6 * sig + 2.5e-7 * np.abs(ref)
     assert (d[~near] <= np.broadcast_to(tol, d.shape)[~near]).all(), d.max()
+
+
+def test_move_reports_an_out_of_range_ancestor(torch, pkg):
+    """Ancestor arrays built on the host with entries at L_in and -1: the
+    kernel's own check catches them (nothing faults), the sticky error word
+    gets TMA_DEVERR_BOUNDS, tma_get_error returns TMA_ERR_BOUNDS with the word,
+    and every child is the one of the repaired ancestor min(l, L_in - 1)."""
+    p = S.shrink(S.config2(), L=4096)
+    L_in, L = 3000, 4096
+    rng = _rng(91)
+    u = torch.from_numpy(S.random_controls(p, L, rng)).cuda()
+    anc = rng.integers(0, L_in, size=(p.N, L)).astype(np.int32)
+    bad = anc.copy()
+    bad[3, 17], bad[5, 4000], bad[0, 2999] = L_in, -1, 0x7FFFFFFF
+    fixed = bad.copy()
+    for i, l in ((3, 17), (5, 4000), (0, 2999)):
+        fixed[i, l] = min(l, L_in - 1)
+    solver = pkg.Solver(p)
+    assert pkg.tma_get_error(solver.h) == 0
+    out_ok = torch.empty_like(u)
+    pkg.tma_move_to(solver.h, u[:L_in], torch.from_numpy(fixed).cuda(), 3, out_ok)
+    assert pkg.tma_get_error(solver.h) == 0               # in-range ancestors set nothing
+    out_bad = torch.empty_like(u)
+    pkg.tma_move_to(solver.h, u[:L_in], torch.from_numpy(bad).cuda(), 3, out_bad)
+    word = ctypes.c_uint32()
+    st = pkg.lib().tma_get_error(solver.h, ctypes.byref(word), pkg._stream())
+    assert st == pkg.TMA_ERR_BOUNDS and word.value == pkg.TMA_DEVERR_BOUNDS
+    assert pkg.tma_get_error(solver.h) == 0               # cleared by the read
+    assert torch.equal(out_ok, out_bad)
+    solver.close()
 
 
 def test_init_controls_match_oracle(torch, pkg):
