@@ -26,6 +26,8 @@
 //             ancestors are drawn from the Lin weighted particles of the
 //             segment (Lout = Lin for a fixed particle count).
 #include <cfloat>
+#include <cuda.h>
+
 #include <mutex>
 
 #include "device_common.cuh"
@@ -529,16 +531,53 @@ cudaError_t launch_lse(const float *cbar, int nseg, int64_t L, double kappa, dou
 // caller-provided workspace.  Every GPU that loads this library keeps the
 // array (about 512 KB) until the process exits.  Host code must not use the
 // array's name as a device address: its device address is fetched once per
-// device with cudaGetSymbolAddress and passed to the kernels.
+// device with cudaGetSymbolAddress and passed to the kernels.  The address
+// belongs to the device's context: after cudaDeviceReset the next call finds a
+// new context (its driver ID differs) and fetches the address again.
 
 namespace {
 constexpr long long kNoAllocMaxPartials = 65536;   // nseg * ceil(L / 2048) at most
 static __device__ __align__(256) unsigned long long g_resample_scratch[kNoAllocMaxPartials + 2];
 std::mutex g_scratch_mu;
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchSetUp {
+    void *addr = nullptr;
+    unsigned long long ctx_id = 0;   // driver ID of the context the address belongs to
+};
+ScratchSetUp g_scratch[kMaxDevices];
 
-// Device address of the array on the current device (set up on first use).
+// Driver ID of the current context (0 if the driver cannot tell), through the
+// driver's entry points (this library links only the runtime).
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f);
+            get_id = reinterpret_cast<GetId>(g);
+        }
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+// Device address of the array on the current device: set up on the first call
+// with this device current, and again when the device's context has changed
+// (or had not been created yet at the previous set-up: its ID then read 0).
 cudaError_t scratch_address(void **out)
 {
     int dev = 0;
@@ -546,13 +585,16 @@ cudaError_t scratch_address(void **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    ScratchSetUp &su = g_scratch[dev];
+    if (!su.addr || su.ctx_id != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_resample_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        su.addr = p;
+        su.ctx_id = ctx;
     }
-    *out = g_scratch_addr[dev];
+    *out = su.addr;
     return cudaSuccess;
 }
 }  // namespace
