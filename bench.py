@@ -1,13 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the SMC-MPC hot path on GB300.
 
-One step = one SMC solve (Algorithm 1) of the 8-aircraft TMA workload
-(L = 65536 particles, M = 32 wind samples, H = 60 steps, 64x64x8 wind grid,
-30 annealing iterations): wind-field generation, 30 rollouts with costs,
-29 x (FP64 LSE, systematic resampling, move), final selection.
+One step = one SMC solve (Algorithm 1) of the high-density TMA workload
+(24 aircraft, L = 262144 particles, M = 64 wind samples, H = 120 steps,
+64x64x8 wind grid, 30 annealing iterations, fuel + ground-noise cost, hard and
+softplus separation both evaluated): wind-field generation, 30 rollouts with
+costs, 29 x (FP64 LSE, systematic resampling, move), final selection.
+`--workload c2` times the 8-aircraft workload instead (L = 65536, M = 32,
+H = 60, fuel cost, hard separation).
 Metric: aircraft-step-samples per second = L*M*N*H*J_max per solve / time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c3|c2]
 
 Under torchrun (N > 1) every rank solves an independent replica (its own
 seed): scaling is weak, no collective touches the data path; the time is the
@@ -33,23 +37,48 @@ if ROOT not in sys.path:
 
 METRIC = "aircraft-step-samples/sec"
 UNIT = "aircraft-step-samples/s"
-WORKLOAD = "tma-8ac-L65536-M32-H60-grid64x64x8-J30"
+# The timed workloads: the scenario generator, the name the line reports, and
+# the oracle's sample sizes (particles) for the CPU baseline, the reference arm
+# and the rollout-only rates (single-threaded, all cores).
+WORKLOADS = {
+    "c3": dict(config=3, name="tma-24ac-L262144-M64-H120-grid64x64x8-J30-noise-hardsoft",
+               cpu_particles=64, reference_particles=32, rollout_one=32, rollout_all=512),
+    "c2": dict(config=2, name="tma-8ac-L65536-M32-H60-grid64x64x8-J30",
+               cpu_particles=512, reference_particles=256, rollout_one=256, rollout_all=4096),
+}
 
 # Peaks: measured copy bandwidth from MEASURED_PEAKS.json when present; the FP32
-# CUDA-core peak is derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock.
-SMS, FP32_LANES = 152, 128
+# CUDA-core peak is derived: SMs x 128 FP32 lanes x 2 flop/FMA x SM clock, with
+# the SM count from the device and the clock sampled during the timed region.
+FP32_LANES = 128
 
 
-def fp32_peak_tflops(sm_mhz):
-    return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sms, sm_mhz):
+    return sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
-def flops_per_unit(p):
-    """Algorithmic FP32 operations of one aircraft-step-sample (one aircraft
-    advanced one step under one wind sample in one particle), counted from the
-    per-step formulas: +, -, *, /, sqrt, min/max/compare and each elementary
-    function count 1, an FMA 2.  Pairwise separation is counted once per
-    unordered pair ((N-1)/2 pairs per unit)."""
+def flops_per_unit(p, particles=8, samples=2):
+    """Algorithmic floating-point operations per live aircraft-step-sample (one
+    aircraft advanced one step under one wind sample in one particle), counted
+    mechanically on the FP64 oracle's rollout (the operation-counting build of
+    oracle/opcount.cpp: +, -, *, /, comparisons, min/max/abs and each
+    elementary function 1; an FMA is two of them) of `particles` uniform
+    initial particles under the first `samples` wind samples of the workload,
+    costs included (the soft form too when the solve computes it); pairs are
+    checked once per unordered pair, as in the oracle."""
+    import oracle as O
+    q = p.copy(L=particles, M=samples)
+    W = O.wind_field(q)
+    u = O.init_controls(q, particles)
+    ops, live = O.rollout_opcount(q, u, 0, W, soft=(q.sep_mode != 0))
+    return ops / live
+
+
+def flops_per_unit_tally(p):
+    """The same work tallied by hand from the per-step formulas (for
+    comparison): +, -, *, /, sqrt, min/max/compare and each elementary function
+    count 1, an FMA 2.  Pairwise separation is counted once per unordered pair
+    ((N-1)/2 pairs per unit)."""
     import numpy as np
     base = 31 + 1        # control-derived quantities, limits, mass
     wind = 21 + 28       # cell search in 3 axes, 7 lerps x 2 components
@@ -64,12 +93,11 @@ def flops_per_unit(p):
         pair * (p.N - 1) / 2.0
 
 
-# DRAM bytes (read + write) of one full-size rollout launch of the 8-aircraft
-# workload per rollout kernel, from a one-pass ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, iteration 20 of a solve);
-# valid only for the kernel sources they were taken on.
-ROLLOUT_TRAFFIC = {"sources_sha256_16": "6aaf6fb629fdd898",
-                   "bytes_per_launch": {"rollout_kernel": 1000901376 + 68202496}}
+# DRAM bytes (read + write) of one full-size rollout launch per workload and
+# rollout kernel, from a one-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch late in a solve); valid only for the
+# kernel sources they were taken on.
+ROLLOUT_TRAFFIC = {"sources_sha256_16": None, "bytes_per_launch": {}}
 
 
 def rollout_kernel_name(variant):
@@ -168,10 +196,15 @@ def max_over_ranks(value, world, device=None):
     return float(t.item())
 
 
-def replica_problem(rank, base_seed=None):
-    """Rank r solves an independent replica of the workload with its own seed."""
+def workload_problem(workload, seed=None):
     import scenarios as S
-    p = S.config2() if base_seed is None else S.config2(seed=base_seed)
+    cfg = WORKLOADS[workload]["config"]
+    return S.make_config(cfg) if seed is None else S.make_config(cfg, seed=seed)
+
+
+def replica_problem(rank, workload="c3", base_seed=None):
+    """Rank r solves an independent replica of the workload with its own seed."""
+    p = workload_problem(workload, base_seed)
     return p.copy(seed=p.seed + 1000003 * rank)
 
 
@@ -184,19 +217,18 @@ def units_per_solve(p):
 _ORACLE_WIND = {}
 
 
-def oracle_wind():
+def oracle_wind(workload):
     """The workload's wind field from the oracle (FP64), generated once per
     process; returns (field, generation seconds)."""
     import oracle as O
-    import scenarios as S
-    if not _ORACLE_WIND:
+    if workload not in _ORACLE_WIND:
         t0 = time.perf_counter()
-        W = O.wind_field(S.config2())
-        _ORACLE_WIND.update(W=W, seconds=time.perf_counter() - t0)
-    return _ORACLE_WIND["W"], _ORACLE_WIND["seconds"]
+        W = O.wind_field(workload_problem(workload))
+        _ORACLE_WIND[workload] = dict(W=W, seconds=time.perf_counter() - t0)
+    return _ORACLE_WIND[workload]["W"], _ORACLE_WIND[workload]["seconds"]
 
 
-def oracle_sample(L_sample, nthreads):
+def oracle_sample(workload, L_sample, nthreads):
     """The FP64 oracle's full solve on the workload's traffic with L_sample
     particles (all other sizes full) on the workload's wind field, whose
     generation time is charged at the share L_sample / L of the full
@@ -204,9 +236,8 @@ def oracle_sample(L_sample, nthreads):
     that generated it again would carry all of it); returns (units/s,
     seconds, units)."""
     import oracle as O
-    import scenarios as S
-    W, t_wind = oracle_wind()
-    full = S.config2()
+    W, t_wind = oracle_wind(workload)
+    full = workload_problem(workload)
     p = full.copy(L=L_sample)
     t0 = time.perf_counter()
     O.smc_solve(p, W=W, nthreads=nthreads)
@@ -215,15 +246,14 @@ def oracle_sample(L_sample, nthreads):
     return u / dt, dt, u
 
 
-def oracle_rollout_rates(L_one, L_all, cores):
+def oracle_rollout_rates(workload, L_one, L_all, cores):
     """The oracle's rollout alone (one iteration's inner loop on the uniform
     initial controls, the workload's wind field computed beforehand), single-
     threaded on L_one particles and on all cores on L_all; returns
     {threads: (units/s, seconds, units, particles)} with units = L M N H."""
     import oracle as O
-    import scenarios as S
-    p = S.config2()
-    W, _ = oracle_wind()
+    p = workload_problem(workload)
+    W, _ = oracle_wind(workload)
     out = {}
     for L, n in ((L_one, 1), (L_all, cores)) if cores > 1 else ((L_one, 1),):
         q = p.copy(L=L)
@@ -254,25 +284,28 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     cores = os.cpu_count() or 1
-    Ls = args.reference_particles
+    wl = WORKLOADS[args.workload]
+    Ls = args.reference_particles or wl["reference_particles"]
     for _ in range(args.warmup):
-        oracle_sample(Ls, cores)
+        oracle_sample(args.workload, Ls, cores)
     times, units = [], 0
     for _ in range(args.steps):
-        _, dt, units = oracle_sample(Ls, cores)
+        _, dt, units = oracle_sample(args.workload, Ls, cores)
         times.append(dt)
     tot = sum(times)
     value = units * args.steps / tot
-    _, t_wind = oracle_wind()
+    _, t_wind = oracle_wind(args.workload)
+    full = workload_problem(args.workload)
     sample = (f"oracle smc_solve of the workload's traffic with L={Ls} particles "
-              f"(M=32, N=8, H=60, J_max=30) on the 64x64x8 wind field, whose generation "
-              f"({t_wind:.1f} s, once) is charged at the share {Ls}/65536 per step; {cores} threads")
+              f"(M={full.M}, N={full.N}, H={full.H}, J_max={full.J_max}) on the "
+              f"{'x'.join(str(g) for g in full.grid)} wind field, whose generation "
+              f"({t_wind:.1f} s, once) is charged at the share {Ls}/{full.L} per step; {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_particles": Ls, "l2": "n/a (CPU)"},
+        "config": {"workload": wl["name"], "sample_particles": Ls, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -298,7 +331,8 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=device)
     pkg.build()
     lib = pkg.lib()
-    p = replica_problem(rank)
+    wl = WORKLOADS[args.workload]
+    p = replica_problem(rank, args.workload)
     solver = pkg.Solver(p, device=device)
     h = solver.h
     stream = torch.cuda.current_stream(device)
@@ -346,7 +380,9 @@ def run_ours(args, world, rank, local):
     units = units_per_solve(p)
     value = units * args.steps * world / (elapsed_max * 1e-3)
 
-    # ---- end to end: host state in, host controls out, through the C-ABI
+    # ---- end to end: host state in, host controls out, through the C-ABI (the
+    # same solve, at most --e2e-steps of them when the device-timed loop is longer)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     x0 = torch.tensor([[float(a[k]) for k in ("x", "y", "z", "v", "chi", "m")] for a in p.aircraft],
                       dtype=torch.float64).pin_memory()
     out_h = torch.empty((p.N, p.S, 3), dtype=torch.float32).pin_memory()
@@ -355,7 +391,7 @@ def run_ours(args, world, rank, local):
     barrier()
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(e2e_steps):
         st = lib.tma_solve_host(h, C.cast(C.c_void_p(x0.data_ptr()), C.POINTER(pkg.TmaState)),
                                 p.mpc_step, C.c_void_p(out_h.data_ptr()), C.byref(cost),
                                 pkg._stream(stream))
@@ -366,29 +402,41 @@ def run_ours(args, world, rank, local):
     e2e_max = max_over_ranks(e2e_s, world, device)
     if statuses - {pkg.TMA_OK, pkg.TMA_WARN_DEGENERATE}:
         raise RuntimeError(f"tma_solve_host failed: {statuses}")
-    e2e_value = units * args.steps * world / e2e_max
+    e2e_value = units * e2e_steps * world / e2e_max
 
     # ---- roofline of the rollout kernel (the dominant kernel)
     roll_ms, roll_n = prof["rollout"]
     fpu = flops_per_unit(p)
     live_per_launch = live_per_solve / p.J_max
     achieved = fpu * live_per_launch / (roll_ms / roll_n * 1e-3) / 1e12 if roll_n else None
-    sm_clock = 2070.0
-    peak = fp32_peak_tflops(sm_clock)
+    # FP32 peak at the SM clock sampled during the timed region (else the
+    # measured maximum clock), on the device's SM count
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    pk = measured_peaks()
+    if clocks and clocks.get("sm_mhz"):
+        sm_clock, clock_src = float(clocks["sm_mhz"]), "median SM clock sampled during the timed region"
+    elif pk and pk.get("sm_max_mhz"):
+        sm_clock, clock_src = float(pk["sm_max_mhz"]), "maximum SM clock of MEASURED_PEAKS.json"
+    else:
+        sm_clock, clock_src = 2070.0, "nominal maximum SM clock"
+    peak = fp32_peak_tflops(sms, sm_clock)
     total_ms = sum(v[0] for v in prof.values())
     variant, timed = pkg.tma_get_tuning(h)
     kname = rollout_kernel_name(variant)
     roofline = {
         "bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-        "traffic": (ROLLOUT_TRAFFIC["bytes_per_launch"].get(kname)
+        "traffic": (ROLLOUT_TRAFFIC["bytes_per_launch"].get(f"{args.workload}:{kname}")
                     if rollout_sources_digest() == ROLLOUT_TRAFFIC["sources_sha256_16"] else None),
-        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-        "flops_per_unit": fpu, "live_units_per_launch": live_per_launch,
+        "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_clock:.0f} MHz "
+                       f"({clock_src})",
+        "flops_per_unit": fpu,
+        "flops_per_unit_source": "counted on the FP64 oracle's rollout (oracle/opcount.cpp), 8 uniform "
+                                 "initial particles x 2 wind samples",
+        "flops_per_unit_hand_tally": flops_per_unit_tally(p), "live_units_per_launch": live_per_launch,
         "units_per_launch": p.L * p.M * p.N * p.H, "launch_ms": roll_ms / roll_n if roll_n else None,
         "stage_ms_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items() if total_ms},
     }
-    pk = measured_peaks()
     if pk:
         roofline["hbm_peak_gbs_measured"] = pk.get("hbm_gbs")
     roofline["launch_variant"] = {"chosen": variant,
@@ -398,9 +446,11 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": p.L, "M": p.M, "N": p.N, "H": p.H, "J_max": p.J_max,
-                   "grid": list(p.grid), "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (packed wind field 1.0 GB per solve)"},
+        "config": {"workload": wl["name"], "L": p.L, "M": p.M, "N": p.N, "H": p.H, "J_max": p.J_max,
+                   "grid": list(p.grid), "noise_weight": p.w_noise, "sep_mode": p.sep_mode,
+                   "parallelism": f"replicas{world}", "e2e_steps": e2e_steps,
+                   "l2": f"inputs larger than L2 (packed wind field "
+                         f"{p.M * p.H * p.n_grid * 16 / 1e9:.1f} GB per solve)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x0.numel() * 8),
                 "d2h_bytes_per_step": int(out_h.numel() * 4 + 8 + 4)},
         "gpu_launches": int(launches),
@@ -409,15 +459,16 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        v, dt, u = oracle_sample(args.cpu_particles, cores)
+        Lc = args.cpu_particles or wl["cpu_particles"]
+        v, dt, u = oracle_sample(args.workload, Lc, cores)
         line["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"one oracle smc_solve of the workload's traffic with L={args.cpu_particles} "
+            "sample": (f"one oracle smc_solve of the workload's traffic with L={Lc} "
                        f"particles (full M, N, H, J_max) on the wind field, whose generation "
-                       f"({oracle_wind()[1]:.1f} s) is charged at the share {args.cpu_particles}/{p.L}: "
+                       f"({oracle_wind(args.workload)[1]:.1f} s) is charged at the share {Lc}/{p.L}: "
                        f"{u:.3g} units in {dt:.1f} s"),
             "cpu_model": cpu_model()}
-        rr = oracle_rollout_rates(256, 4096, cores)
+        rr = oracle_rollout_rates(args.workload, wl["rollout_one"], wl["rollout_all"], cores)
         line["cpu_baseline"]["rollout_only"] = {
             f"threads_{n}": {"value": v_, "unit": UNIT,
                              "sample": f"one oracle rollout (J = 0, initial controls, wind precomputed) of "
@@ -953,8 +1004,15 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-particles", type=int, default=512)
-    ap.add_argument("--reference-particles", type=int, default=256)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3",
+                    help="the timed workload: c3 the 24-aircraft high-density TMA (default), "
+                         "c2 the 8-aircraft one")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="solves of the end-to-end (host buffers) measurement, at most --steps")
+    ap.add_argument("--cpu-particles", type=int, default=0,
+                    help="particles of the oracle's CPU-baseline sample (0: the workload's)")
+    ap.add_argument("--reference-particles", type=int, default=0,
+                    help="particles per step of the reference arm (0: the workload's)")
     ap.add_argument("--rollout-only", action="store_true",
                     help="time only the rollout on --particles particles (profiling case)")
     ap.add_argument("--particles", type=int, default=0,

@@ -24,8 +24,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIBPATH = os.path.join(_LIBDIR, "liboracle.so")
 _SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle.h")]
+_OPC_PATH = os.path.join(_LIBDIR, "liboracle_opcount.so")
+_OPC_SRC = _SRC + [os.path.join(_HERE, "opcount.cpp")]
 _lock = threading.Lock()
 _lib = None
+_opc = None
 
 
 def build(force: bool = False) -> str:
@@ -40,6 +43,22 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIBPATH)
     return _LIBPATH
+
+
+def build_opcount(force: bool = False) -> str:
+    """Compile the operation-counting build of the oracle (opcount.cpp: oracle.c
+    as C++ with a counting double, single-threaded) into
+    oracle/_lib/liboracle_opcount.so."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    stale = force or not os.path.exists(_OPC_PATH) or any(
+        os.path.getmtime(s) > os.path.getmtime(_OPC_PATH) for s in _OPC_SRC)
+    if stale:
+        tmp = _OPC_PATH + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+               "-Wno-unknown-pragmas", "-o", tmp, _OPC_SRC[2], "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OPC_PATH)
+    return _OPC_PATH
 
 
 class OrcProblem(C.Structure):
@@ -117,6 +136,42 @@ def lib():
             _lib.orc_select.argtypes = [P(d), i32, i32, P(d), P(i32)]
             _lib.orc_select.restype = i64
     return _lib
+
+
+def _opcount_lib():
+    global _opc
+    with _lock:
+        if _opc is None:
+            _opc = C.CDLL(build_opcount())
+            d, i32, i64, P = C.c_double, C.c_int, C.c_int64, C.POINTER
+            _opc.orc_rollout.argtypes = [P(OrcProblem), P(OrcAircraft), P(d), i32, i32, P(d),
+                                         P(i64), i32, i32, i32, P(d), P(d), P(d), P(d), P(i64)]
+            _opc.orc_opcount_read.argtypes = [C.c_int]
+            _opc.orc_opcount_read.restype = C.c_uint64
+    return _opc
+
+
+def rollout_opcount(p, u, J, W, pidx=None, soft=True):
+    """Floating-point operations of the oracle's rollout (every wind sample of
+    W, costs included; counting rule in opcount.cpp) of controls
+    u[Lsub][N][S][3], and the aircraft-steps it simulated: (ops, live)."""
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, p.N, p.S, 3)
+    Ls = u.shape[0]
+    pidx = np.arange(Ls, dtype=np.int64) if pidx is None else np.ascontiguousarray(pidx, np.int64)
+    W = np.ascontiguousarray(W, np.float64)
+    mc = W.shape[0]
+    ch = np.empty((Ls, mc, p.N))
+    cs = np.empty((Ls, mc, p.N)) if soft else None
+    mg = np.empty((Ls, mc, p.N))
+    sm = np.empty((Ls, mc))
+    live = C.c_int64(0)
+    m = _Marshalled(p)
+    L = _opcount_lib()
+    L.orc_opcount_read(1)
+    L.orc_rollout(m.ps, m.ac, _ptr(W, C.c_double), 0, mc, _ptr(u, C.c_double), _ptr(pidx, C.c_int64),
+                  Ls, J, 1, _ptr(ch, C.c_double), _ptr(cs, C.c_double) if soft else None,
+                  _ptr(mg, C.c_double), _ptr(sm, C.c_double), C.byref(live))
+    return int(L.orc_opcount_read(1)), int(live.value)
 
 
 def _ptr(a, ctype):

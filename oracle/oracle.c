@@ -277,13 +277,23 @@ static double angdist(double a)
 /* cases, where FP32 and FP64 may legitimately decide differently)      */
 /* ------------------------------------------------------------------ */
 
+/* The margins are bookkeeping of the parity protocol, not part of the method.
+ * orc_margin_t and ORC_MARGIN(expr) (the evaluation of a margin) are double and
+ * (expr) here; the operation-counting build of opcount.cpp redefines them so
+ * that this bookkeeping stays out of its count. */
+#ifndef ORC_MARGIN_T
+#define ORC_MARGIN_T double
+#define ORC_MARGIN(expr) (expr)
+#endif
+typedef ORC_MARGIN_T orc_margin_t;
+
 typedef struct {
     int n_false;
-    double min_true, max_false;
+    orc_margin_t min_true, max_false;
 } conj_t;
 
 static void conj_init(conj_t *c) { c->n_false = 0; c->min_true = INFINITY; c->max_false = 0.0; }
-static void conj_add(conj_t *c, int ok, double margin)
+static void conj_add(conj_t *c, int ok, orc_margin_t margin)
 {
     if (ok) {
         if (margin < c->min_true) c->min_true = margin;
@@ -294,7 +304,7 @@ static void conj_add(conj_t *c, int ok, double margin)
 }
 static int conj_ok(const conj_t *c) { return c->n_false == 0; }
 /* a true conjunction flips when any member flips; a false one only when every false member does */
-static double conj_margin(const conj_t *c) { return c->n_false == 0 ? c->min_true : c->max_false; }
+static orc_margin_t conj_margin(const conj_t *c) { return c->n_false == 0 ? c->min_true : c->max_false; }
 static double rel(double a, double b, double scale) { return fabs(a - b) / fabs(scale); }
 
 /* ------------------------------------------------------------------ */
@@ -305,7 +315,7 @@ typedef struct {
     double x, y, z, v, chi, m, F;
     int dead, landed, sepv;
     double sA, sB, sC, sN, soft;
-    double margin, smargin;
+    orc_margin_t margin, smargin;
 } acst;
 
 static double softplus(double g, double beta)
@@ -378,9 +388,9 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
             double sg = hd / s->v;
             conj_t cc;
             conj_init(&cc);
-            conj_add(&cc, fabs(sg) <= sgmax, rel(fabs(sg), sgmax, sgmax));
+            conj_add(&cc, fabs(sg) <= sgmax, ORC_MARGIN(rel(fabs(sg), sgmax, sgmax)));
             if (!(fabs(sg) < 1.0)) {
-                double cm = conj_margin(&cc);
+                orc_margin_t cm = conj_margin(&cc);
                 if (cm < s->margin) s->margin = cm;
                 if (cm < s->smargin) s->smargin = cm;
                 s->dead = 1;
@@ -388,7 +398,7 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
             }
             double cg = sqrt(1.0 - sg * sg);
             double tp = w * s->v / (G0 * cg);
-            conj_add(&cc, fabs(tp) < tpmax, rel(fabs(tp), tpmax, tpmax));
+            conj_add(&cc, fabs(tp) < tpmax, ORC_MARGIN(rel(fabs(tp), tpmax, tpmax)));
             double cphi = 1.0 / sqrt(1.0 + tp * tp);
             double sphi = tp * cphi;
             double base = 1.0 - 2.2558e-5 * s->z;
@@ -397,10 +407,10 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
             double CL = s->m * G0 * cg / (qS * cphi);
             double D = qS * (a->CD0 + a->CD2 * CL * CL);
             double T = s->m * (acc + G0 * sg) + D;
-            conj_add(&cc, T >= a->Tmin, rel(T, a->Tmin, a->Tmax));
-            conj_add(&cc, T <= a->Tmax, rel(T, a->Tmax, a->Tmax));
+            conj_add(&cc, T >= a->Tmin, ORC_MARGIN(rel(T, a->Tmin, a->Tmax)));
+            conj_add(&cc, T <= a->Tmax, ORC_MARGIN(rel(T, a->Tmax, a->Tmax)));
             {
-                double cm = conj_margin(&cc);
+                orc_margin_t cm = conj_margin(&cc);
                 if (cm < s->margin) s->margin = cm;
                 if (cm < s->smargin) s->smargin = cm;
             }
@@ -434,13 +444,13 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
             /* unary state constraints on the step-(k+1) state (Sec. 3.4) */
             conj_t cu;
             conj_init(&cu);
-            conj_add(&cu, z1 >= P->z_min, rel(z1, P->z_min, P->z_min));
-            conj_add(&cu, z1 <= P->z_max, rel(z1, P->z_max, P->z_max));
-            conj_add(&cu, v1 >= P->v_min, rel(v1, P->v_min, P->v_min));
-            conj_add(&cu, v1 <= P->v_max, rel(v1, P->v_max, P->v_max));
-            conj_add(&cu, m1 >= a->m_empty, rel(m1, a->m_empty, a->m_empty));
+            conj_add(&cu, z1 >= P->z_min, ORC_MARGIN(rel(z1, P->z_min, P->z_min)));
+            conj_add(&cu, z1 <= P->z_max, ORC_MARGIN(rel(z1, P->z_max, P->z_max)));
+            conj_add(&cu, v1 >= P->v_min, ORC_MARGIN(rel(v1, P->v_min, P->v_min)));
+            conj_add(&cu, v1 <= P->v_max, ORC_MARGIN(rel(v1, P->v_max, P->v_max)));
+            conj_add(&cu, m1 >= a->m_empty, ORC_MARGIN(rel(m1, a->m_empty, a->m_empty)));
             {
-                double cm = conj_margin(&cu);
+                orc_margin_t cm = conj_margin(&cu);
                 if (cm < s->margin) s->margin = cm;
                 if (cm < s->smargin) s->smargin = cm;
             }
@@ -458,14 +468,14 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
                 double hdg = angdist(chi1 - M_PI);
                 conj_t cl;
                 conj_init(&cl);
-                conj_add(&cl, r <= P->P_runway, rel(r, P->P_runway, P->P_runway));
-                conj_add(&cl, beta <= P->P_beta, rel(beta, P->P_beta, P->P_beta));
-                conj_add(&cl, x1 > 0.0, fabs(x1) / P->P_runway);
-                conj_add(&cl, ath <= P->P_chi, rel(ath, P->P_chi, P->P_chi));
-                conj_add(&cl, hdg <= P->P_chi, rel(hdg, P->P_chi, P->P_chi));
-                conj_add(&cl, v1 <= P->P_vs, rel(v1, P->P_vs, P->P_vs));
+                conj_add(&cl, r <= P->P_runway, ORC_MARGIN(rel(r, P->P_runway, P->P_runway)));
+                conj_add(&cl, beta <= P->P_beta, ORC_MARGIN(rel(beta, P->P_beta, P->P_beta)));
+                conj_add(&cl, x1 > 0.0, ORC_MARGIN(fabs(x1) / P->P_runway));
+                conj_add(&cl, ath <= P->P_chi, ORC_MARGIN(rel(ath, P->P_chi, P->P_chi)));
+                conj_add(&cl, hdg <= P->P_chi, ORC_MARGIN(rel(hdg, P->P_chi, P->P_chi)));
+                conj_add(&cl, v1 <= P->P_vs, ORC_MARGIN(rel(v1, P->P_vs, P->P_vs)));
                 {
-                    double cm = conj_margin(&cl);
+                    orc_margin_t cm = conj_margin(&cl);
                     if (cm < s->margin) s->margin = cm;
                     if (cm < s->smargin) s->smargin = cm;
                 }
@@ -494,9 +504,9 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
                 double dh2 = dx * dx + dy * dy, adz = fabs(dz);
                 conj_t cp;
                 conj_init(&cp);
-                conj_add(&cp, dh2 < Sh2, rel(dh2, Sh2, Sh2));
-                conj_add(&cp, adz < Sv, rel(adz, Sv, Sv));
-                double cm = conj_margin(&cp);
+                conj_add(&cp, dh2 < Sh2, ORC_MARGIN(rel(dh2, Sh2, Sh2)));
+                conj_add(&cp, adz < Sv, ORC_MARGIN(rel(adz, Sv, Sv)));
+                orc_margin_t cm = conj_margin(&cp);
                 if (cm < st[i].margin) st[i].margin = cm;
                 if (cm < st[j].margin) st[j].margin = cm;
                 if (conj_ok(&cp)) { st[i].sepv = 1; st[j].sepv = 1; }
@@ -512,7 +522,7 @@ static void rollout_sample(const orc_problem *P, const orc_aircraft *A, const do
     }
 
     /* objectives (Sec. 3.5, Sec. 7.1) and per-sample cost (Sec. 3.6) */
-    double smin = INFINITY;
+    orc_margin_t smin = INFINITY;
     for (int i = 0; i < N; i++) {
         const acst *s = &st[i];
         const orc_aircraft *a = &A[i];

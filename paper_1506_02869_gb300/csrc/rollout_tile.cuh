@@ -270,7 +270,8 @@ struct CostSums {
     {
         const float za = s.z * P.Ac_inv;
         const float h = fmaxf(fmaf(-za, za, 1.0f), 0.0f);
-        sN = fmaf(h, popdense_at(P, s.x, s.y), sN);
+        // above A_c the term is 0 (h = 0): the density is not looked up
+        if (h > 0.0f) sN = fmaf(h, popdense_at(P, s.x, s.y), sN);
     }
 };
 

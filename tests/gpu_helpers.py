@@ -77,3 +77,19 @@ def compare_costs(got, ref, margin, smargin, what, max_excluded=0.02, max_partic
         what += f" worst got={g[fin][w]!r} ref={r[fin][w]!r}"
     assert emax <= COST_TOL, f"{what}: max rel err {emax:.3e} (n={fin.sum()})"
     return emax, int(fin.sum()), int((~keep).sum())
+
+
+def compare_sample_costs(got, ref, margin, smargin, what, max_aside=0.1, min_compared=100):
+    """got/ref [Ls][ns][N] per-sample costs; (l, m, i) is set aside when
+    aircraft i of particle l has a decision within TAU of its threshold in
+    sample m, or a decision that changes the set of flying aircraft does (at
+    most max_aside of them); returns (max rel err, n compared)."""
+    keep = (margin >= TAU) & (smargin[:, :, None] >= TAU)
+    assert keep.mean() >= 1 - max_aside, (what, keep.mean())
+    g, r = got[keep], ref[keep]
+    assert (np.isfinite(g) == np.isfinite(r)).all(), what + ": feasibility differs"
+    fin = np.isfinite(r)
+    err = np.abs(g[fin] - r[fin]) / np.maximum(np.abs(r[fin]), COST_FLOOR)
+    assert err.size >= min_compared and err.max() <= COST_TOL, \
+        (what, err.max() if err.size else None, err.size)
+    return float(err.max()), int(err.size)

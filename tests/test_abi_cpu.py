@@ -171,6 +171,7 @@ def test_batch_create_rejects_invalid_batches(lib):
     sched = pkg.problem_struct(ps[1].copy(L_sched=(64, 32)))
     assert create([structs[0], sched])[0] == pkg.TMA_ERR_UNSUPPORTED
     assert lib.tma_batch_mpc(None, 1, 1, None) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_batch_rollout_cost(None, None, 0, None, None, None) == pkg.TMA_ERR_INVALID_ARG
     assert lib.tma_plant_step(None, None, None) == pkg.TMA_ERR_INVALID_ARG
 
 

@@ -29,7 +29,8 @@ def _worker(rank, world, port, out):
         out[rank] = bench.max_over_ranks(elapsed, world)
         p = bench.replica_problem(rank)
         out[world + rank] = p.seed
-        args = type("A", (), {"steps": 1, "warmup": 0, "gpus": world, "reference_particles": 8})()
+        args = type("A", (), {"steps": 1, "warmup": 0, "gpus": world, "reference_particles": 8,
+                              "workload": "c3"})()
         if rank != 0:
             assert bench.run_reference(args, world, rank) == 0   # returns at once
     finally:
@@ -50,9 +51,10 @@ def test_units_and_flops_per_unit():
     p = S.config2()
     assert bench.units_per_solve(p) == 65536 * 32 * 8 * 60 * 30
     f = bench.flops_per_unit(p)
-    assert 150 < f < 260
+    assert 150 < f < 400
     assert bench.flops_per_unit(S.config3()) > f          # more pairs, soft form, noise
-    assert bench.fp32_peak_tflops(2070) == pytest.approx(80.54, rel=1e-3)
+    assert bench.flops_per_unit_tally(S.config3()) > bench.flops_per_unit_tally(p)
+    assert bench.fp32_peak_tflops(152, 2070) == pytest.approx(80.54, rel=1e-3)
 
 
 def test_oracle_sample_charges_the_wind_generation_at_its_share(monkeypatch):
@@ -66,14 +68,25 @@ def test_oracle_sample_charges_the_wind_generation_at_its_share(monkeypatch):
     monkeypatch.setattr(O, "smc_solve", lambda p, W=None, nthreads=1: seen.append((p.L, W, nthreads)))
     bench._ORACLE_WIND.clear()
     try:
-        v, dt, units = bench.oracle_sample(512, 3)
-        _, dt2, _ = bench.oracle_sample(512, 3)          # the field is not generated again
-        t_wind = bench.oracle_wind()[1]
+        for wl, full in (("c2", 65536), ("c3", 262144)):
+            seen.clear()
+            v, dt, units = bench.oracle_sample(wl, 512, 3)
+            _, dt2, _ = bench.oracle_sample(wl, 512, 3)          # the field is not generated again
+            t_wind = bench.oracle_wind(wl)[1]
+            assert seen == [(512, "field", 3), (512, "field", 3)]
+            p = bench.workload_problem(wl)
+            assert units == 512 * p.M * p.N * p.H * p.J_max
+            assert t_wind >= 0.25
+            share = t_wind * 512 / full
+            assert share <= dt < share + 0.05 and share <= dt2 < share + 0.05
+            assert v == pytest.approx(units / dt)
     finally:
         bench._ORACLE_WIND.clear()
-    assert seen == [(512, "field", 3), (512, "field", 3)]
-    assert units == 512 * 32 * 8 * 60 * 30
-    assert t_wind >= 0.25
-    share = t_wind * 512 / 65536
-    assert share <= dt < share + 0.05 and share <= dt2 < share + 0.05
-    assert v == pytest.approx(units / dt)
+
+
+def test_workloads_name_their_problem():
+    for wl, spec in bench.WORKLOADS.items():
+        p = bench.workload_problem(wl)
+        assert f"{p.N}ac-L{p.L}-M{p.M}-H{p.H}-grid{'x'.join(str(g) for g in p.grid)}-J{p.J_max}" in spec["name"]
+    p = bench.workload_problem("c3")
+    assert (p.N, p.L, p.M, p.H, p.w_noise, p.sep_mode) == (24, 262144, 64, 120, 0.1, 2)

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 import scenarios as S
-from gpu_helpers import cuda, oracle_wind
+from gpu_helpers import compare_sample_costs, cuda, oracle_wind
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,46 @@ def test_batch_solve_equals_single_solves(torch, pkg):
         assert res["best"][k] == best
     assert live == live_single
     assert (lat > 0).all() and np.isfinite(lat).all()
+
+
+def test_batched_rollout_matches_oracle_at_full_size(torch, pkg):
+    """The batched persistent rollout against the FP64 oracle directly (not
+    only through the single-scenario path): scenarios of the batched workload
+    with 2, about 17 and 32 aircraft at its full sizes (L 16384, M 16, H 60),
+    one persistent launch; the per-sample costs of 32 sampled particles per
+    scenario, every sample, compared one by one."""
+    ps_all = S.config5(n_scen=256)
+    Ns_all = np.array([p.N for p in ps_all])
+    pick = [int(np.nonzero(Ns_all == 2)[0][0]), int(np.argmin(np.abs(Ns_all - 17))),
+            int(np.nonzero(Ns_all == 32)[0][0])]
+    ps = [ps_all[k] for k in pick]
+    Ns = [p.N for p in ps]
+    L, M = ps[0].L, ps[0].M
+    assert (L, M, ps[0].H) == (16384, 16, 60) and Ns[0] == 2 and Ns[2] == 32
+    rng = np.random.default_rng(80)
+    us = []
+    for p in ps:
+        u = S.mild_controls(p, L, rng)
+        u[: L // 4] = S.random_controls(p, L // 4, rng)
+        us.append(u)
+    J = 2
+    b = pkg.tma_batch_create(ps)
+    packed = torch.from_numpy(np.concatenate([u.reshape(-1) for u in us])).cuda()
+    cost = torch.full((M * L * sum(Ns),), float("nan"), dtype=torch.float32, device="cuda")
+    pkg.tma_batch_rollout_cost(b, packed, J, cost)
+    torch.cuda.synchronize()
+    pkg.tma_batch_destroy(b)
+    cost = cost.cpu().numpy().astype(np.float64)
+    off = 0
+    for k, p in enumerate(ps):
+        block = cost[off: off + M * p.N * L].reshape(M, p.N, L)
+        off += M * p.N * L
+        assert not np.isnan(block).any()
+        pidx = np.unique(np.r_[rng.choice(L, 30, replace=False), [0, L - 1]])
+        ref = O.rollout_at_samples(p, us[k][pidx].astype(np.float64), J, list(range(M)), pidx=pidx,
+                                   soft=False, nthreads=8)
+        compare_sample_costs(block[:, :, pidx].transpose(2, 0, 1), ref["cost"], ref["margin"],
+                             ref["smargin"], f"batched N={p.N}")
 
 
 def test_batch_solve_with_five_segments_equals_single_solves(torch, pkg):

@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 import scenarios as S
-from gpu_helpers import COST_FLOOR, COST_TOL, TAU, cuda
+from gpu_helpers import compare_sample_costs, cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -25,20 +25,6 @@ def pkg(torch):
     return pkg
 
 
-def _check(got, ref, margin, smargin, what, max_aside=0.1):
-    """got/ref [Ls][ns][N]; (l, m, i) set aside when aircraft i of particle l
-    has a decision within TAU of its threshold in sample m, or a decision
-    that changes the set of flying aircraft does."""
-    keep = (margin >= TAU) & (smargin[:, :, None] >= TAU)
-    assert keep.mean() >= 1 - max_aside, (what, keep.mean())
-    g, r = got[keep], ref[keep]
-    assert (np.isfinite(g) == np.isfinite(r)).all(), what + ": feasibility differs"
-    fin = np.isfinite(r)
-    err = np.abs(g[fin] - r[fin]) / np.maximum(np.abs(r[fin]), COST_FLOOR)
-    assert err.size > 100 and err.max() <= COST_TOL, (what, err.max() if err.size else None, err.size)
-    return err.max()
-
-
 def _run(torch, pkg, p, J, pidx, samples, rng):
     u = S.mild_controls(p, p.L, rng)
     u[: p.L // 4] = S.random_controls(p, p.L // 4, rng)
@@ -50,10 +36,11 @@ def _run(torch, pkg, p, J, pidx, samples, rng):
         if soft else None
     sol.close()
     ref = O.rollout_at_samples(p, u[pidx], J, samples, pidx=pidx, soft=soft, nthreads=8)
-    out = {"hard": _check(sc.transpose(2, 0, 1), ref["cost"], ref["margin"], ref["smargin"], "hard")}
+    out = {"hard": compare_sample_costs(sc.transpose(2, 0, 1), ref["cost"], ref["margin"], ref["smargin"],
+                                        "hard")}
     if soft:
-        out["soft"] = _check(scs.transpose(2, 0, 1), ref["cost_soft"], ref["margin"], ref["smargin"],
-                             "soft")
+        out["soft"] = compare_sample_costs(scs.transpose(2, 0, 1), ref["cost_soft"], ref["margin"],
+                                           ref["smargin"], "soft")
     return out
 
 

@@ -4,11 +4,11 @@ differences; its proposal and accept step, pinned by the Metropolis-Hastings
 ratio and Gaussian-target invariance).
 
 Gradient bar: relative L2 error per particle <= 1e-3 of the oracle's gradient,
-for particles whose threshold decisions are not within 1e-5 (relative) of
-their thresholds in the oracle.  A gradient also has kinks (|.|, the wrapped
-angle, the min of the separation gap) where FP32 and FP64 may take opposite
-sides; a small share of particles (<= 3 %) may exceed the bar, none by more
-than 5e-2."""
+for every particle whose threshold decisions are not within 1e-5 (relative) of
+their thresholds in the oracle.  (A gradient also has kinks -- |.|, the
+wrapped angle, the min of the separation gap -- where FP32 and FP64 could take
+opposite sides; on these seeded cases no particle comes near the bar: the
+largest error is 5.7e-5, so no allowance for them is made.)"""
 import numpy as np
 import pytest
 
@@ -84,11 +84,44 @@ def test_gradient_matches_oracle_adjoint(torch, pkg, case):
         errs.append(e)
     errs = np.array(errs)
     n_bad = int((errs > GRAD_TOL).sum())
-    assert n_bad <= max(1, 0.03 * errs.size) and errs.max() <= 5e-2, \
-        (case, n_bad, errs.size, float(np.median(errs)), float(errs.max()))
+    print(f"gradient {case}: {errs.size} particles compared, {n_bad} above {GRAD_TOL}, "
+          f"median {np.median(errs):.2e}, max {errs.max():.2e}")
+    assert n_bad == 0, (case, n_bad, errs.size, float(np.median(errs)), float(errs.max()))
     # infeasible particles: +inf cost and a zero gradient
     inf = ~np.isfinite(g["cost"])
     assert not g["grad"][inf].any()
+
+
+def test_gradient_matches_oracle_adjoint_at_full_size(torch, pkg):
+    """The 12-aircraft workload at its full size (L 16384, M 16, H 60,
+    softplus separation, checkpoints every 10 steps) in the launch the solver
+    runs; the gradients of 64 sampled particles against the oracle's adjoint
+    (the compared ones: those without a decision near its threshold and
+    feasible)."""
+    p = S.config4()
+    assert (p.L, p.M, p.N, p.H) == (16384, 16, 12, 60)
+    J = 3
+    g = _grad_case(torch, pkg, p, J, seed=21)
+    g["sol"].close()
+    rng = np.random.default_rng(22)
+    pidx = np.unique(np.r_[rng.choice(p.L, 62, replace=False), [0, p.L - 1]])
+    W = oracle_wind(p)
+    ref = O.rollout(p, g["u"][pidx].astype(np.float64), J, pidx=pidx, W=W, nthreads=8)
+    keep = (ref["smargin"] >= TAU) & (ref["margin"].min(axis=0) >= TAU)
+    feas = np.isfinite(ref["cbar_soft"]).all(axis=0)
+    assert np.array_equal(np.isfinite(g["cost"][pidx])[keep], feas[keep])
+    errs = []
+    for q in np.nonzero(keep & feas)[0]:
+        l = int(pidx[q])
+        c_ref, g_ref = O.rollout_grad(p, g["u"][l].astype(np.float64), W, l=l, J=J)
+        assert abs(g["cost"][l] - c_ref) <= 1e-4 * max(abs(c_ref), 1e-2)
+        errs.append(np.linalg.norm(g["grad"][l] - g_ref) / max(np.linalg.norm(g_ref), 1e-30))
+    errs = np.array(errs)
+    n_bad = int((errs > GRAD_TOL).sum())
+    print(f"full-size gradient: {errs.size} particles compared, {n_bad} above {GRAD_TOL}, "
+          f"median {np.median(errs):.2e}, max {errs.max():.2e}")
+    assert errs.size >= 20
+    assert n_bad == 0, (n_bad, errs.size, float(errs.max()))
 
 
 def test_gradient_pass_costs_are_the_rollout_costs(torch, pkg):
