@@ -411,8 +411,22 @@ tma_status tma_batch_solve(tma_batch *b, tma_stream_t stream);
  * into a CUDA graph (re-captured when n_steps changes) and launched; the
  * results equal those without the graph. */
 tma_status tma_batch_mpc(tma_batch *b, int32_t n_steps, int32_t use_graph, tma_stream_t stream);
-/* The batched rollout alone (the persistent launch inside tma_batch_solve;
- * Sec. 3.3-3.6 for every scenario), on given controls: generates every
+/* The batch's rollout dispatch (the paper's layout sweep of Sec. 4.4 done by
+ * measurement): at creation every scenario's launch variant of the
+ * single-scenario rollout kernel is tuned (cached like the solvers'), and two
+ * forms are timed on one rollout of the whole batch -- 0: one persistent
+ * launch over a work queue of every scenario's tiles; 1: one launch of the
+ * single-scenario kernel per scenario, spread over four streams forked from and
+ * joined to the caller's (also inside a graph capture) -- and the
+ * faster is kept.  get: the form in use and the two timings (ms; any pointer
+ * may be NULL).  set: forces a form (0 or 1, else TMA_ERR_INVALID_ARG); a
+ * captured MPC loop of the other form is discarded.  Both forms compute the
+ * same bits. */
+tma_status tma_batch_get_dispatch(tma_batch *b, int32_t *dispatch, float *ms_persistent, float *ms_per_scenario);
+tma_status tma_batch_set_dispatch(tma_batch *b, int32_t dispatch);
+/* The batched rollout alone (the rollout inside tma_batch_solve, in the
+ * batch's dispatch form; Sec. 3.3-3.6 for every scenario), on given controls:
+ * generates every
  * scenario's wind field for its current MPC step, then rolls out d_u at
  * iteration J (the first SampleSchedule(J) samples in sample mode 1, else all
  * M) and writes the per-sample costs.  Packed layouts, scenario after scenario

@@ -41,6 +41,7 @@ EXPORTS = [
     "tma_mh_stats", "tma_get_grad_tuning", "tma_get_particles", "tma_mpc_run", "tma_get_error",
     "tma_resample_to", "tma_move_to", "tma_set_finished", "tma_get_status", "tma_set_tuning",
     "tma_lse_resample_workspace", "tma_lse_resample", "tma_batch_rollout_cost",
+    "tma_batch_get_dispatch", "tma_batch_set_dispatch",
 ]
 
 
@@ -157,6 +158,8 @@ def lib():
                 "tma_batch_latency": ([vp, P(d), st], C.c_int),
                 "tma_batch_live_steps": ([vp, P(u64), st], C.c_int),
                 "tma_batch_rollout_cost": ([vp, vp, i32, vp, vp, st], C.c_int),
+                "tma_batch_get_dispatch": ([vp, P(i32), P(C.c_float), P(C.c_float)], C.c_int),
+                "tma_batch_set_dispatch": ([vp, i32], C.c_int),
                 "tma_resample_noalloc": ([vp, i32, i64, u64, u32, u32, u32, vp, st], C.c_int),
                 "tma_profile_read": ([vp, P(TmaProfile), C.c_int], C.c_int),
                 "tma_set_wind_stream": ([vp, u32], C.c_int),
@@ -548,6 +551,18 @@ def tma_batch_solve(h, stream=None):
 
 def tma_batch_mpc(h, n_steps, use_graph=True, stream=None):
     _check(lib().tma_batch_mpc(h, int(n_steps), int(bool(use_graph)), _stream(stream)), "tma_batch_mpc")
+
+
+def tma_batch_get_dispatch(h):
+    """(form in use: 0 persistent launch, 1 a launch per scenario; timed ms of
+    each form on one rollout of the batch at creation)."""
+    d, a, b = C.c_int32(), C.c_float(), C.c_float()
+    _check(lib().tma_batch_get_dispatch(h, C.byref(d), C.byref(a), C.byref(b)), "tma_batch_get_dispatch")
+    return d.value, {0: a.value, 1: b.value}
+
+
+def tma_batch_set_dispatch(h, dispatch):
+    _check(lib().tma_batch_set_dispatch(h, int(dispatch)), "tma_batch_set_dispatch")
 
 
 def tma_batch_rollout_cost(h, u, J, cost_ms, cost_ms_soft=None, stream=None):

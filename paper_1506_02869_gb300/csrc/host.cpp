@@ -438,20 +438,58 @@ static const uint32_t *dyn_mpc(const tma_solver *s)
 static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune_cache;
 
-static std::string tune_key(const tma_solver *s)
+static std::string tune_key_of(const tma_problem &p, int device)
 {
     cudaDeviceProp prop;
     char key[320];
-    if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) prop.name[0] = 0;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) prop.name[0] = 0;
     // the workload's size class: tiles of the tuning launch (32 particles x one
     // wind sample each, at most 8192 particles), by power of two -- a small
     // solver's choice is not reused for a large one
-    const long long tiles = (std::min<long long>(s->prob.L, 8192) + 31) / 32 * (long long)s->prob.M;
+    const long long tiles = (std::min<long long>(p.L, 8192) + 31) / 32 * (long long)p.M;
     int lg = 0;
     while ((2LL << lg) <= tiles) ++lg;
-    snprintf(key, sizeof key, "%s|N=%d|pop=%d|wind=%d|rolling=%d|sep=%d|tiles=2^%d", prop.name,
-             s->prob.N, s->prob.pop_n[0] > 0, s->prob.wind_mode, s->prob.rolling, s->prob.sep_mode, lg);
+    snprintf(key, sizeof key, "%s|N=%d|pop=%d|wind=%d|rolling=%d|sep=%d|tiles=2^%d", prop.name, p.N,
+             p.pop_n[0] > 0, p.wind_mode, p.rolling, p.sep_mode, lg);
     return key;
+}
+
+static std::string tune_key(const tma_solver *s) { return tune_key_of(s->prob, s->device); }
+
+// Times every launch variant of the rollout kernel valid for P on the given
+// buffers (Lp particles, all wind samples, iteration 0, the hard costs only):
+// one untimed launch and three timed per variant; *best = the fastest, and the
+// timings in tv[] / tms[] (*nt entries).
+static cudaError_t time_rollout_variants(const ProblemC &P, const DynState *dyn, const float *u,
+                                         const float *W, int64_t Lp, float *cost, cudaStream_t st,
+                                         cudaEvent_t e0, cudaEvent_t e1, int *best, int *nt, int *tv,
+                                         float *tms)
+{
+    int cand[kMaxRolloutVariants];
+    const int nc = rollout_variants(P, cand);
+    *best = cand[0];
+    *nt = 0;
+    float best_ms = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        e = launch_rollout(P, dyn, u, W, Lp, 0, cost, nullptr, nullptr, st, cand[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+            e = launch_rollout(P, dyn, u, W, Lp, 0, cost, nullptr, nullptr, st, cand[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        tv[*nt] = cand[c];
+        tms[*nt] = ms / 3.0f;
+        ++*nt;
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = cand[c];
+        }
+    }
+    return e;
 }
 
 }  // namespace tma
@@ -768,28 +806,9 @@ static tma_status autotune_rollout(tma_solver *s)
     ctrl_f(s->prob, lo, hi, sg);
     if (r == TMA_OK) {
         e = launch_init_controls(s->P, s->d_dyn, lo, hi, s->d_u[0], Lp, st);
-        float best = 1e30f;
-        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-            // one untimed launch, then three timed
-            e = launch_rollout(s->P, s->d_dyn, s->d_u[0], s->d_W, Lp, 0, s->d_cost_ms, nullptr,
-                               nullptr, st, cand[c]);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
-                e = launch_rollout(s->P, s->d_dyn, s->d_u[0], s->d_W, Lp, 0, s->d_cost_ms, nullptr,
-                                   nullptr, st, cand[c]);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) break;
-            s->tuned_variant[s->n_tuned] = cand[c];
-            s->tuned_ms[s->n_tuned] = ms / 3.0f;
-            ++s->n_tuned;
-            if (ms < best) {
-                best = ms;
-                s->rollout_variant = cand[c];
-            }
-        }
+        if (e == cudaSuccess)
+            e = time_rollout_variants(s->P, s->d_dyn, s->d_u[0], s->d_W, Lp, s->d_cost_ms, st, e0, e1,
+                                      &s->rollout_variant, &s->n_tuned, s->tuned_variant, s->tuned_ms);
         if (e != cudaSuccess) r = cuda_fail(e);
     }
     cleanup();
@@ -1592,6 +1611,11 @@ static void batch_free(tma_batch *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (int q = 0; q < tma_batch::kAuxStreams; ++q) {
+        if (b->aux[q]) cudaStreamDestroy(b->aux[q]);
+        if (b->join_ev[q]) cudaEventDestroy(b->join_ev[q]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     void *ptrs[] = {b->d_probs, b->d_scen, b->d_seg_scen, b->d_segkeys, b->d_dyns, b->d_Lxy,
                     b->d_Btmp, b->d_W, b->d_u[0], b->d_u[1], b->d_cost_ms, b->d_cost_ms_soft,
                     b->d_cbar, b->d_cbar_soft, b->d_wtilde, b->d_anc, b->d_work, b->d_best,
@@ -1629,6 +1653,32 @@ static tma_status batch_wind(tma_batch *b, cudaStream_t st)
     return TMA_OK;
 }
 
+// One rollout of every scenario at iteration J (Mj wind samples), in the
+// batch's dispatch form.
+static cudaError_t batch_rollout(tma_batch *b, const float *d_u, int J, int Mj, float *cost,
+                                 float *cost_soft, int dispatch, cudaStream_t st)
+{
+    if (dispatch == 0)
+        return launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, d_u, b->d_W, b->L, J, Mj,
+                                    cost, cost_soft, b->d_live, b->d_queue, b->grid, b->probs[0].wind_mode, st);
+    // scenarios round-robin over the auxiliary streams, so that one launch's
+    // last wave overlaps the next scenario's first
+    const int ns = tma_batch::kAuxStreams;
+    cudaError_t e = cudaEventRecord(b->fork_ev, st);
+    for (int q = 0; q < ns && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(b->aux[q], b->fork_ev, 0);
+    for (int s = 0; s < b->n_scen && e == cudaSuccess; ++s) {
+        const BatchScen &sc = b->scen[s];
+        ProblemC Ps = b->pc_h[s];
+        Ps.M = Mj;
+        const size_t co = (size_t)sc.seg_off * b->M * (size_t)b->L;
+        e = launch_rollout(Ps, b->d_dyns + s, d_u + sc.u_off, b->d_W + (size_t)sc.w_off * 4, b->L, J, cost + co,
+                           cost_soft ? cost_soft + co : nullptr, b->d_live, b->aux[s % ns], b->scen_variant[s]);
+    }
+    for (int q = 0; q < ns && e == cudaSuccess; ++q) e = cudaEventRecord(b->join_ev[q], b->aux[q]);
+    for (int q = 0; q < ns && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(st, b->join_ev[q], 0);
+    return e;
+}
+
 static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
 {
     const long long L = b->L;
@@ -1645,10 +1695,8 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
     float *cb = b->sep_mode == 1 ? b->d_cbar_soft : b->d_cbar;
     for (int J = 0; J < b->J_max; ++J) {
         const int Mj = samples_of(b->probs[0], J);
-        TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, b->d_u[cur],
-                                      b->d_W, L, J, Mj, b->d_cost_ms,
-                                      soft ? b->d_cost_ms_soft : nullptr, b->d_live, b->d_queue,
-                                      b->grid, b->probs[0].wind_mode, st));
+        TMA_CUDA(batch_rollout(b, b->d_u[cur], J, Mj, b->d_cost_ms, soft ? b->d_cost_ms_soft : nullptr,
+                               b->dispatch, st));
         TMA_CUDA(launch_batch_sample_mean(b->d_cost_ms, b->d_scen, b->d_seg_scen, b->nseg, L, b->M,
                                           Mj, b->d_cbar, st));
         if (soft)
@@ -1669,6 +1717,66 @@ static tma_status batch_solve_device(tma_batch *b, cudaStream_t st)
                                  b->d_best_sum, b->d_ninf, b->d_best_u, b->d_t_end, st));
     b->final_u = cur;
     return TMA_OK;
+}
+
+// The batch's rollout dispatch: every scenario's variant of the single-scenario
+// kernel (the solvers' autotuner and cache, timed on the scenario's own first
+// 8192 particles), then both dispatch forms timed on the whole batch at
+// iteration 0 (uniform initial controls; one untimed and one timed rollout
+// each); the faster form is kept.  On an idle device, like the solvers' tuner.
+static tma_status batch_tune(tma_batch *b)
+{
+    const int n = b->n_scen;
+    b->scen_variant.assign(n, 0);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TMA_CUDA(cudaDeviceSynchronize());
+    TMA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamDestroy(st);
+    };
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    tma_status r = e == cudaSuccess ? batch_wind(b, st) : cuda_fail(e);
+    if (r == TMA_OK) e = launch_batch_init(b->d_scen, b->d_seg_scen, b->d_dyns, b->nseg, b->L, b->S, b->d_u[0], st);
+    const int64_t Lp = std::min<int64_t>(b->L, 8192);
+    for (int s = 0; s < n && r == TMA_OK && e == cudaSuccess; ++s) {
+        const std::string key = tune_key_of(b->probs[s], b->device);
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                b->scen_variant[s] = it->second;
+                continue;
+            }
+        }
+        const BatchScen &sc = b->scen[s];
+        int best = 0, nt = 0, tv[kMaxRolloutVariants];
+        float tms[kMaxRolloutVariants];
+        e = time_rollout_variants(b->pc_h[s], b->d_dyns + s, b->d_u[0] + sc.u_off, b->d_W + (size_t)sc.w_off * 4,
+                                  Lp, b->d_cost_ms + (size_t)sc.seg_off * b->M * (size_t)b->L, st, e0, e1, &best,
+                                  &nt, tv, tms);
+        if (e == cudaSuccess) {
+            b->scen_variant[s] = best;
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            g_tune_cache[key] = best;
+        }
+    }
+    const int M0 = samples_of(b->probs[0], 0);
+    for (int form = 0; form < 2 && r == TMA_OK && e == cudaSuccess; ++form) {
+        e = batch_rollout(b, b->d_u[0], 0, M0, b->d_cost_ms, nullptr, form, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = batch_rollout(b, b->d_u[0], 0, M0, b->d_cost_ms, nullptr, form, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b->dispatch_ms[form], e0, e1);
+    }
+    if (r == TMA_OK && e != cudaSuccess) r = cuda_fail(e);
+    if (r == TMA_OK) b->dispatch = b->dispatch_ms[1] < b->dispatch_ms[0] ? 1 : 0;
+    cleanup();
+    return r;
 }
 
 static tma_status batch_mpc_steps(tma_batch *b, int n_steps, cudaStream_t st)
@@ -1851,7 +1959,13 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
         if ((e = cudaMemcpy(b->d_dyns, b->dyn_h.data(), sizeof(DynState) * n_scen, cudaMemcpyHostToDevice))) return fail(e);
         if ((e = cudaMemcpy(b->d_Lxy, lxy->L.data(), lxy->L.size() * 4, cudaMemcpyHostToDevice))) return fail(e);
         if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking))) return fail(e);
+        for (int q = 0; q < tma_batch::kAuxStreams; ++q) {
+            if ((e = cudaStreamCreateWithFlags(&b->aux[q], cudaStreamNonBlocking))) return fail(e);
+            if ((e = cudaEventCreateWithFlags(&b->join_ev[q], cudaEventDisableTiming))) return fail(e);
+        }
+        if ((e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming))) return fail(e);
         b->grid = batch_rollout_grid();
+        b->pc_h = pc;
     } catch (const std::bad_alloc &) {
         if (b) {
             batch_free(b);
@@ -1859,7 +1973,34 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
         }
         return TMA_ERR_OOM;
     }
+    const tma_status r = batch_tune(b);
+    if (r != TMA_OK) {
+        batch_free(b);
+        delete b;
+        return r;
+    }
     *out = b;
+    return TMA_OK;
+}
+
+tma_status tma_batch_get_dispatch(tma_batch *b, int32_t *dispatch, float *ms_persistent, float *ms_per_scenario)
+{
+    if (!b) return TMA_ERR_INVALID_ARG;
+    if (dispatch) *dispatch = b->dispatch;
+    if (ms_persistent) *ms_persistent = b->dispatch_ms[0];
+    if (ms_per_scenario) *ms_per_scenario = b->dispatch_ms[1];
+    return TMA_OK;
+}
+
+tma_status tma_batch_set_dispatch(tma_batch *b, int32_t dispatch)
+{
+    if (!b || (dispatch != 0 && dispatch != 1)) return TMA_ERR_INVALID_ARG;
+    if (dispatch != b->dispatch && b->graph) {      // a captured loop holds the other form
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_steps = 0;
+    }
+    b->dispatch = dispatch;
     return TMA_OK;
 }
 
@@ -1951,9 +2092,8 @@ tma_status tma_batch_rollout_cost(tma_batch *b, const float *d_u, int32_t J, flo
     if (r != TMA_OK) return r;
     const bool soft = b->sep_mode != 0 && d_cost_ms_soft != nullptr;
     TMA_CUDA(cudaMemsetAsync(b->d_live, 0, 8, st));
-    TMA_CUDA(launch_batch_rollout(b->d_probs, b->d_scen, b->n_scen, b->d_dyns, d_u, b->d_W, b->L, J,
-                                  samples_of(b->probs[0], J), d_cost_ms, soft ? d_cost_ms_soft : nullptr,
-                                  b->d_live, b->d_queue, b->grid, b->probs[0].wind_mode, st));
+    TMA_CUDA(batch_rollout(b, d_u, J, samples_of(b->probs[0], J), d_cost_ms, soft ? d_cost_ms_soft : nullptr,
+                           b->dispatch, st));
     return TMA_OK;
 }
 

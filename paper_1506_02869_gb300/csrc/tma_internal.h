@@ -327,6 +327,18 @@ struct tma_batch {
     unsigned long long *d_t_start = nullptr, *d_t_end = nullptr, *d_live = nullptr, *d_queue = nullptr;
     unsigned int *d_flags = nullptr;
     unsigned int *d_err = nullptr;      // sticky error word (TMA_DEVERR_BOUNDS), read by tma_batch_results
+    // rollout dispatch, chosen at creation by timing both forms on the batch:
+    // 0 one persistent launch over every scenario's tiles, 1 one launch of the
+    // single-scenario kernel per scenario (its autotuned variant each)
+    int dispatch = 0;
+    float dispatch_ms[2] = {0.f, 0.f};
+    std::vector<tma::ProblemC> pc_h;    // every scenario's kernel problem (host copy)
+    std::vector<int> scen_variant;      // its variant of the single-scenario rollout kernel
+    // form 1 spreads the per-scenario launches over these streams (forked from
+    // and joined to the caller's stream by events, also inside a capture)
+    static constexpr int kAuxStreams = 4;
+    cudaStream_t aux[kAuxStreams] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kAuxStreams] = {};
     std::vector<float *> d_pops;
     int final_u = 0;
     // captured MPC loop

@@ -172,6 +172,8 @@ def test_batch_create_rejects_invalid_batches(lib):
     assert create([structs[0], sched])[0] == pkg.TMA_ERR_UNSUPPORTED
     assert lib.tma_batch_mpc(None, 1, 1, None) == pkg.TMA_ERR_INVALID_ARG
     assert lib.tma_batch_rollout_cost(None, None, 0, None, None, None) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_batch_get_dispatch(None, None, None, None) == pkg.TMA_ERR_INVALID_ARG
+    assert lib.tma_batch_set_dispatch(None, 0) == pkg.TMA_ERR_INVALID_ARG
     assert lib.tma_plant_step(None, None, None) == pkg.TMA_ERR_INVALID_ARG
 
 

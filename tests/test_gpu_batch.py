@@ -38,11 +38,18 @@ def _states(p):
     return np.array([[a[k] for k in ("x", "y", "z", "v", "chi", "m")] for a in p.aircraft])
 
 
-def test_batch_solve_equals_single_solves(torch, pkg):
+@pytest.mark.parametrize("dispatch", [0, 1])
+def test_batch_solve_equals_single_solves(torch, pkg, dispatch):
+    """Both rollout dispatch forms (one persistent launch; a launch per
+    scenario)."""
     ps = mixed_batch(6)
     Ns = [p.N for p in ps]
     assert min(Ns) <= 3 and max(Ns) > 16
     b = pkg.tma_batch_create(ps)
+    form, timed = pkg.tma_batch_get_dispatch(b)
+    assert form in (0, 1) and timed[0] > 0 and timed[1] > 0
+    assert form == (1 if timed[1] < timed[0] else 0)
+    pkg.tma_batch_set_dispatch(b, dispatch)
     pkg.tma_batch_solve(b)
     res = pkg.tma_batch_results(b, Ns, ps[0].S)
     live = pkg.tma_batch_live_steps(b)
@@ -85,11 +92,16 @@ def test_batched_rollout_matches_oracle_at_full_size(torch, pkg):
     J = 2
     b = pkg.tma_batch_create(ps)
     packed = torch.from_numpy(np.concatenate([u.reshape(-1) for u in us])).cuda()
-    cost = torch.full((M * L * sum(Ns),), float("nan"), dtype=torch.float32, device="cuda")
-    pkg.tma_batch_rollout_cost(b, packed, J, cost)
-    torch.cuda.synchronize()
+    costs = []
+    for form in (0, 1):                        # the persistent launch, then a launch per scenario
+        pkg.tma_batch_set_dispatch(b, form)
+        c = torch.full((M * L * sum(Ns),), float("nan"), dtype=torch.float32, device="cuda")
+        pkg.tma_batch_rollout_cost(b, packed, J, c)
+        torch.cuda.synchronize()
+        costs.append(c.cpu().numpy())
     pkg.tma_batch_destroy(b)
-    cost = cost.cpu().numpy().astype(np.float64)
+    assert np.array_equal(costs[0], costs[1])
+    cost = costs[0].astype(np.float64)
     off = 0
     for k, p in enumerate(ps):
         block = cost[off: off + M * p.N * L].reshape(M, p.N, L)
