@@ -198,7 +198,7 @@ struct TermGrad {
             dratio = s.th * (1.0f / 3.0f);
         } else {
             float sn, cs;
-            sincosf(ath, &sn, &cs);
+            __sincosf(ath, &sn, &cs);                 // ath in [0, pi]: no range reduction needed
             if (sn >= 0.25f * ath) {
                 ratio = ath / sn;
                 dratio = sgnf(s.th) * (sn - ath * cs) / (sn * sn);
@@ -251,7 +251,7 @@ __device__ __forceinline__ void step_adjoint(const ProblemC &P, const AircraftC 
     const float dcg_dv = uh * uh * iv * iv * iv * icg;
     const float dcg_dh = -uh * iv * iv * icg;
     const float base = fmaxf(fmaf(-2.2558e-5f, z, 1.0f), 1e-30f);
-    const float rho = 1.225f * exp2f(4.2559f * log2f(base));
+    const float rho = 1.225f * ex2_approx(4.2559f * __log2f(base));   // as the forward step
     const float q = A.halfS * rho * v * v;
     const float iq = 1.0f / q;
     const float dq_dz = q * (4.2559f * -2.2558e-5f) / base;
@@ -276,7 +276,7 @@ __device__ __forceinline__ void step_adjoint(const ProblemC &P, const AircraftC 
     float2 dwx, dwy, dwz;
     wind_grad(P, Wk, x, y, z, dwx, dwy, dwz);
     float sc, cc;
-    sincosf(chi, &sc, &cc);
+    sincos_reduced(chi, &sc, &cc);
     const float proj = fmaf(cc, X, sc * Y);            // along-track adjoint
     const float fe = FF * dt * eta;                     // fuel adjoint times d F'/d T
     const float nX = X + dt * fmaf(X, dwx.x, Y * dwx.y);
