@@ -74,6 +74,19 @@ def flops_per_unit(p, particles=8, samples=2):
     return ops / live
 
 
+def flops_per_unit_isolated(workload):
+    """flops_per_unit of the named workload, counted in a child process (the
+    counting build of the oracle never shares a process with the timed GPU
+    work); None if the child fails."""
+    code = ("import sys; sys.path.insert(0, %r); import bench; "
+            "print(bench.flops_per_unit(bench.workload_problem(%r)))" % (ROOT, workload))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return None
+
+
 def flops_per_unit_tally(p):
     """The same work tallied by hand from the per-step formulas (for
     comparison): +, -, *, /, sqrt, min/max/compare and each elementary function
@@ -406,7 +419,8 @@ def run_ours(args, world, rank, local):
 
     # ---- roofline of the rollout kernel (the dominant kernel)
     roll_ms, roll_n = prof["rollout"]
-    fpu = flops_per_unit(p)
+    fpu_counted = flops_per_unit_isolated(args.workload)
+    fpu = fpu_counted if fpu_counted else flops_per_unit_tally(p)
     live_per_launch = live_per_solve / p.J_max
     achieved = fpu * live_per_launch / (roll_ms / roll_n * 1e-3) / 1e12 if roll_n else None
     # FP32 peak at the SM clock sampled during the timed region (else the
@@ -431,8 +445,9 @@ def run_ours(args, world, rank, local):
         "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_clock:.0f} MHz "
                        f"({clock_src})",
         "flops_per_unit": fpu,
-        "flops_per_unit_source": "counted on the FP64 oracle's rollout (oracle/opcount.cpp), 8 uniform "
-                                 "initial particles x 2 wind samples",
+        "flops_per_unit_source": ("counted on the FP64 oracle's rollout (oracle/opcount.cpp), 8 uniform "
+                                  "initial particles x 2 wind samples" if fpu_counted else
+                                  "hand tally (the counting run failed)"),
         "flops_per_unit_hand_tally": flops_per_unit_tally(p), "live_units_per_launch": live_per_launch,
         "units_per_launch": p.L * p.M * p.N * p.H, "launch_ms": roll_ms / roll_n if roll_n else None,
         "stage_ms_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items() if total_ms},

@@ -21,10 +21,11 @@
 #include <string.h>
 
 namespace opcount {
-// one count per thread; the counting library is built without OpenMP, so the
-// rollout runs on the calling thread
-thread_local uint64_t t_ops = 0;
-thread_local int t_paused = 0;
+// one count for the library: it is built without OpenMP, so the rollout runs
+// on the calling thread, and its callers count from one thread at a time
+// (plain globals, no thread-local storage in a library loaded at run time)
+uint64_t t_ops = 0;
+int t_paused = 0;
 inline void tick(uint64_t n = 1)
 {
     if (!t_paused) t_ops += n;
@@ -92,8 +93,7 @@ static inline orc_plain_double opcount_resume(orc_plain_double v) { --opcount::t
 
 extern "C" {
 
-/* Operations the calling thread counted since the last reset; reset != 0
- * zeroes the count. */
+/* Operations counted since the last reset; reset != 0 zeroes the count. */
 uint64_t orc_opcount_read(int reset)
 {
     const uint64_t n = opcount::t_ops;
