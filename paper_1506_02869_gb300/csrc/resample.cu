@@ -287,20 +287,22 @@ __device__ __forceinline__ bool above(const U128 &SL, unsigned long long Q, unsi
 // Number of particles l in [0, Lout) whose threshold lies below S (S Lout >
 // l Q + Rhi): the condition holds up to the count and fails beyond.  The FP32
 // estimate S Lout / Q - r 2^-32 has a relative error below 2^-22, so for
-// Lout <= 2^21 it lies within 1/2 of the count's real bound; with
-// n0 = ceil(estimate) the count is n0 - 1, n0 or n0 + 1, told apart by the
-// exact conditions at n0 - 1 and n0.  Larger Lout steps from n0 until both
-// conditions agree with the count.
+// Lout <= 2^21 it lies within 1/2 of the count's real bound x (the count is
+// ceil(x), or x when x is an integer): the count is c0 = ceil(est - 1/2) or
+// c0 + 1, told apart by the exact condition at c0.  Larger Lout steps from
+// ceil(est) until the conditions agree with the count.
 __device__ __forceinline__ int count_below(unsigned long long S, const Thresholds &T)
 {
     const U128 SL = mul64x32(S, T.Lout);
     const float est = fminf(fmaxf(fmaf(u64_to_float(S), T.ratio, -T.shift), 0.0f), (float)T.Lout);
-    int n = __float2int_ru(est);
     if (T.Lout <= (1u << 21)) {
-        const bool below_prev = n > 0 && above(SL, T.Q, T.Rhi, n - 1);
-        const bool below_n = n < (int)T.Lout && above(SL, T.Q, T.Rhi, n);
-        return n - (n > 0 && !below_prev ? 1 : 0) + (below_n ? 1 : 0);
+        // the true bound x lies within 1/2 of est, so with c0 = ceil(est - 1/2)
+        // the particles below c0 - 1 < x all count and the count is c0 or
+        // c0 + 1: one exact comparison, at c0, tells them apart
+        const int c0 = max(__float2int_ru(est - 0.5f), 0);
+        return c0 >= (int)T.Lout ? (int)T.Lout : c0 + (above(SL, T.Q, T.Rhi, c0) ? 1 : 0);
     }
+    int n = __float2int_ru(est);
     while (n < (int)T.Lout && above(SL, T.Q, T.Rhi, n)) ++n;
     while (n > 0 && !above(SL, T.Q, T.Rhi, n - 1)) --n;
     return n;
