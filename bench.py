@@ -110,7 +110,8 @@ def flops_per_unit_tally(p):
 # rollout kernel, from a one-pass ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch late in a solve); valid only for the
 # kernel sources they were taken on.
-ROLLOUT_TRAFFIC = {"sources_sha256_16": None, "bytes_per_launch": {}}
+ROLLOUT_TRAFFIC = {"sources_sha256_16": "6a939771f200f0c9",
+                   "bytes_per_launch": {"c3:rollout_kernel": 56576245248 + 3255205376}}
 
 
 def rollout_kernel_name(variant):
