@@ -115,8 +115,9 @@ ROLLOUT_TRAFFIC = {"sources_sha256_16": "6a939771f200f0c9",
 
 
 def rollout_kernel_name(variant):
-    """The rollout kernel a launch variant runs (8 and up: two wind samples per thread)."""
-    return "rollout_pair_kernel" if variant is not None and variant >= 8 else "rollout_kernel"
+    """The rollout kernel a launch variant runs (8-12: two wind samples per thread; 13-15 the
+    one-sample kernel on 16-particle tiles)."""
+    return "rollout_pair_kernel" if variant is not None and 8 <= variant < 13 else "rollout_kernel"
 
 
 def rollout_sources_digest():

@@ -21,8 +21,10 @@ namespace {
 // register budget per thread is 65536 / (cap * blocks); the autotuner picks
 // among the variants whose cap fits the block (32 * N threads).  OwnWind is
 // wind mode 1 (per-particle fields) and Rolling the rolling window, each a
-// kernel of its own so that the plain problem keeps its register allocation.
-template <int kMaxThreads, int kMinBlocks, bool OwnWind, bool Rolling, bool Soft>
+// kernel of its own so that the plain problem keeps its register allocation;
+// Soft the softplus form; TP the particles of a tile (32, or 16: the half tile,
+// a warp holding two aircraft, so that the blocks of a large N are half as big).
+template <int kMaxThreads, int kMinBlocks, bool OwnWind, bool Rolling, bool Soft, int TP = kPB>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const ProblemC P,
                                                        const DynState *__restrict__ dyn,
                                                        const float *__restrict__ u,
@@ -33,10 +35,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) rollout_kernel(const 
 {
     extern __shared__ float spos[];
     const int m = blockIdx.x / nLb;            // wind sample: block-uniform
-    const long long l0 = (long long)(blockIdx.x - m * nLb) * kPB;
-    const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
-    const TileResult r = rollout_tile_mode<OwnWind, Rolling, Soft>(P, dyn, u, W + (size_t)m * P.H * P.P, L, l0,
-                                                                   i, j, m, J, spos, 0, blockDim.x);
+    const long long l0 = (long long)(blockIdx.x - m * nLb) * TP;
+    const int i = threadIdx.x / TP, j = threadIdx.x % TP;
+    const TileResult r = rollout_tile_mode<OwnWind, Rolling, Soft, true, TP>(
+        P, dyn, u, W + (size_t)m * P.H * P.P, L, l0, i, j, m, J, spos, 0, blockDim.x);
     store_tile(r, P.N, L, l0 + j, i, j, m, cost_ms, cost_ms_soft, live);
 }
 
@@ -68,6 +70,17 @@ struct Variant {
 constexpr Variant kVariants[] = {{256, 4}, {256, 3}, {512, 2}, {512, 1}, {1024, 1},
                                  {256, 2}, {384, 2}, {768, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+// the half tile (16 particles, block 16 N): shared wind field, no rolling window,
+// even N (full warps); registers per thread 85, 85, 64
+constexpr Variant kHalfVariants[] = {{768, 1}, {384, 2}, {512, 2}};
+constexpr int kNumHalfVariants = sizeof(kHalfVariants) / sizeof(kHalfVariants[0]);
+static_assert(kHalfVariantBase + kNumHalfVariants <= kMaxRolloutVariants, "variant table");
+
+static bool half_valid(const ProblemC &P, int v)
+{
+    return P.wind_mode == 0 && !P.rolling && (P.N & 1) == 0 && v >= 0 && v < kNumHalfVariants &&
+           kHalfVariants[v].max_threads >= P.N * 16;
+}
 
 int rollout_variants(const ProblemC &P, int *out)
 {
@@ -77,7 +90,43 @@ int rollout_variants(const ProblemC &P, int *out)
     int pv[kMaxRolloutVariants];
     const int np = rollout_pair_variants(P, pv);
     for (int c = 0; c < np; ++c) out[n++] = kPairVariantBase + pv[c];
+    for (int v = 0; v < kNumHalfVariants; ++v)
+        if (half_valid(P, v)) out[n++] = kHalfVariantBase + v;
     return n;
+}
+
+// The one-sample kernel on half tiles (variant kHalfVariantBase + v).
+static cudaError_t launch_rollout_half(const ProblemC &P, const DynState *dyn, const float *u, const float4 *W4,
+                                       int64_t L, int J, float *cost_ms, float *cost_ms_soft,
+                                       unsigned long long *live, cudaStream_t st, int v)
+{
+    constexpr int TP = 16;
+    const long long nLb = (L + TP - 1) / TP;
+    const unsigned grid = (unsigned)(nLb * P.M);
+    const int block = P.N * TP;
+    const size_t smem = (size_t)tile_smem_words(P.N, 0, TP) * sizeof(float);
+#define TMA_HALF_K(T, B, F)                                                                      \
+    do {                                                                                         \
+        if (smem > 48 * 1024)                                                                    \
+            cudaFuncSetAttribute(rollout_kernel<T, B, false, false, F, TP>,                      \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+        rollout_kernel<T, B, false, false, F, TP><<<grid, block, smem, st>>>(                    \
+            P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live);                         \
+    } while (0)
+#define TMA_HALF(T, B)                                                                           \
+    do {                                                                                         \
+        if (cost_ms_soft) TMA_HALF_K(T, B, true);                                                \
+        else TMA_HALF_K(T, B, false);                                                            \
+    } while (0)
+    switch (v) {
+    case 0: TMA_HALF(768, 1); break;
+    case 1: TMA_HALF(384, 2); break;
+    default: TMA_HALF(512, 2); break;
+    }
+#undef TMA_HALF
+#undef TMA_HALF_K
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
@@ -85,7 +134,12 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
                            unsigned long long *live, cudaStream_t st, int variant)
 {
     if (L <= 0) return cudaSuccess;
-    if (variant >= kPairVariantBase) {
+    if (variant >= kHalfVariantBase) {
+        if (half_valid(P, variant - kHalfVariantBase))
+            return launch_rollout_half(P, dyn, u, reinterpret_cast<const float4 *>(W), L, J, cost_ms,
+                                       cost_ms_soft, live, st, variant - kHalfVariantBase);
+        variant = -1;                  // not valid for this problem: the one-sample kernel
+    } else if (variant >= kPairVariantBase) {
         int pv[kMaxRolloutVariants];
         const int np = rollout_pair_variants(P, pv);
         for (int c = 0; c < np; ++c)

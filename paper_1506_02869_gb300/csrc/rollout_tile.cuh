@@ -438,10 +438,10 @@ __device__ __forceinline__ float total_objective(const ProblemC &P, const Aircra
 // [2][N][32], and in wind mode 1 the particles' wind state [2][16][32].
 __host__ __device__ constexpr int tile_pair_slots(int N) { return (N - 1) / 2 + 1; }
 __host__ __device__ constexpr int tile_pos_rows(int N) { return 2 * N + 4; }
-__host__ __device__ constexpr int tile_smem_words(int N, int wind_mode)
+// tp: particles of the tile (32, or 16 for the half tile)
+__host__ __device__ constexpr int tile_smem_words(int N, int wind_mode, int tp = kTileParticles)
 {
-    return (4 * 2 * tile_pos_rows(N) + N + 2 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) *
-           kTileParticles;
+    return (4 * 2 * tile_pos_rows(N) + N + 2 * N + 2 * N * tile_pair_slots(N) + (wind_mode == 1 ? 32 : 0)) * tp;
 }
 
 // Simulates aircraft i (this warp) of particles l0..l0+31 (lane j) under the
@@ -478,7 +478,11 @@ struct TileResult {
 // space reloads them at every use) and the turbulence draws take the
 // precomputed round keys.  The batched kernel holds P in shared memory and
 // keeps the reference, its register budget is full.
-template <bool OwnWind, bool Rolling, bool Soft, bool ParamP = true>
+// TP: particles of the tile, 32 (one warp per aircraft) or 16 (the half tile:
+// a warp holds aircraft 2w and 2w + 1, lanes 0-15 and 16-31; every warp of the
+// block is full when N is even), so that two blocks of a large N share an SM.
+// The shared buffers are laid out the same way with TP particles per row.
+template <bool OwnWind, bool Rolling, bool Soft, bool ParamP = true, int TP = kTileParticles>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
                                                         const float *__restrict__ u,
                                                         const float4 *__restrict__ Wm, long long L,
@@ -486,6 +490,8 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
                                                         float *spos, int bar_id,
                                                         int bar_count)
 {
+    static_assert(TP == kTileParticles || (TP == 16 && !OwnWind), "half tiles: shared wind field only");
+    constexpr int kPB = TP;     // particles per row of every shared buffer of this tile
     const int N = P.N;
     const long long l = l0 + j;
     const bool exists = l < L;
@@ -521,10 +527,10 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
     unsigned int nlive = 0;
     const int plane = N * kPB;
     const int rows = tile_pos_rows(N);
-    float4 *pos = reinterpret_cast<float4 *>(spos);                          // [2][2N + 4][32]
-    int *vflag = reinterpret_cast<int *>(spos + 8 * rows * kPB);            // [N][32]
-    unsigned *rmark = reinterpret_cast<unsigned *>(vflag + plane);         // [2][N][32]
-    float *recv = reinterpret_cast<float *>(rmark + 2 * plane);           // [2][N][slots][32]
+    float4 *pos = reinterpret_cast<float4 *>(spos);                          // [2][2N + 4][TP]
+    int *vflag = reinterpret_cast<int *>(spos + 8 * rows * kPB);            // [N][TP]
+    unsigned *rmark = reinterpret_cast<unsigned *>(vflag + plane);         // [2][N][TP]
+    float *recv = reinterpret_cast<float *>(rmark + 2 * plane);           // [2][N][slots][TP]
     const int slots = tile_pair_slots(N);
     // ordered before any partner's mark by the step-0 (and step-1) barrier
     vflag[i * kPB + j] = 0;
@@ -663,8 +669,9 @@ __device__ __forceinline__ void store_tile(const TileResult &r, int N, long long
         if (cost_ms_soft) cost_ms_soft[o] = r.cost_soft;
     }
     if (live != nullptr) {
+        // one atomic per warp (a half-tile warp holds two aircraft)
         const unsigned int tot = __reduce_add_sync(0xffffffffu, r.live);
-        if (j == 0 && tot) atomicAdd(live, (unsigned long long)tot);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(live, (unsigned long long)tot);
     }
 }
 

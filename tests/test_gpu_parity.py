@@ -168,39 +168,48 @@ def test_autotuner_choice_is_valid_and_cached(torch, pkg):
         assert not timed2            # the second solver reused the cached choice
 
 
+@pytest.mark.parametrize("sep", [0, 2])
 @pytest.mark.parametrize("n", [5, 12, 20])
-def test_every_launch_variant_computes_the_same(torch, pkg, n):
-    """The launch-bound variants only change the register budget (0-7) or give
-    each thread two wind samples (8-12): forced one by one (as the layout sweep
-    does), they give identical costs; a variant whose block cap is below 32 N
-    threads is refused."""
+def test_every_launch_variant_computes_the_same(torch, pkg, n, sep):
+    """The launch-bound variants only change the register budget (0-7), give
+    each thread two wind samples (8-12) or halve the tile to 16 particles, two
+    aircraft per warp (13-15): forced one by one (as the layout sweep does),
+    they give identical costs, hard and soft forms alike (300 particles: a
+    ragged last tile); a variant whose block does not fit its cap, or a half
+    tile for an odd aircraft count, is refused."""
     base = S.config5(n_scen=1)[0]
     rng = _rng(19 + n)
     ac = S._traffic(rng, n // 2, n - n // 2, ring=45000.0, z_top=9000.0, sep_h=base.sep_h,
                     sep_v=base.sep_v)
-    p = base.copy(N=n, L=300, M=2, H=30, sep_mode=2)
+    p = base.copy(N=n, L=300, M=2, H=30, sep_mode=sep)
     p.aircraft = ac
     u = torch.from_numpy(S.mild_controls(p, p.L, rng)).cuda()
     sol = pkg.Solver(p)
     ref = None
     ran = 0
+    ran_half = 0
     caps = {0: 256, 1: 256, 2: 512, 3: 512, 4: 1024, 5: 256, 6: 384, 7: 768,
-            8: 256, 9: 256, 10: 384, 11: 512, 12: 768}
-    for v in range(13):
+            8: 256, 9: 256, 10: 384, 11: 512, 12: 768, 13: 768, 14: 384, 15: 512}
+    for v in range(16):
         try:
             pkg.tma_set_tuning(sol.h, v)
         except pkg.TmaError:
-            assert 32 * n > caps[v]
+            # the half tiles (13-15: 16 particles, block 16 n) need an even count
+            assert (32 * n > caps[v]) if v < 13 else (16 * n > caps[v] or n % 2 == 1)
             continue
-        c, cs = sol.rollout_cost(u, 1, soft=True)
-        out = (c.cpu().numpy(), cs.cpu().numpy())
+        if v >= 13:
+            ran_half += 1
+        c, cs = sol.rollout_cost(u, 1, soft=sep != 0)
+        out = (c.cpu().numpy(), cs.cpu().numpy() if sep else None, sol.live_steps())
         if ref is None:
             ref = out
         else:
-            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), v
+            assert np.array_equal(out[0], ref[0]), v
+            assert sep == 0 or np.array_equal(out[1], ref[1]), v
+            assert out[2] == ref[2], v
         ran += 1
     sol.close()
-    assert ran >= 2
+    assert ran >= 2 and (ran_half >= 1 or n % 2 == 1)
 
 
 def test_rollout_live_steps_counts_flying_aircraft(torch, pkg):
