@@ -242,7 +242,7 @@ tma_status tma_best_index(tma_solver *s, int64_t *h_best, tma_stream_t stream);
  * valid launch-bound variant -- block-size cap and minimum resident blocks --
  * is timed on the solver's own workload and the fastest kept; the choice is
  * cached per device, aircraft count, problem kind and workload size class).
- * *n_timed is 0 when the choice came from the cache; h_variants/h_ms (up to 16
+ * *n_timed is 0 when the choice came from the cache; h_variants/h_ms (up to 24
  * entries, may be NULL) receive the
  * candidates and their mean time per rollout in ms. */
 tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int32_t *h_variants,

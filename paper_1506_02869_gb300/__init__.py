@@ -375,7 +375,7 @@ def tma_best_index(h, stream=None):
 def tma_get_tuning(h):
     """(chosen rollout variant, {variant: ms per rollout} timed by the autotuner)."""
     v, n = C.c_int32(), C.c_int32()
-    vs, ms = (C.c_int32 * 16)(), (C.c_float * 16)()
+    vs, ms = (C.c_int32 * 24)(), (C.c_float * 24)()
     _check(lib().tma_get_tuning(h, C.byref(v), C.byref(n), vs, ms), "tma_get_tuning")
     return v.value, {vs[k]: ms[k] for k in range(n.value)}
 

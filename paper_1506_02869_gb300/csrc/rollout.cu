@@ -70,16 +70,19 @@ struct Variant {
 constexpr Variant kVariants[] = {{256, 4}, {256, 3}, {512, 2}, {512, 1}, {1024, 1},
                                  {256, 2}, {384, 2}, {768, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-// the half tile (16 particles, block 16 N): shared wind field, no rolling window,
-// even N (full warps); registers per thread 85, 85, 64
+// the smaller tiles (TP particles, block TP N, 32 / TP aircraft per warp):
+// shared wind field, no rolling window, N a multiple of 32 / TP (full warps).
+// Half tiles (16): registers per thread 85, 85, 64; quarter tiles (8): 64, 85.
 constexpr Variant kHalfVariants[] = {{768, 1}, {384, 2}, {512, 2}};
 constexpr int kNumHalfVariants = sizeof(kHalfVariants) / sizeof(kHalfVariants[0]);
-static_assert(kHalfVariantBase + kNumHalfVariants <= kMaxRolloutVariants, "variant table");
+constexpr Variant kQuarterVariants[] = {{512, 2}, {384, 2}};
+constexpr int kNumQuarterVariants = sizeof(kQuarterVariants) / sizeof(kQuarterVariants[0]);
+static_assert(kHalfVariantBase + kNumHalfVariants <= kQuarterVariantBase, "variant table");
+static_assert(kQuarterVariantBase + kNumQuarterVariants <= kMaxRolloutVariants, "variant table");
 
-static bool half_valid(const ProblemC &P, int v)
+static bool small_tile_valid(const ProblemC &P, int tp, int cap)
 {
-    return P.wind_mode == 0 && !P.rolling && (P.N & 1) == 0 && v >= 0 && v < kNumHalfVariants &&
-           kHalfVariants[v].max_threads >= P.N * 16;
+    return P.wind_mode == 0 && !P.rolling && P.N % (32 / tp) == 0 && cap >= P.N * tp;
 }
 
 int rollout_variants(const ProblemC &P, int *out)
@@ -91,42 +94,35 @@ int rollout_variants(const ProblemC &P, int *out)
     const int np = rollout_pair_variants(P, pv);
     for (int c = 0; c < np; ++c) out[n++] = kPairVariantBase + pv[c];
     for (int v = 0; v < kNumHalfVariants; ++v)
-        if (half_valid(P, v)) out[n++] = kHalfVariantBase + v;
+        if (small_tile_valid(P, 16, kHalfVariants[v].max_threads)) out[n++] = kHalfVariantBase + v;
+    for (int v = 0; v < kNumQuarterVariants; ++v)
+        if (small_tile_valid(P, 8, kQuarterVariants[v].max_threads)) out[n++] = kQuarterVariantBase + v;
     return n;
 }
 
-// The one-sample kernel on half tiles (variant kHalfVariantBase + v).
-static cudaError_t launch_rollout_half(const ProblemC &P, const DynState *dyn, const float *u, const float4 *W4,
-                                       int64_t L, int J, float *cost_ms, float *cost_ms_soft,
-                                       unsigned long long *live, cudaStream_t st, int v)
+// The one-sample kernel on tiles of TP < 32 particles with launch bounds (T, B).
+template <int T, int B, int TP>
+static void launch_small_tile(const ProblemC &P, const DynState *dyn, const float *u, const float4 *W4,
+                              int64_t L, int J, float *cost_ms, float *cost_ms_soft,
+                              unsigned long long *live, cudaStream_t st)
 {
-    constexpr int TP = 16;
     const long long nLb = (L + TP - 1) / TP;
     const unsigned grid = (unsigned)(nLb * P.M);
     const int block = P.N * TP;
     const size_t smem = (size_t)tile_smem_words(P.N, 0, TP) * sizeof(float);
-#define TMA_HALF_K(T, B, F)                                                                      \
-    do {                                                                                         \
-        if (smem > 48 * 1024)                                                                    \
-            cudaFuncSetAttribute(rollout_kernel<T, B, false, false, F, TP>,                      \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        rollout_kernel<T, B, false, false, F, TP><<<grid, block, smem, st>>>(                    \
-            P, dyn, u, W4, L, (int)nLb, J, cost_ms, cost_ms_soft, live);                         \
-    } while (0)
-#define TMA_HALF(T, B)                                                                           \
-    do {                                                                                         \
-        if (cost_ms_soft) TMA_HALF_K(T, B, true);                                                \
-        else TMA_HALF_K(T, B, false);                                                            \
-    } while (0)
-    switch (v) {
-    case 0: TMA_HALF(768, 1); break;
-    case 1: TMA_HALF(384, 2); break;
-    default: TMA_HALF(512, 2); break;
+    if (cost_ms_soft) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(rollout_kernel<T, B, false, false, true, TP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rollout_kernel<T, B, false, false, true, TP><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J,
+                                                                              cost_ms, cost_ms_soft, live);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(rollout_kernel<T, B, false, false, false, TP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rollout_kernel<T, B, false, false, false, TP><<<grid, block, smem, st>>>(P, dyn, u, W4, L, (int)nLb, J,
+                                                                               cost_ms, cost_ms_soft, live);
     }
-#undef TMA_HALF
-#undef TMA_HALF_K
-    count_launch();
-    return cudaGetLastError();
 }
 
 cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *u, const float *W,
@@ -135,9 +131,24 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
 {
     if (L <= 0) return cudaSuccess;
     if (variant >= kHalfVariantBase) {
-        if (half_valid(P, variant - kHalfVariantBase))
-            return launch_rollout_half(P, dyn, u, reinterpret_cast<const float4 *>(W), L, J, cost_ms,
-                                       cost_ms_soft, live, st, variant - kHalfVariantBase);
+        const float4 *W4 = reinterpret_cast<const float4 *>(W);
+        const int hv = variant - kHalfVariantBase, qv = variant - kQuarterVariantBase;
+        bool done = true;
+        if (hv >= 0 && hv < kNumHalfVariants && small_tile_valid(P, 16, kHalfVariants[hv].max_threads)) {
+            if (hv == 0) launch_small_tile<768, 1, 16>(P, dyn, u, W4, L, J, cost_ms, cost_ms_soft, live, st);
+            else if (hv == 1) launch_small_tile<384, 2, 16>(P, dyn, u, W4, L, J, cost_ms, cost_ms_soft, live, st);
+            else launch_small_tile<512, 2, 16>(P, dyn, u, W4, L, J, cost_ms, cost_ms_soft, live, st);
+        } else if (qv >= 0 && qv < kNumQuarterVariants &&
+                   small_tile_valid(P, 8, kQuarterVariants[qv].max_threads)) {
+            if (qv == 0) launch_small_tile<512, 2, 8>(P, dyn, u, W4, L, J, cost_ms, cost_ms_soft, live, st);
+            else launch_small_tile<384, 2, 8>(P, dyn, u, W4, L, J, cost_ms, cost_ms_soft, live, st);
+        } else {
+            done = false;
+        }
+        if (done) {
+            count_launch();
+            return cudaGetLastError();
+        }
         variant = -1;                  // not valid for this problem: the one-sample kernel
     } else if (variant >= kPairVariantBase) {
         int pv[kMaxRolloutVariants];

@@ -478,10 +478,11 @@ struct TileResult {
 // space reloads them at every use) and the turbulence draws take the
 // precomputed round keys.  The batched kernel holds P in shared memory and
 // keeps the reference, its register budget is full.
-// TP: particles of the tile, 32 (one warp per aircraft) or 16 (the half tile:
-// a warp holds aircraft 2w and 2w + 1, lanes 0-15 and 16-31; every warp of the
-// block is full when N is even), so that two blocks of a large N share an SM.
-// The shared buffers are laid out the same way with TP particles per row.
+// TP: particles of the tile, 32 (one warp per aircraft), 16 or 8 (a warp holds
+// 32 / TP consecutive aircraft, TP lanes each; every warp of the block is full
+// when N is a multiple of 32 / TP), so that several blocks of a large N share
+// an SM.  The shared buffers are laid out the same way with TP particles per
+// row.
 template <bool OwnWind, bool Rolling, bool Soft, bool ParamP = true, int TP = kTileParticles>
 __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const DynState *__restrict__ dyn,
                                                         const float *__restrict__ u,
@@ -490,7 +491,8 @@ __device__ __forceinline__ TileResult rollout_tile_mode(const ProblemC &P, const
                                                         float *spos, int bar_id,
                                                         int bar_count)
 {
-    static_assert(TP == kTileParticles || (TP == 16 && !OwnWind), "half tiles: shared wind field only");
+    static_assert(TP == kTileParticles || ((TP == 16 || TP == 8) && !OwnWind),
+                  "smaller tiles: shared wind field only");
     constexpr int kPB = TP;     // particles per row of every shared buffer of this tile
     const int N = P.N;
     const long long l = l0 + j;
@@ -669,7 +671,7 @@ __device__ __forceinline__ void store_tile(const TileResult &r, int N, long long
         if (cost_ms_soft) cost_ms_soft[o] = r.cost_soft;
     }
     if (live != nullptr) {
-        // one atomic per warp (a half-tile warp holds two aircraft)
+        // one atomic per warp (a warp of a smaller tile holds several aircraft)
         const unsigned int tot = __reduce_add_sync(0xffffffffu, r.live);
         if ((threadIdx.x & 31) == 0 && tot) atomicAdd(live, (unsigned long long)tot);
     }

@@ -16,7 +16,8 @@ constexpr int kMaxN = TMA_MAX_AIRCRAFT;
 constexpr int kTileParticles = 32;   // particles per rollout tile (one warp per aircraft)
 constexpr int kPairVariantBase = 8;  // first rollout variant index of the two-sample kernel
 constexpr int kHalfVariantBase = 13; // first rollout variant index of the 16-particle (half) tile
-constexpr int kMaxRolloutVariants = 16;
+constexpr int kQuarterVariantBase = 16; // first rollout variant index of the 8-particle tile
+constexpr int kMaxRolloutVariants = 24;
 
 // Per-aircraft constants in FP32 (derived on the host in FP64).
 struct AircraftC {
@@ -117,8 +118,9 @@ cudaError_t launch_rollout(const ProblemC &P, const DynState *dyn, const float *
                            unsigned long long *live, cudaStream_t st, int variant);
 // Launch-bound variants of the rollout kernel valid for the problem (indices
 // into the variant table: 0-7 the one-sample kernel, kPairVariantBase + v the
-// two-sample kernel of rollout_pair.cu, kHalfVariantBase + v the one-sample
-// kernel on 16-particle tiles); returns their number (at least 1, at most 16).
+// two-sample kernel of rollout_pair.cu, kHalfVariantBase + v and
+// kQuarterVariantBase + v the one-sample kernel on 16- and 8-particle tiles);
+// returns their number (at least 1, at most kMaxRolloutVariants).
 int rollout_variants(const ProblemC &P, int *out);
 // The two-sample kernel (shared wind field, no rolling window, M >= 2): its
 // variants valid for the problem (0-based) and its launcher.

@@ -172,11 +172,11 @@ def test_autotuner_choice_is_valid_and_cached(torch, pkg):
 @pytest.mark.parametrize("n", [5, 12, 20])
 def test_every_launch_variant_computes_the_same(torch, pkg, n, sep):
     """The launch-bound variants only change the register budget (0-7), give
-    each thread two wind samples (8-12) or halve the tile to 16 particles, two
-    aircraft per warp (13-15): forced one by one (as the layout sweep does),
-    they give identical costs, hard and soft forms alike (300 particles: a
-    ragged last tile); a variant whose block does not fit its cap, or a half
-    tile for an odd aircraft count, is refused."""
+    each thread two wind samples (8-12) or shrink the tile to 16 or 8
+    particles, two or four aircraft per warp (13-15, 16-17): forced one by one
+    (as the layout sweep does), they give identical costs, hard and soft forms
+    alike (300 particles: a ragged last tile); a variant whose block does not
+    fit its cap, or a smaller tile whose warps would not be full, is refused."""
     base = S.config5(n_scen=1)[0]
     rng = _rng(19 + n)
     ac = S._traffic(rng, n // 2, n - n // 2, ring=45000.0, z_top=9000.0, sep_h=base.sep_h,
@@ -189,13 +189,14 @@ def test_every_launch_variant_computes_the_same(torch, pkg, n, sep):
     ran = 0
     ran_half = 0
     caps = {0: 256, 1: 256, 2: 512, 3: 512, 4: 1024, 5: 256, 6: 384, 7: 768,
-            8: 256, 9: 256, 10: 384, 11: 512, 12: 768, 13: 768, 14: 384, 15: 512}
-    for v in range(16):
+            8: 256, 9: 256, 10: 384, 11: 512, 12: 768, 13: 768, 14: 384, 15: 512, 16: 512, 17: 384}
+    for v in range(18):
+        tp = 32 if v < 13 else (16 if v < 16 else 8)     # particles per tile
         try:
             pkg.tma_set_tuning(sol.h, v)
         except pkg.TmaError:
-            # the half tiles (13-15: 16 particles, block 16 n) need an even count
-            assert (32 * n > caps[v]) if v < 13 else (16 * n > caps[v] or n % 2 == 1)
+            # smaller tiles (13-15: 16 particles, 16-17: 8) need full warps: 32 / tp | n
+            assert tp * n > caps[v] or n % (32 // tp) != 0
             continue
         if v >= 13:
             ran_half += 1
