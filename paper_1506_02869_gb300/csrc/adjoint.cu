@@ -448,9 +448,12 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
                     for (int d = 0; d < n_pairs; ++d) {
                         i2 = (i2 + 1 == N) ? 0 : i2 + 1;
                         float2 ps = make_float2(0.0f, 0.0f);
-                        if (act) {
-                            const float4 q = buf[i2 * kPB + j];
-                            const float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
+                        const float4 q = buf[i2 * kPB + j];
+                        const float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
+                        // beyond reach the penalty and its weight are below e^-30: 0,
+                        // as in the rollout; only a warp with a lane in reach evaluates
+                        const bool near = act && fmaf(dx, dx, dy * dy) < P.sp_far_h2 && fabsf(dz) < P.sp_far_v;
+                        if (__any_sync(0xffffffffu, near) && near) {
                             ps = pair_penalty(P, dx, dy, dz);
                             soft += ps.x;
                             if (ps.y != 0.0f) pair_grad(P, sep_c * ps.y, dx, dy, dz, sx, sy, sz);
@@ -462,6 +465,7 @@ rollout_grad_kernel(const ProblemC P, const DynState *__restrict__ dyn, const fl
                         if (i2 == i) continue;
                         const float4 q = buf[i2 * kPB + j];
                         const float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
+                        if (fmaf(dx, dx, dy * dy) >= P.sp_far_h2 || fabsf(dz) >= P.sp_far_v) continue;   // out of reach
                         const float2 ps = pair_penalty(P, dx, dy, dz);
                         soft += ps.x;
                         if (ps.y != 0.0f) pair_grad(P, sep_c * ps.y, dx, dy, dz, sx, sy, sz);

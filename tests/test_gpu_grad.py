@@ -8,7 +8,7 @@ for every particle whose threshold decisions are not within 1e-5 (relative) of
 their thresholds in the oracle.  (A gradient also has kinks -- |.|, the
 wrapped angle, the min of the separation gap -- where FP32 and FP64 could take
 opposite sides; on these seeded cases no particle comes near the bar: the
-largest error is 5.7e-5, so no allowance for them is made.)"""
+largest error is 1.8e-4, so no allowance for them is made.)"""
 import numpy as np
 import pytest
 
