@@ -118,16 +118,15 @@ __device__ __forceinline__ void wind_grad(const ProblemC &P, const float4 *__res
 __device__ __forceinline__ float popdense_grad(const ProblemC &P, float x, float y, float &gx, float &gy)
 {
     gx = gy = 0.0f;
-    if (P.popdense == nullptr) return 0.0f;
+    if (P.popcell == nullptr) return 0.0f;
     if (!(x >= P.pop_lo[0] && x <= P.pop_hi[0] && y >= P.pop_lo[1] && y <= P.pop_hi[1]))
         return 0.0f;
     const float f0 = (x - P.pop_lo[0]) * P.pop_inv_h[0];
     const float f1 = (y - P.pop_lo[1]) * P.pop_inv_h[1];
     const int i0 = min((int)f0, P.pop_n[0] - 2), i1 = min((int)f1, P.pop_n[1] - 2);
     const float t0 = f0 - (float)i0, t1 = f1 - (float)i1;
-    const float *g = P.popdense + (size_t)i0 * P.pop_n[1] + i1;
-    const float g00 = __ldg(g), g01 = __ldg(g + 1);
-    const float g10 = __ldg(g + P.pop_n[1]), g11 = __ldg(g + P.pop_n[1] + 1);
+    const float4 g = __ldg(P.popcell + (size_t)i0 * (P.pop_n[1] - 1) + i1);
+    const float g00 = g.x, g01 = g.y, g10 = g.z, g11 = g.w;
     gx = fmaf(t1, (g11 - g01) - (g10 - g00), g10 - g00) * P.pop_inv_h[0];
     gy = fmaf(t0, (g11 - g10) - (g01 - g00), g01 - g00) * P.pop_inv_h[1];
     const float a = fmaf(t1, g01 - g00, g00), b = fmaf(t1, g11 - g10, g10);

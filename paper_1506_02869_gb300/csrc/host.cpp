@@ -197,8 +197,25 @@ static tma_status validate(const tma_problem *p, const tma_aircraft *ac)
     return TMA_OK;
 }
 
+// The population density's cells with their four corner values, the layout
+// of ProblemC::popcell: cell (a, b) of the row-major [n0][n1] grid g holds
+// g[a][b], g[a][b+1], g[a+1][b], g[a+1][b+1] (FP32).
+static std::vector<float> pack_popcells(const double *g, int n0, int n1)
+{
+    std::vector<float> c((size_t)(n0 - 1) * (n1 - 1) * 4);
+    for (int a = 0; a + 1 < n0; ++a)
+        for (int b = 0; b + 1 < n1; ++b) {
+            float *o = &c[((size_t)a * (n1 - 1) + b) * 4];
+            o[0] = (float)g[(size_t)a * n1 + b];
+            o[1] = (float)g[(size_t)a * n1 + b + 1];
+            o[2] = (float)g[(size_t)(a + 1) * n1 + b];
+            o[3] = (float)g[(size_t)(a + 1) * n1 + b + 1];
+        }
+    return c;
+}
+
 static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraft,
-                               const float *d_popdense)
+                               const float *d_popcell)
 {
     ProblemC P;
     std::memset(&P, 0, sizeof P);
@@ -266,7 +283,7 @@ static ProblemC derive_problem(const tma_problem &p, const tma_aircraft *aircraf
     for (int j = 0; j < 3; ++j) P.a_arr[j] = (float)p.alpha_arr[j];
     P.w_noise = (float)p.w_noise;
     P.Ac_inv = (float)(p.A_c > 0 ? 1.0 / p.A_c : 0.0);
-    P.popdense = d_popdense;
+    P.popcell = reinterpret_cast<const float4 *>(d_popcell);
     for (int d = 0; d < 2; ++d) {
         P.pop_n[d] = p.pop_n[d];
         P.pop_lo[d] = (float)p.pop_lo[d];
@@ -550,9 +567,9 @@ tma_status tma_create(const tma_problem *prob, const tma_aircraft *aircraft, tma
             return e == cudaErrorMemoryAllocation ? TMA_ERR_OOM : cuda_fail(e);
         };
         cudaError_t e;
-        // popdense to device (FP32)
+        // population density to device: FP32 cells with their four corners
         if (!s->popdense_host.empty()) {
-            std::vector<float> pf(s->popdense_host.begin(), s->popdense_host.end());
+            const std::vector<float> pf = pack_popcells(s->popdense_host.data(), p.pop_n[0], p.pop_n[1]);
             if ((e = alloc(&s->d_popdense, pf.size() * 4))) return fail(e);
             if ((e = cudaMemcpy(s->d_popdense, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice)))
                 return fail(e);
@@ -1831,7 +1848,7 @@ tma_status tma_batch_create(const tma_problem *probs, const tma_aircraft *const 
             b->aircraft.emplace_back(aircraft[s], aircraft[s] + p.N);
             float *dpop = nullptr;
             if (p.pop_n[0] >= 2) {
-                std::vector<float> pf(p.popdense, p.popdense + (size_t)p.pop_n[0] * p.pop_n[1]);
+                const std::vector<float> pf = pack_popcells(p.popdense, p.pop_n[0], p.pop_n[1]);
                 if ((e = alloc(&dpop, pf.size() * 4))) return fail(e);
                 b->d_pops.push_back(dpop);
                 if ((e = cudaMemcpy(dpop, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice))) return fail(e);

@@ -53,7 +53,10 @@ struct ProblemC {
     float w_noise, Ac_inv;
     int pop_n[2];
     float pop_lo[2], pop_hi[2], pop_inv_h[2];
-    const float *popdense; // device [pop_n0][pop_n1] or nullptr
+    // device, or nullptr: the density's cells [pop_n0 - 1][pop_n1 - 1], each
+    // holding its four corner values (g[a][b], g[a][b+1], g[a+1][b], g[a+1][b+1])
+    // so that one 16-byte load gives a bilinear lookup
+    const float4 *popcell;
     float P_runway, P_beta, P_chi, P_vs, beta_f;
     int rolling;           // 1: rolling window (t_enter, finished aircraft)
     int wind_mode;         // 1: a wind field per (particle, sample) on the box corners
@@ -242,7 +245,7 @@ struct tma_solver {
     float *d_cbar = nullptr, *d_cbar_soft = nullptr;
     double *d_wtilde = nullptr;
     int32_t *d_anc = nullptr;
-    float *d_popdense = nullptr;
+    float *d_popdense = nullptr;          // population density cells (ProblemC::popcell), or nullptr
     void *d_work = nullptr;             // LSE workspace, then the resampling's at lse_work_bytes
     size_t work_bytes = 0, lse_work_bytes = 0;
     int64_t *d_best = nullptr;
