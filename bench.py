@@ -108,10 +108,10 @@ def flops_per_unit_tally(p):
 
 # DRAM bytes (read + write) of one full-size rollout launch per workload and
 # rollout kernel, from a one-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch: the first of a solve, on the uniform
-# initial particles); valid only for the kernel sources they were taken on.
-ROLLOUT_TRAFFIC = {"sources_sha256_16": "48e9ccfb6df0436a",
-                   "bytes_per_launch": {"c3:rollout_kernel": 29634564608 + 3243880192}}
+# dram__bytes_write.sum of one launch late in a solve: iteration 20 of 30);
+# valid only for the kernel sources they were taken on.
+ROLLOUT_TRAFFIC = {"sources_sha256_16": "817f23a322d9a32f",
+                   "bytes_per_launch": {"c3:rollout_kernel": 45993266688 + 3255089920}}
 
 
 def rollout_kernel_name(variant):

@@ -458,9 +458,11 @@ tma_status tma_batch_live_steps(tma_batch *b, uint64_t *h_live, tma_stream_t str
 
 /* Annealed log-weights and their FP64 normalisation per segment (Sec. 3.6,
  * schedule of Sec. 5.1): l_j = -kappa * (double)cbar_j, lmax = max over finite
- * l_j, d_wtilde[s][j] = exp(l_j - lmax) (0 for +inf cost), d_lmax[s], d_wsum[s]
- * = sum_j wtilde.  A segment with no finite cost gets lmax = -inf, wtilde = 0.
- * d_lmax / d_wsum may be NULL.  Scratch: d_work of tma_lse_workspace() bytes. */
+ * l_j, d_wtilde[s][j] = exp(l_j - lmax) = exp(kappa (cmin - cbar_j)) (0 for
+ * +inf cost; relative error below 1e-15 against the exact value, evaluated in
+ * integer fixed point), d_lmax[s], d_wsum[s] = sum_j wtilde.  A segment with
+ * no finite cost gets lmax = -inf, wtilde = 0.  d_lmax / d_wsum may be NULL.
+ * Scratch: d_work of tma_lse_workspace() bytes. */
 size_t tma_lse_workspace(int32_t nseg, int64_t L);
 tma_status tma_lse(const float *d_cbar, int32_t nseg, int64_t L, double kappa, double *d_wtilde,
                    double *d_lmax, double *d_wsum, void *d_work, size_t work_bytes,

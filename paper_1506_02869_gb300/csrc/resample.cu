@@ -5,10 +5,11 @@
 // of kChunk particles; one 256-thread block handles one (chunk, segment).
 //
 //   LSE:      (1) chunk minima of the finite costs; (2) every block reduces its
-//             segment's minima to lmax = -kappa * min c (exact: multiplying by
-//             kappa > 0 is monotone), writes wtilde = exp(-kappa c - lmax) in
-//             FP64 (table-driven exponential) and, when asked, a chunk partial
-//             sum; (3) the partial sums are added in chunk order into wsum.
+//             segment's minima to cmin (lmax = -kappa cmin: multiplying by
+//             kappa > 0 is monotone), writes wtilde = exp(kappa (cmin - c)) as
+//             FP64 values (table-driven exponential in integer fixed point, no
+//             FP64 arithmetic) and, when asked, a chunk partial sum; (3) the
+//             partial sums are added in chunk order into wsum.
 //   Resample: (1) chunk sums of q = floor(wtilde 2^40) (uint64, exact), by
 //             their own pass or by the LSE pass that writes wtilde;
 //             (2) every block forms its chunk's inclusive prefix S_j, and for
@@ -111,35 +112,86 @@ __global__ void __launch_bounds__(kThreads) lse_chunk_min(const float *__restric
     if (threadIdx.x == 0) cmin[(size_t)s * nchunk + c] = mn;
 }
 
-// exp(x) for x = kappa (cmin - c) <= 0 in FP64, by the table-driven method of
-// Tang (ACM TOMS 15(2), 1989) with 256 table entries: k = rint(x 256 / ln 2),
-// x = k ln2/256 + r with |r| <= ln2/512 (plus a sliver: k comes from the FP32
-// copy xf of x), exp(x) = 2^(k >> 8) 2^((k & 255)/256) exp(r) and
-// exp(r) = 1 + r + r^2 (1/2 + r/6 + r^2/24) + O(r^5 / 120 < 4e-17).  The
-// reduction is one fused multiply-add with ln2/256 rounded to FP64 (kExpL1; the
-// tail kExpL2 < 1e-19 left out moves r by k kExpL2 < 2.5e-14 over the range,
-// k < 2.8e5); the small term r^2 (1/2 + r/6 + r^2/24) < 1e-6 is formed in FP32
-// (absolute error below 1e-13).  Relative error of the result: about 2e-13.
-// FP64 carries x, r and the result; the FP64 instructions per call are about
-// half of a general-purpose exp's.  tab: 2^(j/256) (kExp2Frac), staged in
-// shared memory.
-__device__ __forceinline__ double exp_nonpos(double x, float xf, const double *tab)
+// The normalisation's exponential w = exp(x), x = kappa (cmin - c) <= 0, with
+// no FP64 instruction (GB300 issues FP64 at a small fraction of its FP32 and
+// integer rate): the table-driven method of Tang (ACM TOMS 15(2), 1989) with
+// 256 entries, carried out in 64-bit integer fixed point.
+//   x:  cmin - c = dh + dl exactly (FP32 two-sum), kappa = K 2^eK with the
+//       53-bit integer K, so kappa dh and kappa dl are integer products below
+//       2^77, taken to the scale 2^53 by a shift (truncated, error below 2^-52).
+//   k = rint(x 256 / ln 2) from the FP32 copy xf of x; r = x - k ln2/256 at the
+//       scale 2^53 with ln2/256 = (kExpC1 + kExpC2 / 2^32) 2^-53 (error below
+//       2^-52), |r| < 1.5e-3.
+//   exp(r) = 1 + r + r^2/2 + (r^3/6 + r^4/24) + O(r^5/120 < 7e-17): r^2/2 from
+//       a 64 x 64-bit product at the scale 2^62, the last bracket (< 5e-10) in
+//       FP32 (absolute error below 2e-16).
+//   y = 2^((k & 255)/256) exp(r) as the high half of the 128-bit product of
+//       the table entry (scale 2^63) and exp(r) (scale 2^62), rounded to 53
+//       bits, times 2^(k >> 8) in the exponent field; results below the
+//       smallest normal double through one FP64 multiply by 2^-64 (rare).
+// Relative error below 1e-15.  x = 0 gives exactly 1.
+struct KappaFix {
+    unsigned long long K;  // 53-bit significand of kappa (kappa > 0 finite)
+    int e;                 // kappa = K 2^e
+};
+
+__device__ __forceinline__ KappaFix kappa_fix(double kappa)
 {
-    if (!(xf > -746.0f)) return 0.0;               // exp(x) below half the smallest subnormal (and -inf)
-    const int k = __float2int_rn(xf * 369.329794f); // 256 / ln 2
-    const double kd = (double)k;
-    const double r = fma(-kd, kExpL1, x);
-    const float rf = __double2float_rn(r);
-    const float small = rf * rf * fmaf(fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f), rf, 0.5f);
-    const double p = r + (double)small;            // exp(r) - 1
-    const double t = tab[k & 255];
-    const double y = fma(t, p, t);                  // in [0.99, 2)
-    // times 2^m, m = floor(k / 256) in [-1075, 0]: into the exponent field, with
-    // a final scaling by 2^-64 when the result is subnormal
-    const int m = k >> 8;
-    if (m >= -1000)
-        return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
-    return __longlong_as_double(__double_as_longlong(y) + ((long long)(m + 64) << 52)) * 0x1p-64;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(kappa);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    KappaFix f;
+    f.K = ex ? ((u & ((1ull << 52) - 1)) | (1ull << 52)) : (u & ((1ull << 52) - 1));
+    f.e = (ex ? ex : 1) - 1075;
+    return f;
+}
+
+// |d| kappa at the scale 2^53, truncated, for a finite FP32 d with |d kappa| < 2^10
+__device__ __forceinline__ long long kappa_times(float d, const KappaFix &kf)
+{
+    const uint32_t u = __float_as_uint(d);
+    const int E = (int)((u >> 23) & 0xff);
+    if (E == 0) return 0;                                  // zero (subnormals are flushed)
+    const uint32_t M = (u & 0x7fffffu) | 0x800000u;        // |d| = M 2^(E - 150)
+    const unsigned long long plo = (unsigned long long)M * (uint32_t)kf.K;
+    const unsigned long long phi = (unsigned long long)M * (uint32_t)(kf.K >> 32);
+    const unsigned long long lo = plo + (phi << 32);
+    const unsigned long long hi = (phi >> 32) + (lo < plo ? 1ull : 0ull);   // M K = hi 2^64 + lo
+    // |d| kappa 2^53 = M K 2^(E - 150 + e + 53): a right shift by sh >= 14
+    // whenever the result is below 2^63
+    const int sh = 150 - 53 - E - kf.e;
+    if (sh >= 128) return 0;
+    if (sh >= 64) return (long long)(hi >> (sh - 64));
+    if (sh <= 0) return 0x7fffffffffffffffLL;              // out of range (not reached)
+    return (long long)((lo >> sh) | (hi << (64 - sh)));
+}
+
+__device__ __forceinline__ double exp_fixed(float cmin, float c, float xf, const KappaFix &kf,
+                                            const unsigned long long *tab)
+{
+    if (!(xf > -746.0f)) return 0.0;                       // below half the smallest subnormal
+    // cmin - c = dh + dl exactly
+    const float dh = cmin - c;
+    const float bb = dh - cmin;
+    const float dl = (cmin - (dh - bb)) + (-c - bb);
+    const long long ah = kappa_times(dh, kf), al = kappa_times(dl, kf);
+    const long long x53 = (dh < 0.0f ? -ah : ah) + (dl < 0.0f ? -al : al);
+    const int k = __float2int_rn(xf * 369.329794f);        // 256 / ln 2
+    const long long r53 = x53 - (long long)k * kExpC1 - (((long long)k * kExpC2) >> 32);
+    const long long r62 = r53 * 512;
+    const unsigned long long ar = (unsigned long long)(r62 < 0 ? -r62 : r62);
+    const long long s62 = (long long)(__umul64hi(ar, ar) << 1);           // r^2 / 2
+    const float rf = (float)(int)(r53 >> 13) * 0x1p-40f;
+    const float t = rf * rf * rf * fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f);  // r^3/6 + r^4/24
+    const long long t62 = (long long)__float2int_rn(t * 0x1p60f) * 4;
+    const unsigned long long e62 = (unsigned long long)((1LL << 62) + r62 + s62 + t62);
+    const unsigned long long y61 = __umul64hi(tab[k & 255], e62);         // y 2^61, y in (0.99, 2.01)
+    const int p = 63 - __clzll((long long)y61);                           // 60, 61 or 62
+    const int shm = p - 52;
+    const unsigned long long m = (y61 + (1ull << (shm - 1))) >> shm;      // in [2^52, 2^53]
+    const int E = 1023 + (k >> 8) + (p - 61);
+    if (E >= 1) return __longlong_as_double((long long)(((unsigned long long)(E - 1) << 52) + m));
+    if (E < -60) return 0.0;
+    return __longlong_as_double((long long)(((unsigned long long)(E + 63) << 52) + m)) * 0x1p-64;
 }
 
 // Writes wtilde; csum (chunk sums of wtilde, fixed order) and cq (chunk sums
@@ -153,15 +205,15 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
 {
     __shared__ float shf[32];
     __shared__ unsigned long long shq[32];
-    __shared__ double tab[256];
+    __shared__ unsigned long long tab[256];
     const int s = blockIdx.y, c = blockIdx.x;
-    for (int j = threadIdx.x; j < 256; j += kThreads) tab[j] = kExp2Frac[j];
+    for (int j = threadIdx.x; j < 256; j += kThreads) tab[j] = kExp2Frac63[j];
     float mn = __int_as_float(0x7f800000);
     for (int j = threadIdx.x; j < nchunk; j += kThreads) mn = fminf(mn, cmin[(size_t)s * nchunk + j]);
     mn = block_reduce(mn, MinOp(), shf, __int_as_float(0x7f800000));   // its barriers also cover tab
     const bool any = !isinf(mn);
-    const double lmax = -kappa * (double)mn;
     const float kf = (float)kappa;
+    const KappaFix kfix = kappa_fix(kappa);
     const float *row = cbar + (size_t)s * L;
     double *out = wtilde + (size_t)s * L;
     const long long base = (long long)c * kChunk;
@@ -174,9 +226,9 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
         if (idx < L) {
             const float v = __ldg(row + idx);
             double w = 0.0;
-            // -kappa c - lmax = kappa (cmin - c) <= 0 (0 at the minimum: both
-            // products rounded alike); its FP32 copy picks the table entry
-            if (any && !isinf(v) && !isnan(v)) w = exp_nonpos(-kappa * (double)v - lmax, kf * (mn - v), tab);
+            // -kappa c - lmax = kappa (cmin - c) <= 0 (exactly 0 at the
+            // minimum); its FP32 copy picks the table entry
+            if (any && !isinf(v) && !isnan(v)) w = exp_fixed(mn, v, kf * (mn - v), kfix, tab);
             out[idx] = w;
             if (want_sum) acc += w;
             qacc += qfix(w);

@@ -244,6 +244,23 @@ def test_lse_matches_oracle(torch, pkg, nseg, L, kappa):
     assert np.allclose(ws, rws, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("kappa", [0.37, 11.0, 708.0])
+def test_lse_weights_are_the_integer_exponential(torch, pkg, kappa):
+    """Every weight the kernel writes is, bit for bit, the integer fixed-point
+    exponential its source documents (emulated in tests/test_kernel_constants.py,
+    whose error bound is checked against 60-digit decimals)."""
+    from test_kernel_constants import exp_fixed
+    rng = _rng(int(kappa * 100))
+    c = S.random_cbar(2, 4099, rng, frac_inf=0.1, scale=40.0 / kappa)
+    wt, _, _ = pkg.lse(torch.from_numpy(c).cuda(), kappa)
+    wt = wt.cpu().numpy()
+    for s in range(2):
+        cmin = np.float32(np.min(c[s][np.isfinite(c[s])]))
+        for j in range(0, 4099, 7):
+            want = exp_fixed(cmin, c[s, j], kappa) if np.isfinite(c[s, j]) else 0.0
+            assert wt[s, j] == want, (s, j, c[s, j], wt[s, j], want)
+
+
 # ------------------------------------------------------------- resampling
 
 @pytest.mark.parametrize("nseg,L", [(8, 65536), (24, 262144), (1, 1), (3, 5), (2, 2049), (4, 6144),
