@@ -152,22 +152,22 @@ __device__ __forceinline__ long long kappa_times(float d, const KappaFix &kf)
     const int E = (int)((u >> 23) & 0xff);
     if (E == 0) return 0;                                  // zero (subnormals are flushed)
     const uint32_t M = (u & 0x7fffffu) | 0x800000u;        // |d| = M 2^(E - 150)
-    const unsigned long long plo = (unsigned long long)M * (uint32_t)kf.K;
-    const unsigned long long phi = (unsigned long long)M * (uint32_t)(kf.K >> 32);
-    const unsigned long long lo = plo + (phi << 32);
-    const unsigned long long hi = (phi >> 32) + (lo < plo ? 1ull : 0ull);   // M K = hi 2^64 + lo
-    // |d| kappa 2^53 = M K 2^(E - 150 + e + 53): a right shift by sh >= 14
-    // whenever the result is below 2^63
+    // |d| kappa 2^53 = M K 2^(E - 150 + e + 53) = floor(M K / 2^sh); M K >= 2^75
+    // and a result below 746 2^53 < 2^62.6 give sh >= 13; with K = Kh 2^21 + Kl,
+    // floor(M K / 2^13) = M Kh 2^8 + floor(M Kl / 2^13), below 2^64 as M K < 2^77
     const int sh = 150 - 53 - E - kf.e;
-    if (sh >= 128) return 0;
-    if (sh >= 64) return (long long)(hi >> (sh - 64));
-    if (sh <= 0) return 0x7fffffffffffffffLL;              // out of range (not reached)
-    return (long long)((lo >> sh) | (hi << (64 - sh)));
+    if (sh < 13) return 0x7fffffffffffffffLL;              // out of range (not reached)
+    if (sh >= 77) return 0;
+    const unsigned long long p13 = (((unsigned long long)M * (uint32_t)(kf.K >> 21)) << 8) +
+                                   (((unsigned long long)M * (uint32_t)(kf.K & 0x1fffffu)) >> 13);
+    return (long long)(p13 >> (sh - 13));
 }
 
+// Also gives q = floor(w 2^40), the resampling's fixed-point weight (qfix(w)).
 __device__ __forceinline__ double exp_fixed(float cmin, float c, float xf, const KappaFix &kf,
-                                            const unsigned long long *tab)
+                                            const unsigned long long *tab, unsigned long long &q)
 {
+    q = 0ull;
     if (!(xf > -746.0f)) return 0.0;                       // below half the smallest subnormal
     // cmin - c = dh + dl exactly
     const float dh = cmin - c;
@@ -189,6 +189,8 @@ __device__ __forceinline__ double exp_fixed(float cmin, float c, float xf, const
     const int shm = p - 52;
     const unsigned long long m = (y61 + (1ull << (shm - 1))) >> shm;      // in [2^52, 2^53]
     const int E = 1023 + (k >> 8) + (p - 61);
+    // w = m 2^(E - 1075), so floor(w 2^40) = m >> (1035 - E) (w <= 1: E <= 1023)
+    if (E > 971) q = m >> (1035 - E);
     if (E >= 1) return __longlong_as_double((long long)(((unsigned long long)(E - 1) << 52) + m));
     if (E < -60) return 0.0;
     return __longlong_as_double((long long)(((unsigned long long)(E + 63) << 52) + m)) * 0x1p-64;
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
     for (int j = threadIdx.x; j < nchunk; j += kThreads) mn = fminf(mn, cmin[(size_t)s * nchunk + j]);
     mn = block_reduce(mn, MinOp(), shf, __int_as_float(0x7f800000));   // its barriers also cover tab
     const bool any = !isinf(mn);
-    const float kf = (float)kappa;
+    const float kf = (float)fmin(kappa, 3.0e38);   // finite, so that xf is 0 at the minimum
     const KappaFix kfix = kappa_fix(kappa);
     const float *row = cbar + (size_t)s * L;
     double *out = wtilde + (size_t)s * L;
@@ -226,12 +228,13 @@ __global__ void __launch_bounds__(kThreads) lse_exp(const float *__restrict__ cb
         if (idx < L) {
             const float v = __ldg(row + idx);
             double w = 0.0;
+            unsigned long long q = 0ull;
             // -kappa c - lmax = kappa (cmin - c) <= 0 (exactly 0 at the
             // minimum); its FP32 copy picks the table entry
-            if (any && !isinf(v) && !isnan(v)) w = exp_fixed(mn, v, kf * (mn - v), kfix, tab);
+            if (any && !isinf(v) && !isnan(v)) w = exp_fixed(mn, v, kf * (mn - v), kfix, tab, q);
             out[idx] = w;
             if (want_sum) acc += w;
-            qacc += qfix(w);
+            qacc += q;
         }
     }
     if (cq) {

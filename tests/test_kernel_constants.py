@@ -92,7 +92,9 @@ def _kappa_times(d, kappa):
     K = int(mant * 2.0 ** 53)
     e = int(ex) - 53
     sh = 150 - 53 - E - e
-    return (M * K) >> sh if sh < 128 else 0
+    # the kernel forms floor(M K / 2^13) first: every in-range result has sh >= 13
+    assert sh >= 13 or (M * K) >> sh >= 746 << 53
+    return (M * K) >> sh if sh < 77 else 0
 
 
 def exp_fixed(cmin, c, kappa, tail=True, half=True):
@@ -101,7 +103,7 @@ def exp_fixed(cmin, c, kappa, tail=True, half=True):
     half off plant a mistake: the tail of ln2/256 dropped, r^2 for r^2/2."""
     f32 = np.float32
     cmin, c = f32(cmin), f32(c)
-    xf = f32(f32(kappa) * f32(cmin - c))
+    xf = f32(f32(min(kappa, 3.0e38)) * f32(cmin - c))
     if not xf > f32(-746.0):
         return 0.0
     dh = f32(cmin - c)
@@ -147,6 +149,10 @@ def test_exp_fixed_meets_its_error_bound():
         for dd in (0.0, 0.5, -0.5):
             x = -(kstep + dd) * np.log(2.0) / 256
             cases.append((np.float32(0.0), np.float32(-x / 3.0), 3.0))
+    # x down to the cut-off, where the product's shift is smallest
+    for kappa in (1.0, 1.37, 708.0, 3.3e-5):
+        for xx in (-745.9, -700.0, -512.5, -511.9):
+            cases.append((np.float32(0.0), np.float32(-xx / kappa), kappa))
     cases += [(np.float32(1.5), np.float32(1.5), 708.0), (np.float32(0.0), np.float32(248.0), 3.0),
               (np.float32(2.0), np.float32(2.0 + 744.0 / 11.0), 11.0), (np.float32(-4.0), np.float32(9.0), 5.5)]
     worst = 0.0
@@ -161,6 +167,10 @@ def test_exp_fixed_meets_its_error_bound():
     assert worst < Decimal("1e-15"), worst
     assert exp_fixed(np.float32(1.5), np.float32(1.5), 708.0) == 1.0
     assert exp_fixed(np.float32(0.0), np.float32(1e30), 1.0) == 0.0
+    # kappa beyond the FP32 range: 1 at the minimum, 0 elsewhere; kappa tiny: 1
+    assert exp_fixed(np.float32(2.0), np.float32(2.0), 1e300) == 1.0
+    assert exp_fixed(np.float32(2.0), np.float32(2.5), 1e300) == 0.0
+    assert exp_fixed(np.float32(2.0), np.float32(9.0), 1e-300) == 1.0
 
 
 def _worst_rel_error(cases, **kw):
