@@ -606,9 +606,11 @@ def run_stages(args, local):
     cbar[torch.rand((N, L), device="cuda", generator=g) < 0.05] = float("inf")
     wt = torch.empty((N, L), dtype=torch.float64, device="cuda")
     anc = torch.empty((N, L), dtype=torch.int32, device="cuda")
-    sol = pkg.Solver(p)
-    u = sol.init_controls()
-    u2 = torch.empty_like(u)
+    only = args.stage
+    # the move's solver (the workload's wind field, several GB) only when the move is timed
+    sol = pkg.Solver(p) if only in ("all", "move") else None
+    u = sol.init_controls() if sol else None
+    u2 = torch.empty_like(u) if sol else None
     lwork = torch.empty(pkg.lib().tma_lse_workspace(N, L), dtype=torch.uint8, device="cuda")
     rwork = torch.empty(pkg.lib().tma_resample_workspace(N, L), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -633,14 +635,17 @@ def run_stages(args, local):
     fwork = torch.empty(pkg.lib().tma_lse_resample_workspace(N, L), dtype=torch.uint8, device="cuda")
     deg = torch.zeros(1, dtype=torch.int32, device="cuda")
     kappa = 11.0
-    ms = {
-        "lse": med_ms(lambda: pkg.tma_lse(cbar, kappa, wt, work=lwork)),
-        "resample": med_ms(lambda: pkg.tma_resample(wt, p.seed, 0, 3, 0, anc, work=rwork)),
-        "lse_resample": med_ms(lambda: pkg.tma_lse_resample(cbar, kappa, p.seed, 0, 3, 0, wt, anc, deg,
-                                                            work=fwork)),
-        "move": med_ms(lambda: pkg.tma_move(sol.h, u, anc, 3, u2)),
+    calls = {
+        "lse": lambda: pkg.tma_lse(cbar, kappa, wt, work=lwork),
+        "resample": lambda: pkg.tma_resample(wt, p.seed, 0, 3, 0, anc, work=rwork),
+        "lse_resample": lambda: pkg.tma_lse_resample(cbar, kappa, p.seed, 0, 3, 0, wt, anc, deg, work=fwork),
+        "move": lambda: pkg.tma_move(sol.h, u, anc, 3, u2),
     }
-    sol.close()
+    if only != "all" and only != "lse":
+        pkg.tma_lse(cbar, kappa, wt, work=lwork)         # weights for the resampling on its own
+    ms = {k: med_ms(f) for k, f in calls.items() if only in ("all", k)}
+    if sol:
+        sol.close()
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs") or 6800.0
     hbm_source = "measured" if peaks.get("hbm_gbs") else "fallback"
@@ -656,10 +661,11 @@ def run_stages(args, local):
         out["stages"][k] = {"ms": round(v, 4), "algorithmic_bytes_per_element": algo[k],
                             "achieved_gbs": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm, 3)}
     # the normalisation evaluates one FP64 exp per element
-    out["stages"]["lse"]["fp64_exp_per_s"] = round(n / (ms["lse"] * 1e-3), 1)
+    if "lse" in ms:
+        out["stages"]["lse"]["fp64_exp_per_s"] = round(n / (ms["lse"] * 1e-3), 1)
     # the resampling's share of the fused call (its expansion pass: wtilde read,
     # ancestors written), by difference from the normalisation alone
-    d = ms["lse_resample"] - ms["lse"]
+    d = ms["lse_resample"] - ms["lse"] if "lse" in ms and "lse_resample" in ms else 0.0
     if d > 0:
         gbs = 12 * n / (d * 1e-3) / 1e9
         out["stages"]["resample_in_fused_call"] = {"ms": round(d, 4), "algorithmic_bytes_per_element": 12,
@@ -1067,6 +1073,8 @@ def main(argv=None):
                          "case small)")
     ap.add_argument("--stages", action="store_true",
                     help="time normalisation, resampling and move alone on the 24-aircraft sizes")
+    ap.add_argument("--stage", choices=("all", "lse", "resample", "lse_resample", "move"), default="all",
+                    help="with --stages: time one stage only (the move's solver is allocated only for the move)")
     ap.add_argument("--late", action="store_true",
                     help="profiling cases: use the particles of a finished solve (late iterations)")
     ap.add_argument("--grad-only", action="store_true",

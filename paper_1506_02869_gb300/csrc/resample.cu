@@ -363,18 +363,48 @@ __device__ __forceinline__ int count_below(unsigned long long S, const Threshold
     return n;
 }
 
+// Count below S_j = Sb + D for a chunk whose start Sb has the count nb and
+// the residual Eb = X_nb - Sb Lout (0 <= Eb < Q): with x the real bound of S_j
+// (count = ceil(x)), x - nb = (D Lout - Eb) / Q.  The FP32 estimate est of
+// x - nb has an error below 1/8 + 2^-6 for Lout <= 2^20 (D <= Q, so the
+// product is at most Lout), hence c = nb + max(ceil(est - 1/2), 0) lies within
+// one of x, the count is c or c + 1, and S_j Lout > X_c is decided by
+//   S_j Lout - X_c = D Lout - Eb - (c - nb) Q,
+// a difference below Q < 2^62 in magnitude: it is exact in 64-bit two's
+// complement although its terms wrap.
+struct ChunkBase {
+    unsigned long long Eb;
+    float eb;       // Eb / Q
+    int nb;
+};
+
+__device__ __forceinline__ int count_from_base(unsigned long long D, const ChunkBase &B,
+                                               unsigned long long Q, uint32_t Lout, float ratio)
+{
+    const float est = fmaf(u64_to_float(D), ratio, -B.eb);
+    const int cr = max(__float2int_ru(est - 0.5f), 0);
+    const int c = B.nb + cr;
+    if (c >= (int)Lout) return (int)Lout;
+    const long long diff = (long long)(D * (unsigned long long)Lout - B.Eb - (unsigned long long)(uint32_t)cr * Q);
+    return c + (diff > 0 ? 1 : 0);
+}
+
 constexpr int kWin = 4096;                 // ancestors written per window
-constexpr int kWinPer = kWin / kThreads;   // 16 per thread
-// one padding word per 32: a thread's 16 consecutive entries fall in
-// distinct banks across the warp
-__device__ __forceinline__ int wpad(int k) { return k + (k >> 5); }
+constexpr int kWinPer = kWin / kThreads;   // 16 per thread, four 16-byte vectors
+// window entry k -> shared word: four padding words per 32, so that the
+// 16-byte vectors of the eight threads of a quarter warp (entries 16 t ..
+// 16 t + 15 per thread) fall in distinct banks and stay 16-byte aligned
+__device__ __forceinline__ int wpad(int k) { return k + ((k >> 5) << 2); }
 
 // Copies of element j are the particles [n_(j-1), n_j), n_j the number of
 // thresholds below S_j.  Every element's count is formed independently (eight
 // per thread, no chain between them); the chunk's particles [lo, hi) are
-// then written in windows of kWin: each element with copies marks its first
-// particle with j + 1, a running maximum over the window fills in the rest,
-// and the window goes out with coalesced stores.
+// then written in windows of kWin starting at lo rounded down to a multiple
+// of 4: each element with copies marks its first particle with j + 1, a
+// running maximum over the window fills in the rest (each thread takes 16
+// consecutive entries in registers, then a warp scan and the warps' maxima),
+// and every thread stores its entries that lie in [lo, hi), as 16-byte
+// vectors where the ancestor row is 16-byte aligned.
 __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict__ wtilde, long long L,
                                                        long long Lout, int nchunk,
                                                        const unsigned long long *__restrict__ cq,
@@ -385,22 +415,48 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
                                                        const SegKey *__restrict__ seg_keys,
                                                        const DynState *__restrict__ dyns)
 {
-    __shared__ int win[kWin + kWin / 32];              // padded: wpad(k)
+    __shared__ __align__(16) int win[kWin + kWin / 8];   // padded: wpad(k)
     __shared__ int lastc[kThreads];
     __shared__ int wmax[kThreads / 32];
     __shared__ unsigned long long wtot[kThreads / 32];
     __shared__ unsigned long long seg_before, seg_total;
     __shared__ Thresholds Tsh;
-    __shared__ int n_before;
+    __shared__ ChunkBase Bsh;
     const int s = blockIdx.y, c = blockIdx.x;
     const long long base = (long long)c * kChunk;
     const int len = (int)min((long long)kChunk, L - base);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
+    // this thread's kPer consecutive weights (16-byte loads where aligned;
+    // zero past the chunk), issued before anything else
+    const double *row = wtilde + (size_t)s * L;
+    const int j0 = threadIdx.x * kPer;
+    const bool full = len == kChunk && (((size_t)s * L + base) & 1) == 0;
+    double wv[kPer];
+    if (full) {
+        const double2 *p2 = reinterpret_cast<const double2 *>(row + base + j0);
+#pragma unroll
+        for (int j = 0; j < kPer / 2; ++j) {
+            const double2 v = __ldg(p2 + j);
+            wv[2 * j] = v.x;
+            wv[2 * j + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) wv[j] = j0 + j < len ? __ldg(row + base + j0 + j) : 0.0;
+    }
+    // this thread's window entries start at zero (ordered before any mark by
+    // the barriers below)
+    {
+        int4 *w4 = reinterpret_cast<int4 *>(win + wpad(kWinPer * threadIdx.x));
+#pragma unroll
+        for (int g = 0; g < kWinPer / 4; ++g) w4[g] = make_int4(0, 0, 0, 0);
+    }
+
     if (wid == 0) {
-        // the segment's bookkeeping, while the other warps load and scan: the
-        // chunk's offset and the segment total (integer, order-free), the
-        // uniform, the thresholds, the count below the chunk's start
+        // the segment's bookkeeping, while the loads are in flight: the chunk's
+        // offset and the segment total (integer, order-free), the uniform, the
+        // thresholds, the count below the chunk's start and its residual
         unsigned long long before = 0, total = 0;
         for (int j = lane; j < nchunk; j += 32) {
             const unsigned long long v = cq[(size_t)s * nchunk + j];
@@ -433,34 +489,25 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
                 T.ratio = __fdiv_rn((float)(uint32_t)Lout, u64_to_float(total));
                 T.shift = (float)r * 2.3283064365386963e-10f;
                 Tsh = T;
-                n_before = count_below(before, T);
+                ChunkBase B;
+                B.nb = count_below(before, T);
+                // X_nb - before Lout lies in [0, Q): its low 64 bits are the value
+                const U128 Xn = add64(mul64x32(T.Q, (uint32_t)B.nb), T.Rhi);
+                B.Eb = Xn.lo - mul64x32(before, T.Lout).lo;
+                B.eb = __fdiv_rn(u64_to_float(B.Eb), u64_to_float(T.Q));
+                Bsh = B;
             }
         }
     }
 
-    // inclusive prefix of q over the chunk: every thread loads its kPer
-    // consecutive values (16-byte loads where aligned; zero past the chunk),
-    // scans them in registers; warp scan of the thread totals, block scan of
-    // the warp totals
-    const double *row = wtilde + (size_t)s * L;
-    const int j0 = threadIdx.x * kPer;
+    // inclusive prefix of q over the chunk: every thread scans its kPer
+    // values in registers; warp scan of the thread totals, block scan of the
+    // warp totals
     unsigned long long qv[kPer];
-    if (len == kChunk && (((size_t)s * L + base) & 1) == 0) {
-        const double2 *p2 = reinterpret_cast<const double2 *>(row + base + j0);
-#pragma unroll
-        for (int j = 0; j < kPer / 2; ++j) {
-            const double2 v = __ldg(p2 + j);
-            qv[2 * j] = qfix(v.x);
-            qv[2 * j + 1] = qfix(v.y);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) qv[j] = j0 + j < len ? qfix(__ldg(row + base + j0 + j)) : 0ull;
-    }
     unsigned long long run = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
-        run += qv[j];
+        run += qfix(wv[j]);
         qv[j] = run;
     }
     unsigned long long incl = run;
@@ -483,23 +530,33 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
     }
     unsigned long long woff = 0;
     for (int w = 0; w < wid; ++w) woff += wtot[w];
-    const unsigned long long add = before + woff + (incl - run);
+    // prefix of q within the chunk before this thread's first element
+    const unsigned long long add = woff + (incl - run);
     const Thresholds T = Tsh;
     // the counts of this thread's elements, independent of each other (the
     // elements past the chunk repeat the chunk's last prefix)
     int nc[kPer];
+    if (T.Lout <= (1u << 20)) {
+        const ChunkBase B = Bsh;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) nc[j] = count_below(qv[j] + add, T);
+        for (int j = 0; j < kPer; ++j) nc[j] = count_from_base(qv[j] + add, B, T.Q, T.Lout, T.ratio);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) nc[j] = count_below(qv[j] + add + before, T);
+    }
     lastc[threadIdx.x] = nc[kPer - 1];
     __syncthreads();
-    const int lo = n_before, hi = lastc[kThreads - 1];
+    const int lo = Bsh.nb, hi = lastc[kThreads - 1];
     const int nprev0 = threadIdx.x == 0 ? lo : lastc[threadIdx.x - 1];
+    // 16-byte stores need the row start aligned (Lout a multiple of 4 and an
+    // aligned output array); the window starts are multiples of 4
+    const bool vec = (reinterpret_cast<uintptr_t>(a) & 15) == 0;
+    const int k0 = kWinPer * threadIdx.x;
+    int4 *mine = reinterpret_cast<int4 *>(win + wpad(k0));
 
     int carry = 0;
-    for (int w0 = lo; w0 < hi; w0 += kWin) {
+    for (int w0 = lo & ~3; lo < hi && w0 < hi; w0 += kWin) {
         const int wl = min(kWin, hi - w0);
-        for (int k = threadIdx.x; k < wl; k += kThreads) win[wpad(k)] = 0;
-        __syncthreads();
         int np = nprev0;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
@@ -507,14 +564,25 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
             np = nc[j];
         }
         __syncthreads();
-        // inclusive running maximum over the window: 16 entries per thread
-        const int k0 = threadIdx.x * kWinPer;
+        // inclusive running maximum over the window: this thread's 16 entries
+        // (zero beyond wl) in registers, read and cleared for the next window
         int v[kWinPer];
         int m = 0;
+        if (k0 < wl) {
 #pragma unroll
-        for (int q = 0; q < kWinPer; ++q) {
-            if (k0 + q < wl) m = max(m, win[wpad(k0 + q)]);
-            v[q] = m;
+            for (int g = 0; g < kWinPer / 4; ++g) {
+                const int4 t = mine[g];
+                mine[g] = make_int4(0, 0, 0, 0);
+                v[4 * g] = t.x;
+                v[4 * g + 1] = t.y;
+                v[4 * g + 2] = t.z;
+                v[4 * g + 3] = t.w;
+            }
+#pragma unroll
+            for (int q = 0; q < kWinPer; ++q) {
+                m = max(m, v[q]);
+                v[q] = m;
+            }
         }
         int inc = m;
 #pragma unroll
@@ -526,16 +594,33 @@ __global__ void __launch_bounds__(kThreads) res_expand(const double *__restrict_
         int ex = __shfl_up_sync(0xffffffffu, inc, 1);
         if (lane == 0) ex = 0;
         __syncthreads();
-        int pre = carry;
-        for (int w = 0; w < wid; ++w) pre = max(pre, wmax[w]);
-        ex = max(ex, pre);
+        int pre = carry, all = carry;
 #pragma unroll
-        for (int q = 0; q < kWinPer; ++q)
-            if (k0 + q < wl) win[wpad(k0 + q)] = max(v[q], ex);
-        for (int w = 0; w < kThreads / 32; ++w) carry = max(carry, wmax[w]);
-        __syncthreads();
-        for (int k = threadIdx.x; k < wl; k += kThreads) a[w0 + k] = (int32_t)(base + win[wpad(k)] - 1);
-        __syncthreads();
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const int t = wmax[w];
+            if (w < wid) pre = t > pre ? t : pre;
+            all = t > all ? t : all;
+        }
+        ex = max(ex, pre);
+        carry = all;
+        if (k0 < wl) {
+            // entries w0 + k0 + q; the ancestor of particle p is base + value - 1
+            const int b1 = (int)base - 1;
+#pragma unroll
+            for (int g = 0; g < kWinPer / 4; ++g) {
+                const int p0 = w0 + k0 + 4 * g;
+                const int4 o = make_int4(b1 + max(v[4 * g], ex), b1 + max(v[4 * g + 1], ex),
+                                         b1 + max(v[4 * g + 2], ex), b1 + max(v[4 * g + 3], ex));
+                if (vec && p0 >= lo && p0 + 4 <= hi) {
+                    *reinterpret_cast<int4 *>(a + p0) = o;
+                } else {
+                    if (p0 >= lo && p0 < hi) a[p0] = o.x;
+                    if (p0 + 1 >= lo && p0 + 1 < hi) a[p0 + 1] = o.y;
+                    if (p0 + 2 >= lo && p0 + 2 < hi) a[p0 + 2] = o.z;
+                    if (p0 + 3 >= lo && p0 + 3 < hi) a[p0 + 3] = o.w;
+                }
+            }
+        }
     }
 }
 

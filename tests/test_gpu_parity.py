@@ -264,8 +264,12 @@ def test_lse_weights_are_the_integer_exponential(torch, pkg, kappa):
 # ------------------------------------------------------------- resampling
 
 @pytest.mark.parametrize("nseg,L", [(8, 65536), (24, 262144), (1, 1), (3, 5), (2, 2049), (4, 6144),
-                                    (1, 1 << 22)])
+                                    (1, 1 << 20), (1, (1 << 20) + 2051), (1, 1 << 22)])
 def test_resample_bit_exact(torch, pkg, nseg, L):
+    """Ancestors equal the oracle's bit for bit.  The kernel settles each
+    element's count three ways by the output count: from its chunk's base with
+    64-bit residuals (up to 2^20), one 128-bit comparison (up to 2^21), a
+    stepped search beyond; the sizes reach all three."""
     rng = _rng(nseg + L)
     w = S.random_wtilde(nseg, L, rng)
     seed, sid, J, mpc = 20150601 + L, nseg % 3, L % 50, 7
