@@ -115,8 +115,8 @@ ROLLOUT_TRAFFIC = {"sources_sha256_16": "817f23a322d9a32f",
 
 
 def rollout_kernel_name(variant):
-    """The rollout kernel a launch variant runs (8-12: two wind samples per thread; 13-15 the
-    one-sample kernel on 16-particle tiles)."""
+    """The rollout kernel a launch variant runs (8-12: two wind samples per thread; 13-15 and
+    16-17 the one-sample kernel on 16- and 8-particle tiles)."""
     return "rollout_pair_kernel" if variant is not None and 8 <= variant < 13 else "rollout_kernel"
 
 
@@ -643,6 +643,8 @@ def run_stages(args, local):
     }
     if only != "all" and only != "lse":
         pkg.tma_lse(cbar, kappa, wt, work=lwork)         # weights for the resampling on its own
+    if only == "move":
+        pkg.tma_resample(wt, p.seed, 0, 3, 0, anc, work=rwork)   # the move's ancestors
     ms = {k: med_ms(f) for k, f in calls.items() if only in ("all", k)}
     if sol:
         sol.close()

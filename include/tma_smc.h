@@ -255,9 +255,13 @@ tma_status tma_get_tuning(tma_solver *s, int32_t *variant, int32_t *n_timed, int
  * wind-independent part of each step -- limits, drag, thrust, fuel, altitude,
  * airspeed, heading -- computed once for both), 256x3, 256x2, 384x2, 512x1,
  * 768x1; only for the shared wind field (wind mode 0) without the rolling
- * window and M >= 2.  Every variant returns the same bits.  A variant whose cap
- * is below the block (32 N threads) or that does not apply to the problem
- * returns TMA_ERR_INVALID_ARG. */
+ * window and M >= 2.  13-15: the one-sample kernel on tiles of 16 particles (a
+ * warp holds two aircraft; block 16 N threads), 768x1, 384x2, 512x2; 16-17: on
+ * tiles of 8 particles (four aircraft per warp; block 8 N threads), 512x2,
+ * 384x2; both for the shared wind field only and for N a multiple of 2 or 4
+ * (full warps).  Every variant returns the same bits.  A variant whose cap is
+ * below the block or that does not apply to the problem returns
+ * TMA_ERR_INVALID_ARG. */
 tma_status tma_set_tuning(tma_solver *s, int32_t variant);
 
 /* The same record for the kernel of tma_rollout_grad, tuned on its first use

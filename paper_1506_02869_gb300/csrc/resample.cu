@@ -20,10 +20,13 @@
 //             n_j > l}: each element with copies marks its first particle in a
 //             shared-memory window and a running maximum fills in the rest.
 //             Because S_j > floor(y) <=> S_j > y for integer S_j, a count is
-//             settled by comparing 128-bit integers (S_j Lout against
+//             settled by comparing integers (S_j Lout against
 //             l Q + floor(r Q / 2^32), no division); an FP32 estimate within
-//             one of the count says which l to compare.  Integer arithmetic
-//             makes the result independent of the summation order.  Lout
+//             one of the count says which l to compare.  The comparison is
+//             taken relative to the chunk's start, where the difference fits
+//             in 64 bits (output counts up to 2^20), else in 128 bits.
+//             Integer arithmetic makes the result independent of the
+//             summation order.  Lout
 //             ancestors are drawn from the Lin weighted particles of the
 //             segment (Lout = Lin for a fixed particle count).
 #include <cfloat>
