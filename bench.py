@@ -110,8 +110,8 @@ def flops_per_unit_tally(p):
 # rollout kernel, from a one-pass ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch late in a solve: iteration 20 of 30);
 # valid only for the kernel sources they were taken on.
-ROLLOUT_TRAFFIC = {"sources_sha256_16": "817f23a322d9a32f",
-                   "bytes_per_launch": {"c3:rollout_kernel": 45993266688 + 3255089920}}
+ROLLOUT_TRAFFIC = {"sources_sha256_16": "9c6681ad7c36f584",
+                   "bytes_per_launch": {"c3:rollout_kernel": 47479898368 + 4464612352}}
 
 
 def rollout_kernel_name(variant):
