@@ -369,9 +369,11 @@ __device__ __forceinline__ int count_below(unsigned long long S, const Threshold
 // Count below S_j = Sb + D for a chunk whose start Sb has the count nb and
 // the residual Eb = X_nb - Sb Lout (0 <= Eb < Q): with x the real bound of S_j
 // (count = ceil(x)), x - nb = (D Lout - Eb) / Q.  The FP32 estimate est of
-// x - nb has an error below 1/8 + 2^-6 for Lout <= 2^20 (D <= Q, so the
-// product is at most Lout), hence c = nb + max(ceil(est - 1/2), 0) lies within
-// one of x, the count is c or c + 1, and S_j Lout > X_c is decided by
+// x - nb is within 6 2^-24 (Lout + 1) of it to first order (D and the ratio
+// Lout / Q as FP32 within 2^-23 and 3 2^-24 relative, D <= Q so the product is
+// at most Lout; Eb / Q within 5 2^-24; one rounding of the fused result), below
+// 1/2 for Lout <= 2^20, hence c = nb + max(ceil(est - 1/2), 0) lies within one
+// of x, the count is c or c + 1, and S_j Lout > X_c is decided by
 //   S_j Lout - X_c = D Lout - Eb - (c - nb) Q,
 // a difference below Q < 2^62 in magnitude: it is exact in 64-bit two's
 // complement although its terms wrap.
